@@ -1,0 +1,377 @@
+"""Throughput of the NBS correlator path on GB300: 52-channel correlators per second at 32^3.
+
+One step = one full pass of the hot path -- propagator rescale, baryon blocks,
+forward FFT, effective blocks and their product in momentum space, inverse
+FFT, FP64 restore -- for every one of the 52 channels on one timeslice of a
+32^3 x 32 lattice (synthetic seeded propagators with exp(-0.5 t) decay).
+Step k processes timeslice (W + k) mod 32.  A correlator is one
+(channel, timeslice): 64 spin components x 32^3 separations.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on the host
+cores on a bounded sample of the same workload, scaled to the same unit.
+Under torchrun every rank runs its own 32^3 x 32 lattice (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_DEFAULT, T_DEFAULT, DECAY, SEED = 32, 32, 0.5, 1607
+METRIC = "52-channel NBS correlators/sec/timeslice at 32^3"
+UNIT = "correlators/s"
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--L", type=int, default=L_DEFAULT)
+    ap.add_argument("--T", type=int, default=T_DEFAULT)
+    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# ---- clocks during the timed region ---------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- the CPU oracle arm ------------------------------------------------------------------
+
+def oracle_sample_setup(L, seed=SEED, t=3):
+    """Oracle state for the bounded sample: one 144-index topology of the pn channel at L^3."""
+    import numpy as np
+    import nbs_inputs as I
+    from oracle import nbs_oracle as O
+    Sl, Ss = I.propagator(seed, "l", L, t, DECAY), I.propagator(seed, "s", L, t, DECAY)
+    props = {"u": Sl, "d": Sl, "s": Ss}
+    blocks = O._Blocks(props)
+    terms = O.topologies("p", "n", "p", "n")
+    term = max(terms, key=O.xi_size)
+    t0 = time.perf_counter()
+    E1 = O.effective_block(term, 1, blocks)
+    E2 = O.effective_block(term, 2, blocks)
+    setup_s = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    return dict(O=O, E1=E1, E2=E2, term=term, L=L, rng=rng, setup_s=setup_s)
+
+
+def oracle_cmac_per_correlator(L):
+    """Complex multiply-adds of the oracle's direct sum for one correlator, averaged over the 52 channels."""
+    from oracle import nbs_oracle as O
+    from paper_1604_07983_gb300 import channel_names
+    names = channel_names()
+    V = L ** 3
+    tot = sum(sum(O.xi_size(t) for t in O.topologies(*ch)) for ch in names)
+    return 64.0 * tot / len(names) * V * V
+
+
+def oracle_step(st, n_r=1):
+    """Direct sum of the sampled topology for n_r random separations; returns the CMAC done."""
+    L = st["L"]
+    rs = [tuple(int(v) for v in st["rng"].integers(0, L, 3)) for _ in range(n_r)]
+    st["O"].direct_sum(st["E1"], st["E2"], L, rs, table_bytes=0)
+    return 64.0 * st["O"].xi_size(st["term"]) * L ** 3 * n_r
+
+
+def host_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d.get("num_threads") for d in threadpool_info() if d.get("internal_api") == "openblas"]
+        if n and n[0]:
+            return int(n[0])
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def cpu_baseline(L, budget_s=15.0):
+    st = oracle_sample_setup(L)
+    cmac, el, n = 0.0, 0.0, 0
+    t0 = time.perf_counter()
+    while el < budget_s or n < 2:
+        cmac += oracle_step(st)
+        n += 1
+        el = time.perf_counter() - t0
+    rate = cmac / el
+    per_corr = oracle_cmac_per_correlator(L)
+    return {"value": rate / per_corr, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "sample": ("FP64 oracle direct sum over X (O(V^2)) of the largest pn topology (|xi|=144) at %d^3, "
+                       "%d separations r in %.1f s after %.1f s of block setup; %.3g CMAC/s scaled by the "
+                       "oracle's CMAC per correlator averaged over the 52 channels (%.3g)"
+                       % (L, n, el, st["setup_s"], rate, per_corr))}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    L = args.L
+    st = oracle_sample_setup(L)
+    per_corr = oracle_cmac_per_correlator(L)
+    for _ in range(args.warmup):
+        oracle_step(st)
+    cmac = 0.0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cmac += oracle_step(st)
+    el = time.perf_counter() - t0
+    value = cmac / el / per_corr
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "%d^3 x %d lattice, 52 channels, exp(-0.5 t) seeded propagators" % (L, args.T),
+                       "precision": "fp64 oracle", "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                             "sample": "each step: oracle direct sum of the largest pn topology at one random r "
+                                       "at %d^3, scaled by the oracle's CMAC per correlator (%.3g)" % (L, per_corr)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- the GPU arm ---------------------------------------------------------------------------
+
+def make_props_host(L, T, seed):
+    import nbs_inputs as I
+    return [(I.propagator(seed, "l", L, t, DECAY), I.propagator(seed, "s", L, t, DECAY)) for t in range(T)]
+
+
+def contraction_flops(ids):
+    from paper_1604_07983_gb300 import plan_tables
+    tb = plan_tables(ids)
+    return 8.0 * 64.0 * float(tb["terms"][:, 1].sum()), tb
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import paper_1604_07983_gb300 as P
+    try:
+        P.lib()
+    except ImportError:
+        from paper_1604_07983_gb300 import build as B
+        B.build()
+        P.lib()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    L, T = args.L, args.T
+    V = L ** 3
+    prec = P.NBS_FP32 if args.precision == "fp32" else P.NBS_FP64
+    ids = list(range(P.channel_count()))
+    nch = len(ids)
+    seed = SEED + rank
+    host_props = make_props_host(L, T, seed)
+
+    ctx = P.Context(L, T, precision=prec)
+    for t, (Sl, Ss) in enumerate(host_props):
+        ctx.load_props(torch.from_numpy(Sl).cuda(), torch.from_numpy(Ss).cuda(), t)
+    out = torch.empty((nch, 1, 4, 4, 2, 2, V), dtype=torch.complex128, device="cuda")
+    torch.cuda.synchronize()
+
+    for k in range(args.warmup):
+        ctx.correlate(ids, k % T, k % T + 1, out)
+    torch.cuda.synchronize()
+
+    ctx.set_profiling(True)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clocks:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        start.record()
+        for k in range(args.steps):
+            t = (args.warmup + k) % T
+            ctx.correlate(ids, t, t + 1, out)
+        stop.record()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    ms = start.elapsed_time(stop)
+    stages, launches = ctx.profile()
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = nch * args.steps * world / (ms / 1e3)
+
+    # ---- end to end through the public API with host buffers ----
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    pin_u = [torch.from_numpy(Sl).pin_memory() for Sl, _ in host_props[:e2e_steps]]
+    pin_s = [torch.from_numpy(Ss).pin_memory() for _, Ss in host_props[:e2e_steps]]
+    out_h = torch.empty((nch, 1, 4, 4, 2, 2, V), dtype=torch.complex128).pin_memory()
+    ctx.set_profiling(False)
+    ctx.load_props(pin_u[0], pin_s[0], 0)
+    ctx.correlate(ids, 0, 1, out_h)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        ctx.load_props(pin_u[k], pin_s[k], k)
+        ctx.correlate(ids, k, k + 1, out_h)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = nch * e2e_steps * world / e2e_s
+    h2d = 2 * V * 144 * 16
+    d2h = nch * 64 * V * 16
+    ctx.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel ----
+    peaks = measured_peaks()
+    fl, tb = contraction_flops(ids)
+    flops_per_launch = fl * V
+    ncomp = 4 * len(tb["cells"])
+    csz = 8 if prec == P.NBS_FP32 else 16
+    dominant = max(stages, key=lambda k: stages[k])
+    per_launch_ms = {k: v / args.steps for k, v in stages.items()}
+    if dominant == "contract":
+        if prec == P.NBS_FP32:
+            peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+            peak_src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+        else:
+            peak = 1.25
+            peak_src = "nominal GB300 FP64 1.25 TFLOP/s"
+        ach = flops_per_launch / (per_launch_ms["contract"] / 1e3) / 1e12
+        roof = {"kernel": "k_contract", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "peak_source": peak_src,
+                "work_per_launch": "8 flop x 64 x sum|xi~| (=%d) x V complex MACs of Eq. (4.3)"
+                                   % int(tb["terms"][:, 1].sum())}
+    else:
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        if dominant == "fft_fwd":
+            nbytes = 2.0 * ncomp * V * csz
+        elif dominant == "fft_inv":
+            nbytes = 2.0 * nch * 64 * V * csz
+        elif dominant == "blocks":
+            nbytes = ncomp * V * csz + 2 * 144 * V * csz
+        else:
+            nbytes = 2 * 144 * V * (16 + csz)
+        ach = nbytes / (per_launch_ms[dominant] / 1e3) / 1e9
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == P.NBS_FP32 else "f64",
+        "data": "synthetic seeded Gaussian propagators, exp(-0.5 t) decay",
+        "config": {"workload": "%d^3 x %d lattice, all %d channels, one timeslice per step" % (L, T, nch),
+                   "precision": "fp64 rescale -> fp32 blocks/FFT/contraction -> fp64 restore"
+                   if prec == P.NBS_FP32 else "fp64", "l2": "inputs larger than L2 (blocks %.2f GB/step)"
+                   % (ncomp * V * csz / 1e9), "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": roof,
+        "stages_ms_per_step": {k: round(v, 4) for k, v in per_launch_ms.items()},
+        "gpu_launches": int(launches),
+        "clocks": clocks.summary(),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(L)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

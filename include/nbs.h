@@ -1,0 +1,168 @@
+/*
+ * nbs.h -- C ABI of the GB300 library for octet-octet Nambu-Bethe-Salpeter
+ * four-point correlators by the effective baryon block algorithm
+ * (H. Nemura, arXiv:1604.07983, LATTICE 2015).
+ *
+ * Computes, for every requested channel <B1 B2 | B3bar B4bar> and timeslice t,
+ *
+ *   F_{a1 a2, a3 a4}(r, t) = sum_X < B1_a1(X + r, t) B2_a2(X, t) Jbar_{B3 a3, B4 a4}(t0) >
+ *
+ * (Sec. 2, first equation) from wall-source light (u = d) and strange quark
+ * propagators, following the paper's pipeline: baryon blocks per site
+ * (Eq. (4.1), Sec. 4 (i)), a forward 3-D FFT per block component (Eq. (2.6)),
+ * effective blocks and their product in momentum space (Eqs. (4.2)-(4.3),
+ * Sec. 4 (ii)-(iii)) and an inverse FFT.
+ *
+ * Conventions: Dirac representation with C gamma5 =
+ * [[0,1,0,0],[-1,0,0,0],[0,0,0,1],[0,0,-1,0]]; source spins a3, a4 in {0,1}
+ * (upper components); forward FFT e^{-iq.x} unnormalised, inverse
+ * e^{+iq.r}/V; X + r periodic; site = x + L*(y + L*z).
+ *
+ * Errors: every call returns NBS_OK (0) or a negative NBS_E* code; the text of
+ * the last error of a context is nbs_last_error().  No call aborts the process.
+ * Threading: a context is used by one host thread at a time.
+ * Memory: the context owns every device buffer it allocates (through the
+ * allocator hook when one is installed, else cudaMalloc); callers own the
+ * buffers they pass in.
+ */
+#ifndef NBS_H
+#define NBS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define NBS_OK        0
+#define NBS_EINVAL   -1   /* bad argument (size, id, null pointer, range)      */
+#define NBS_ENOMEM   -2   /* device or host allocation failed                   */
+#define NBS_ECUDA    -3   /* a CUDA runtime call or kernel launch failed         */
+#define NBS_ESTATE   -4   /* call out of order (e.g. no propagators for t)       */
+#define NBS_ETIMEOUT -5   /* a bounded device wait gave up                       */
+#define NBS_ENAN     -6   /* non-finite value in the propagators                 */
+
+/* ---- precision modes (nbs_set_precision) ------------------------------- */
+#define NBS_FP64   0   /* blocks, FFTs and contraction in complex FP64           */
+#define NBS_FP32   1   /* FP64 rescale -> FP32 blocks/FFT/contraction -> FP64 restore */
+
+/* ---- propagator element types (nbs_load_props) ------------------------- */
+#define NBS_C128   0   /* interleaved complex double */
+#define NBS_C64    1   /* interleaved complex float  */
+
+/* ---- number of output spin components per (channel, t, r) -------------- */
+#define NBS_NSPIN  64  /* a1 (4) x a2 (4) x a3 (2) x a4 (2) */
+
+typedef struct nbs_ctx nbs_ctx;
+typedef struct nbs_plan nbs_plan;
+
+/* Device allocator hook: alloc(bytes, user) returns a device pointer or NULL;
+ * free(ptr, user).  Installed per process before nbs_create; NULL restores
+ * cudaMalloc/cudaFree. */
+typedef void* (*nbs_alloc_fn)(unsigned long long bytes, void* user);
+typedef void (*nbs_free_fn)(void* ptr, void* user);
+int nbs_set_allocator(nbs_alloc_fn alloc, nbs_free_fn free_fn, void* user);
+
+/* Create a context for an L^3 x T lattice on the current CUDA device.
+ * flavours: 2 = {light (u = d), strange} (isospin limit, Sec. 4 (i));
+ * any other value is rejected with NBS_EINVAL.  1 <= L <= 64, 1 <= T <= 4096.
+ * Allocates the propagator store (2 flavours x T timeslices). */
+int nbs_create(nbs_ctx** out, int L, int T, int flavours);
+int nbs_destroy(nbs_ctx* h);
+
+/* Select the arithmetic of the path (NBS_FP64 default, or NBS_FP32). */
+int nbs_set_precision(nbs_ctx* h, int mode);
+
+/* Run every later call of the context on this cudaStream_t (0 = legacy default). */
+int nbs_set_stream(nbs_ctx* h, void* stream);
+
+/* Copy one timeslice of the light (u) and strange (s) propagators into the
+ * context.  Layout of each: [z][y][x][i = 3*alpha + a][j = 3*alpha' + a'],
+ * V*144 complex numbers of `dtype`; on_device selects device or host
+ * pointers.  The library copies; the caller keeps ownership.  0 <= t < T. */
+int nbs_load_props(nbs_ctx* h, const void* u, const void* s, int t, int dtype, int on_device);
+
+/* Build the momentum-space baryon blocks of timeslice t: per-timeslice
+ * power-of-two rescale of the propagators, blocks of Eq. (4.1) for every
+ * sink field, forward 3-D FFT of every component (Sec. 4 (i)).  Replaces the
+ * blocks of any earlier timeslice.  NBS_ESTATE if no propagators for t. */
+int nbs_blocks(nbs_ctx* h, int t);
+
+/* Correlators of n_channels channels (ids of the built-in table, see
+ * nbs_channel_info) for timeslices t_begin <= t < t_end.  For each t the
+ * blocks are (re)built when needed, the effective blocks are formed and
+ * multiplied in momentum space (Eqs. (4.2)-(4.3)), and the inverse FFT
+ * gives F(r).  out: caller-allocated complex128
+ *   [n_channels][t_end - t_begin][a1][a2][a3][a4][z][y][x]
+ * on the device (out_on_device = 1) or on the host (0; pinned memory is
+ * copied asynchronously per timeslice).  Returns when `out` is complete. */
+int nbs_correlate(nbs_ctx* h, const int* channel_ids, int n_channels,
+                  int t_begin, int t_end, void* out, int out_on_device);
+
+/* Zero-momentum projection of the last nbs_correlate's final timeslice,
+ * sum_r F(r) = F~(q = 0), complex128 [n_channels][64] on the host. */
+int nbs_zero_momentum(nbs_ctx* h, double* out);
+
+/* Launch-shape parameters (for tuning; results do not depend on them).
+ * NBS_PARAM_CONTRACT_CFG: A*10 + W, A = sink spins alpha1 per thread of the
+ * contraction (1, 2 or 4), W = warps per block (1, 2 or 4); 0 = default
+ * (42 for FP32, 21 for FP64).  NBS_EINVAL for any other value. */
+#define NBS_PARAM_CONTRACT_CFG 0
+int nbs_set_param(nbs_ctx* h, int param, int value);
+
+/* Profiling (stage timing with CUDA events on the context's stream).
+ * nbs_set_profiling(h, 1) clears the counters and records an event pair around
+ * every stage of later calls; nbs_profile() returns the accumulated device
+ * milliseconds per stage, stage_ms[NBS_NSTAGES] = {rescale (a0), blocks (a1),
+ * forward FFT (a2), effective blocks + contraction (a3, a4), inverse FFT (a5),
+ * restore + output copy (a5)}, and the number of kernels launched. */
+#define NBS_NSTAGES 6
+int nbs_set_profiling(nbs_ctx* h, int on);
+int nbs_profile(nbs_ctx* h, double* stage_ms, long long* launches);
+
+/* Built-in channel table: the 52 octet-octet channels from NN to XiXi
+ * (Sec. 1 and Sec. 4 (iii)), reconstructed as the sink x source pairs of
+ * each strangeness sector at minimal |I3| without the four that vanish
+ * identically for u = d. */
+int nbs_channel_count(void);
+/* Writes "B1 B2 | B3 B4" into buf (len bytes incl. NUL); returns the
+ * number of light quarks n_l (n_s = 6 - n_l) or a negative error. */
+int nbs_channel_info(int id, char* buf, int len);
+
+/* Text of the last error on this context (or of the last context-less call
+ * when h is NULL).  Never NULL. */
+const char* nbs_last_error(const nbs_ctx* h);
+
+/* ---- host-only introspection of the compiled channel tables ------------
+ * nbs_plan_create runs the host "channel compiler" (Sec. 4 (ii)-(iii): the
+ * diagrammatic classification done on the CPU and packed as structures of
+ * arrays) for a channel list without touching a GPU.  Tests use it to check
+ * the tables on the CPU. */
+int nbs_plan_create(nbs_plan** out, const int* channel_ids, int n_channels);
+int nbs_plan_destroy(nbs_plan* p);
+/* sizes[0..NBS_PLAN_NSIZES-1]: see NBS_PS_* below */
+#define NBS_PS_NTYPES     0   /* stored block types                          */
+#define NBS_PS_NCELLS     1   /* total cells (components = 4 * cells)        */
+#define NBS_PS_NTYPETERMS 2   /* recipe terms over all types                 */
+#define NBS_PS_NTERMS     3   /* contraction terms                           */
+#define NBS_PS_NENT1      4   /* side-1 gather entries                       */
+#define NBS_PS_NENT2      5   /* side-2 gather entries                       */
+#define NBS_PS_NCH        6   /* channels                                    */
+#define NBS_PLAN_NSIZES   7
+int nbs_plan_sizes(const nbs_plan* p, long long* sizes);
+/* what: NBS_PX_* ; dst must hold the documented number of int32/double */
+#define NBS_PX_TYPES      0   /* int32 [ntypes][4]: cell_off, ncell, term_off, nterm   */
+#define NBS_PX_TYPETERMS  1   /* int32 [nterms][4]: pattern, a0, a1, a2                */
+#define NBS_PX_TYPECOEF   2   /* double [nterms]                                        */
+#define NBS_PX_CELLS      3   /* int32 [ncells]: y0 + 12*y1 + 144*y2                    */
+#define NBS_PX_TERMS      4   /* int32 [nterm][8]: ch, K, shape, n1, n2, off1, off2, 0  */
+#define NBS_PX_ENT1_CELL  5   /* int32 [nent1]  */
+#define NBS_PX_ENT1_COEF  6   /* double [nent1] */
+#define NBS_PX_ENT2_CELL  7   /* int32 [nent2]  */
+#define NBS_PX_ENT2_COEF  8   /* double [nent2] */
+#define NBS_PX_CHANNELS   9   /* int32 [nch][4]: term_begin, term_end, n_l, n_s         */
+int nbs_plan_export(const nbs_plan* p, int what, void* dst);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBS_H */

@@ -1,0 +1,82 @@
+// common.cuh -- complex helpers and launch declarations shared by the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nbs {
+
+template <typename T> struct cplx_t;
+template <> struct cplx_t<float> { using type = float2; };
+template <> struct cplx_t<double> { using type = double2; };
+template <typename T> using C = typename cplx_t<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ C<T> cmake(T re, T im) { C<T> z; z.x = re; z.y = im; return z; }
+template <typename T> __host__ __device__ __forceinline__ C<T> czero() { return cmake<T>(T(0), T(0)); }
+template <typename T> __host__ __device__ __forceinline__ C<T> cadd(C<T> a, C<T> b) { return cmake<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __host__ __device__ __forceinline__ C<T> csub(C<T> a, C<T> b) { return cmake<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __host__ __device__ __forceinline__ C<T> cmul(C<T> a, C<T> b) {
+  return cmake<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc += a * b
+template <typename T> __host__ __device__ __forceinline__ void cfma(C<T>& acc, C<T> a, C<T> b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += s * a   (s real)
+template <typename T> __host__ __device__ __forceinline__ void crfma(C<T>& acc, T s, C<T> a) {
+  acc.x = fma(s, a.x, acc.x);
+  acc.y = fma(s, a.y, acc.y);
+}
+
+// Gather-table entry of the contraction: stored cell and real coefficient.
+template <typename T> struct Ent { int cell; T coef; };
+template <> struct __align__(16) Ent<double> { int cell; int pad; double coef; };
+
+struct DevTerm { int ch, K, shape, n1, n2, off1, off2, pad; };
+
+// Block-type recipe for the field-block kernel (constant memory).
+#define NBS_MAX_TYPES 8
+#define NBS_MAX_TYPE_TERMS 8
+struct TypeRecipe {
+  int nterms;
+  int cell_off;
+  int ncell;
+  int pad;
+  int pat[NBS_MAX_TYPE_TERMS];
+  int arg[NBS_MAX_TYPE_TERMS];       // a0 + 4*a1 + 16*a2
+  double coef[NBS_MAX_TYPE_TERMS];
+};
+
+// ---- launchers (defined in the .cu files) ----------------------------------
+// kernels_blocks.cu
+cudaError_t launch_props_maxabs(const void* u, const void* s, int in_c64, int V,
+                                unsigned long long* maxbits, int* flags, cudaStream_t st);
+template <typename T>
+cudaError_t launch_props_scale(const void* u, const void* s, int in_c64, int V,
+                               const unsigned long long* maxbits, int* exps, C<T>* out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_diquarks(const C<T>* props, int V, C<T>* Q, cudaStream_t st);
+struct TypeRecipeSet { TypeRecipe t[NBS_MAX_TYPES]; };
+template <typename T>
+cudaError_t launch_field_blocks(const C<T>* props, const C<T>* Q, const int* cells, int ncells,
+                                const TypeRecipeSet& recipes, int V, C<T>* FB, cudaStream_t st);
+// fft.cu
+cudaError_t fft_init();
+bool fft_supported(int L);
+// forward FFT of the stored blocks, layout [cell][z][y][x][alpha]
+template <typename T>
+cudaError_t fft3d_blocks(C<T>* data, long long ncells, int L, cudaStream_t st);
+// inverse FFT of nbatch contiguous cubes [batch][z][y][x]
+template <typename T>
+cudaError_t fft3d_inverse(C<T>* data, long long nbatch, int L, cudaStream_t st);
+// kernels_contract.cu
+template <typename T>
+cudaError_t launch_contract(const C<T>* FB, int L, const DevTerm* terms, const int* ch_tb, int nch,
+                            const Ent<T>* e1, const Ent<T>* e2, C<T>* Ft, int cfg, cudaStream_t st);
+template <typename T>
+cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_nl, const int* exps,
+                           double2* out, long long ch_stride, cudaStream_t st);
+
+}  // namespace nbs

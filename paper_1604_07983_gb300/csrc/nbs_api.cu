@@ -1,0 +1,631 @@
+// nbs_api.cu -- the C ABI (include/nbs.h): context, memory, orchestration.
+//
+// Per timeslice the path is (arXiv:1604.07983, Sec. 4):
+//   a0  max|S| per flavour -> power-of-two rescale + transpose       (kernels_blocks.cu)
+//   a1  diquarks -> field blocks of Eq. (4.1)                        (kernels_blocks.cu)
+//   a2  forward 3-D FFT of every block component                      (fft.cu)
+//   a3+a4 effective blocks and their product in q-space, Eq. (4.3)    (kernels_contract.cu)
+//   a5  inverse 3-D FFT, FP64 restore, copy to the caller             (fft.cu, kernels_contract.cu)
+// all on one stream; host outputs leave through a second stream from two
+// alternating staging buffers so that the copy of t overlaps work on t+1.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nbs.h"
+#include "common.cuh"
+#include "plan.h"
+
+using namespace nbs;
+
+namespace {
+
+nbs_alloc_fn g_alloc = nullptr;
+nbs_free_fn g_free = nullptr;
+void* g_alloc_user = nullptr;
+thread_local std::string g_err;
+
+void* dev_alloc(size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (g_alloc) return g_alloc((unsigned long long)bytes, g_alloc_user);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+void dev_free(void* p, nbs_free_fn f, void* user) {
+  if (!p) return;
+  if (f) f(p, user);
+  else cudaFree(p);
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct nbs_plan {
+  Plan plan;
+};
+
+struct nbs_ctx {
+  int L = 0, T = 0, V = 0, device = 0;
+  int mode = NBS_FP64;
+  cudaStream_t st = 0;
+  cudaStream_t cst = nullptr;
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};   // staging buffer b copied out
+  cudaEvent_t ev_ready[2] = {nullptr, nullptr};  // staging buffer b written
+  std::string err;
+  nbs_free_fn free_fn = nullptr;  // allocator at creation
+  void* free_user = nullptr;
+
+  DevBuf props;                 // [T][2][V*144] complex128 slots
+  std::vector<signed char> have;  // -1 none, NBS_C128, NBS_C64
+  DevBuf propsT, Q, FB, Ft, zm, small;
+  DevBuf stage[2];
+  unsigned long long* maxbits = nullptr;  // [2]
+  int* flags = nullptr;                   // [1]
+  int* exps = nullptr;                    // [2]
+  int* host_flags = nullptr;              // pinned copy of flags
+
+  // compiled channel tables
+  bool plan_ok = false;
+  std::vector<int> plan_ids;
+  Plan plan;
+  int plan_gen = 0;
+  DevBuf d_terms, d_chtb, d_chnl, d_e1, d_e2, d_cells;
+  int tables_mode = -1;
+  TypeRecipeSet recipes;
+
+  int blocks_t = -1, blocks_mode = -1, blocks_gen = -1;
+  int last_nch = 0;
+  int contract_cfg = 0;  // NBS_PARAM_CONTRACT_CFG, 0 = default
+
+  // profiling: CUDA events around each stage, resolved after the final sync
+  bool prof = false;
+  std::vector<cudaEvent_t> evpool;
+  size_t evnext = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  double stage_ms[NBS_NSTAGES] = {};
+  long long launches = 0;
+};
+
+namespace {
+
+int fail(nbs_ctx* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(nbs_ctx* h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return fail(h, NBS_ECUDA, m);
+}
+
+cudaEvent_t prof_event(nbs_ctx* h) {
+  if (h->evnext == h->evpool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->evpool.push_back(e);
+  }
+  return h->evpool[h->evnext++];
+}
+
+// record the start of a stage; returns the event (or null when profiling is off)
+cudaEvent_t stage_begin(nbs_ctx* h) {
+  if (!h->prof) return nullptr;
+  cudaEvent_t e = prof_event(h);
+  if (e) cudaEventRecord(e, h->st);
+  return e;
+}
+void stage_end(nbs_ctx* h, int stage, cudaEvent_t begin) {
+  if (!h->prof || !begin) return;
+  cudaEvent_t e = prof_event(h);
+  if (!e) return;
+  cudaEventRecord(e, h->st);
+  h->marks.push_back({stage, {begin, e}});
+}
+// after a synchronisation: accumulate the stage times and recycle the events
+void prof_resolve(nbs_ctx* h) {
+  for (auto& m : h->marks) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, m.second.first, m.second.second) == cudaSuccess) h->stage_ms[m.first] += ms;
+  }
+  h->marks.clear();
+  h->evnext = 0;
+  cudaGetLastError();
+}
+
+#define CK(call, where)                                  \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return cuda_fail(h, _e, where); \
+  } while (0)
+
+int ensure(nbs_ctx* h, DevBuf& b, size_t bytes, const char* what) {
+  if (b.bytes >= bytes && b.p) return NBS_OK;
+  if (b.p) {
+    cudaStreamSynchronize(h->st);
+    dev_free(b.p, h->free_fn, h->free_user);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  b.p = dev_alloc(bytes);
+  if (!b.p) return fail(h, NBS_ENOMEM, std::string("cannot allocate ") + std::to_string(bytes) + " bytes for " + what);
+  b.bytes = bytes;
+  return NBS_OK;
+}
+
+size_t csize(int mode) { return mode == NBS_FP32 ? sizeof(float2) : sizeof(double2); }
+
+int upload_tables(nbs_ctx* h) {
+  const Plan& P = h->plan;
+  int rc;
+  std::vector<DevTerm> terms(P.terms.size());
+  for (size_t i = 0; i < P.terms.size(); ++i) {
+    const TermHdr& t = P.terms[i];
+    terms[i] = {t.ch, t.K, t.shape, t.n1, t.n2, t.off1, t.off2, 0};
+  }
+  if ((rc = ensure(h, h->d_terms, std::max<size_t>(terms.size(), 1) * sizeof(DevTerm), "terms"))) return rc;
+  if ((rc = ensure(h, h->d_chtb, P.ch_term_begin.size() * sizeof(int), "term ranges"))) return rc;
+  if ((rc = ensure(h, h->d_chnl, std::max<size_t>(P.ch_nl.size(), 1) * sizeof(int), "flavour content"))) return rc;
+  std::vector<int> cells(P.ncells);
+  for (size_t ti = 0; ti < P.types.size(); ++ti) {
+    const BlockType& bt = P.types[ti];
+    for (int c = 0; c < bt.ncell; ++c) cells[bt.cell_off + c] = bt.cells[c] | ((int)ti << 11);
+  }
+  if ((rc = ensure(h, h->d_cells, std::max<size_t>(cells.size(), 1) * sizeof(int), "cells"))) return rc;
+  CK(cudaMemcpyAsync(h->d_terms.p, terms.data(), terms.size() * sizeof(DevTerm), cudaMemcpyHostToDevice, h->st), "upload terms");
+  CK(cudaMemcpyAsync(h->d_chtb.p, P.ch_term_begin.data(), P.ch_term_begin.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload ranges");
+  CK(cudaMemcpyAsync(h->d_chnl.p, P.ch_nl.data(), P.ch_nl.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload nl");
+  CK(cudaMemcpyAsync(h->d_cells.p, cells.data(), cells.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload cells");
+  std::memset(&h->recipes, 0, sizeof(h->recipes));
+  if (P.types.size() > NBS_MAX_TYPES) return fail(h, NBS_EINVAL, "too many block types");
+  for (size_t ti = 0; ti < P.types.size(); ++ti) {
+    const BlockType& bt = P.types[ti];
+    TypeRecipe& r = h->recipes.t[ti];
+    if (bt.terms.size() > NBS_MAX_TYPE_TERMS) return fail(h, NBS_EINVAL, "block type with too many terms");
+    r.nterms = (int)bt.terms.size();
+    r.cell_off = bt.cell_off;
+    r.ncell = bt.ncell;
+    for (size_t k = 0; k < bt.terms.size(); ++k) {
+      r.pat[k] = bt.terms[k].pat;
+      r.arg[k] = bt.terms[k].a[0] | (bt.terms[k].a[1] << 2) | (bt.terms[k].a[2] << 4);
+      r.coef[k] = bt.terms[k].c;
+    }
+  }
+  // gather entries in the arithmetic of the current mode
+  const size_t n1 = P.ent1_cell.size(), n2 = P.ent2_cell.size();
+  if (h->mode == NBS_FP32) {
+    std::vector<Ent<float>> a(n1), b(n2);
+    for (size_t i = 0; i < n1; ++i) a[i] = {P.ent1_cell[i], (float)P.ent1_coef[i]};
+    for (size_t i = 0; i < n2; ++i) b[i] = {P.ent2_cell[i], (float)P.ent2_coef[i]};
+    if ((rc = ensure(h, h->d_e1, std::max<size_t>(n1, 1) * sizeof(Ent<float>), "gathers"))) return rc;
+    if ((rc = ensure(h, h->d_e2, std::max<size_t>(n2, 1) * sizeof(Ent<float>), "gathers"))) return rc;
+    CK(cudaMemcpyAsync(h->d_e1.p, a.data(), n1 * sizeof(Ent<float>), cudaMemcpyHostToDevice, h->st), "upload e1");
+    CK(cudaMemcpyAsync(h->d_e2.p, b.data(), n2 * sizeof(Ent<float>), cudaMemcpyHostToDevice, h->st), "upload e2");
+    CK(cudaStreamSynchronize(h->st), "upload sync");
+  } else {
+    std::vector<Ent<double>> a(n1), b(n2);
+    for (size_t i = 0; i < n1; ++i) { a[i].cell = P.ent1_cell[i]; a[i].pad = 0; a[i].coef = P.ent1_coef[i]; }
+    for (size_t i = 0; i < n2; ++i) { b[i].cell = P.ent2_cell[i]; b[i].pad = 0; b[i].coef = P.ent2_coef[i]; }
+    if ((rc = ensure(h, h->d_e1, std::max<size_t>(n1, 1) * sizeof(Ent<double>), "gathers"))) return rc;
+    if ((rc = ensure(h, h->d_e2, std::max<size_t>(n2, 1) * sizeof(Ent<double>), "gathers"))) return rc;
+    CK(cudaMemcpyAsync(h->d_e1.p, a.data(), n1 * sizeof(Ent<double>), cudaMemcpyHostToDevice, h->st), "upload e1");
+    CK(cudaMemcpyAsync(h->d_e2.p, b.data(), n2 * sizeof(Ent<double>), cudaMemcpyHostToDevice, h->st), "upload e2");
+    CK(cudaStreamSynchronize(h->st), "upload sync");
+  }
+  h->tables_mode = h->mode;
+  return NBS_OK;
+}
+
+int ensure_plan(nbs_ctx* h, const std::vector<int>& ids) {
+  if (h->plan_ok && h->plan_ids == ids) {
+    if (h->tables_mode != h->mode) return upload_tables(h);
+    return NBS_OK;
+  }
+  std::string e = compile_plan(ids, h->plan);
+  if (!e.empty()) {
+    h->plan_ok = false;
+    return fail(h, NBS_EINVAL, e);
+  }
+  h->plan_ids = ids;
+  h->plan_ok = true;
+  ++h->plan_gen;
+  return upload_tables(h);
+}
+
+std::vector<int> all_channels() {
+  std::vector<int> ids(channel_table().size());
+  for (size_t i = 0; i < ids.size(); ++i) ids[i] = (int)i;
+  return ids;
+}
+
+template <typename T>
+int build_blocks(nbs_ctx* h, int t) {
+  const int V = h->V;
+  const Plan& P = h->plan;
+  int rc;
+  if ((rc = ensure(h, h->propsT, 2ull * 144 * V * sizeof(C<T>), "scaled propagators"))) return rc;
+  if ((rc = ensure(h, h->Q, 6ull * 144 * V * sizeof(C<T>), "diquarks"))) return rc;
+  if ((rc = ensure(h, h->FB, 4ull * P.ncells * V * sizeof(C<T>), "baryon blocks"))) return rc;
+  const char* base = (const char*)h->props.p + (size_t)t * 2 * V * 144 * sizeof(double2);
+  const void* u = base;
+  const void* s = base + (size_t)V * 144 * sizeof(double2);
+  const int c64 = h->have[t] == NBS_C64;
+  cudaEvent_t e0 = stage_begin(h);
+  CK(cudaMemsetAsync(h->small.p, 0, 64, h->st), "clear scale scratch");
+  CK(launch_props_maxabs(u, s, c64, V, h->maxbits, h->flags, h->st), "max|S|");
+  CK(launch_props_scale<T>(u, s, c64, V, h->maxbits, h->exps, (C<T>*)h->propsT.p, h->st), "rescale");
+  stage_end(h, 0, e0);
+  cudaEvent_t e1 = stage_begin(h);
+  CK(launch_diquarks<T>((const C<T>*)h->propsT.p, V, (C<T>*)h->Q.p, h->st), "diquarks");
+  CK(launch_field_blocks<T>((const C<T>*)h->propsT.p, (const C<T>*)h->Q.p, (const int*)h->d_cells.p, P.ncells,
+                            h->recipes, V, (C<T>*)h->FB.p, h->st),
+     "field blocks");
+  stage_end(h, 1, e1);
+  cudaEvent_t e2 = stage_begin(h);
+  CK(fft3d_blocks<T>((C<T>*)h->FB.p, P.ncells, h->L, h->st), "forward FFT");
+  stage_end(h, 2, e2);
+  h->launches += 4 + (h->L > 1 ? 3 : 0);
+  CK(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->st), "flags");
+  h->blocks_t = t;
+  h->blocks_mode = h->mode;
+  h->blocks_gen = h->plan_gen;
+  return NBS_OK;
+}
+
+template <typename T>
+int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
+  const int V = h->V;
+  const long long nt = t1 - t0;
+  int rc;
+  if ((rc = ensure(h, h->Ft, (size_t)nch * 64 * V * sizeof(C<T>), "momentum-space correlators"))) return rc;
+  if ((rc = ensure(h, h->zm, (size_t)nch * 64 * sizeof(C<T>), "zero momentum"))) return rc;
+  const size_t per_t = (size_t)nch * 64 * V * sizeof(double2);
+  if (!on_dev) {
+    for (int b = 0; b < 2; ++b)
+      if ((rc = ensure(h, h->stage[b], per_t, "output staging"))) return rc;
+  }
+  for (int t = t0; t < t1; ++t) {
+    if (h->have[t] < 0) return fail(h, NBS_ESTATE, "no propagators loaded for timeslice " + std::to_string(t));
+    if (!(h->blocks_t == t && h->blocks_mode == h->mode && h->blocks_gen == h->plan_gen)) {
+      if ((rc = build_blocks<T>(h, t))) return rc;
+    }
+    cudaEvent_t e3 = stage_begin(h);
+    CK(launch_contract<T>((const C<T>*)h->FB.p, h->L, (const DevTerm*)h->d_terms.p, (const int*)h->d_chtb.p, nch,
+                          (const Ent<T>*)h->d_e1.p, (const Ent<T>*)h->d_e2.p, (C<T>*)h->Ft.p, h->contract_cfg, h->st),
+       "contraction");
+    stage_end(h, 3, e3);
+    h->launches += 1 + (h->L > 1 ? 3 : 0) + 1;
+    if (t == t1 - 1) {
+      // F~(q = 0) of every (channel, spin) before the inverse transform
+      CK(cudaMemcpy2DAsync(h->zm.p, sizeof(C<T>), h->Ft.p, (size_t)V * sizeof(C<T>), sizeof(C<T>), (size_t)nch * 64,
+                           cudaMemcpyDeviceToDevice, h->st),
+         "zero momentum");
+    }
+    cudaEvent_t e4 = stage_begin(h);
+    CK(fft3d_inverse<T>((C<T>*)h->Ft.p, (long long)nch * 64, h->L, h->st), "inverse FFT");
+    stage_end(h, 4, e4);
+    cudaEvent_t e5 = stage_begin(h);
+    const long long tt = t - t0;
+    if (on_dev) {
+      double2* o = (double2*)out + tt * 64 * V;
+      CK(launch_restore<T>((const C<T>*)h->Ft.p, V, nch, (const int*)h->d_chnl.p, h->exps, o, nt * 64 * V, h->st),
+         "restore");
+    } else {
+      const int b = (int)(tt & 1);
+      if (tt >= 2) CK(cudaStreamWaitEvent(h->st, h->ev_done[b], 0), "wait staging");
+      CK(launch_restore<T>((const C<T>*)h->Ft.p, V, nch, (const int*)h->d_chnl.p, h->exps, (double2*)h->stage[b].p,
+                           64LL * V, h->st),
+         "restore");
+      CK(cudaEventRecord(h->ev_ready[b], h->st), "event");
+      CK(cudaStreamWaitEvent(h->cst, h->ev_ready[b], 0), "wait restore");
+      char* dst = (char*)out + tt * 64 * V * sizeof(double2);
+      CK(cudaMemcpy2DAsync(dst, (size_t)nt * 64 * V * sizeof(double2), h->stage[b].p, 64 * V * sizeof(double2),
+                           64 * V * sizeof(double2), nch, cudaMemcpyDeviceToHost, h->cst),
+         "copy out");
+      CK(cudaEventRecord(h->ev_done[b], h->cst), "event");
+    }
+    stage_end(h, 5, e5);
+  }
+  if (!on_dev) CK(cudaStreamSynchronize(h->cst), "copy sync");
+  CK(cudaStreamSynchronize(h->st), "sync");
+  prof_resolve(h);
+  if (*h->host_flags) return fail(h, NBS_ENAN, "non-finite value in the propagators");
+  h->last_nch = nch;
+  return NBS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nbs_set_allocator(nbs_alloc_fn alloc, nbs_free_fn free_fn, void* user) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return fail(nullptr, NBS_EINVAL, "allocator needs both functions");
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_user = user;
+  return NBS_OK;
+}
+
+int nbs_create(nbs_ctx** out, int L, int T, int flavours) {
+  if (!out) return fail(nullptr, NBS_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (flavours != 2) return fail(nullptr, NBS_EINVAL, "only flavours = 2 (light u = d, strange) is supported");
+  if (L < 1 || L > 64 || !fft_supported(L))
+    return fail(nullptr, NBS_EINVAL, "L must be one of 1 2 3 4 6 8 12 16 24 32 48");
+  if (T < 1 || T > 4096) return fail(nullptr, NBS_EINVAL, "T must be in [1, 4096]");
+  nbs_ctx* h = new nbs_ctx();
+  h->L = L;
+  h->T = T;
+  h->V = L * L * L;
+  h->free_fn = g_free;
+  h->free_user = g_alloc_user;
+  h->have.assign(T, -1);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "cudaGetDevice"); }
+  if ((e = fft_init()) != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "FFT twiddles"); }
+  if ((e = cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking)) != cudaSuccess) {
+    delete h;
+    return cuda_fail(nullptr, e, "copy stream");
+  }
+  for (int b = 0; b < 2; ++b) {
+    cudaEventCreateWithFlags(&h->ev_done[b], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&h->ev_ready[b], cudaEventDisableTiming);
+  }
+  if (cudaMallocHost(&h->host_flags, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    nbs_destroy(h);
+    return fail(nullptr, NBS_ENOMEM, "pinned flag");
+  }
+  *h->host_flags = 0;
+  int rc = ensure(h, h->props, (size_t)T * 2 * h->V * 144 * sizeof(double2), "propagator store");
+  if (!rc) rc = ensure(h, h->small, 256, "scale scratch");
+  if (rc) {
+    std::string m = h->err;
+    nbs_destroy(h);
+    return fail(nullptr, rc, m);
+  }
+  h->maxbits = (unsigned long long*)h->small.p;
+  h->flags = (int*)((char*)h->small.p + 16);
+  h->exps = (int*)((char*)h->small.p + 64);
+  *out = h;
+  return NBS_OK;
+}
+
+int nbs_destroy(nbs_ctx* h) {
+  if (!h) return NBS_OK;
+  cudaStreamSynchronize(h->st);
+  if (h->cst) cudaStreamSynchronize(h->cst);
+  DevBuf* bufs[] = {&h->props, &h->propsT, &h->Q, &h->FB, &h->Ft, &h->zm, &h->small, &h->stage[0], &h->stage[1],
+                    &h->d_terms, &h->d_chtb, &h->d_chnl, &h->d_e1, &h->d_e2, &h->d_cells};
+  for (DevBuf* b : bufs) dev_free(b->p, h->free_fn, h->free_user);
+  for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+  for (int b = 0; b < 2; ++b) {
+    if (h->ev_done[b]) cudaEventDestroy(h->ev_done[b]);
+    if (h->ev_ready[b]) cudaEventDestroy(h->ev_ready[b]);
+  }
+  if (h->cst) cudaStreamDestroy(h->cst);
+  if (h->host_flags) cudaFreeHost(h->host_flags);
+  delete h;
+  return NBS_OK;
+}
+
+int nbs_set_precision(nbs_ctx* h, int mode) {
+  if (!h) return fail(nullptr, NBS_EINVAL, "null context");
+  if (mode != NBS_FP64 && mode != NBS_FP32) return fail(h, NBS_EINVAL, "unknown precision mode");
+  h->mode = mode;
+  return NBS_OK;
+}
+
+int nbs_set_stream(nbs_ctx* h, void* stream) {
+  if (!h) return fail(nullptr, NBS_EINVAL, "null context");
+  h->st = (cudaStream_t)stream;
+  return NBS_OK;
+}
+
+int nbs_load_props(nbs_ctx* h, const void* u, const void* s, int t, int dtype, int on_device) {
+  if (!h) return fail(nullptr, NBS_EINVAL, "null context");
+  if (!u || !s) return fail(h, NBS_EINVAL, "null propagator pointer");
+  if (t < 0 || t >= h->T) return fail(h, NBS_EINVAL, "timeslice out of range");
+  if (dtype != NBS_C128 && dtype != NBS_C64) return fail(h, NBS_EINVAL, "dtype must be NBS_C128 or NBS_C64");
+  const size_t bytes = (size_t)h->V * 144 * (dtype == NBS_C128 ? sizeof(double2) : sizeof(float2));
+  char* base = (char*)h->props.p + (size_t)t * 2 * h->V * 144 * sizeof(double2);
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(base, u, bytes, k, h->st), "copy u");
+  CK(cudaMemcpyAsync(base + (size_t)h->V * 144 * sizeof(double2), s, bytes, k, h->st), "copy s");
+  h->have[t] = (signed char)dtype;
+  if (h->blocks_t == t) h->blocks_t = -1;
+  return NBS_OK;
+}
+
+int nbs_blocks(nbs_ctx* h, int t) {
+  if (!h) return fail(nullptr, NBS_EINVAL, "null context");
+  if (t < 0 || t >= h->T) return fail(h, NBS_EINVAL, "timeslice out of range");
+  if (h->have[t] < 0) return fail(h, NBS_ESTATE, "no propagators loaded for timeslice " + std::to_string(t));
+  int rc;
+  if (!h->plan_ok && (rc = ensure_plan(h, all_channels()))) return rc;
+  if (h->tables_mode != h->mode && (rc = upload_tables(h))) return rc;
+  rc = h->mode == NBS_FP32 ? build_blocks<float>(h, t) : build_blocks<double>(h, t);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(h->st), "sync");
+  prof_resolve(h);
+  if (*h->host_flags) return fail(h, NBS_ENAN, "non-finite value in the propagators");
+  return NBS_OK;
+}
+
+int nbs_correlate(nbs_ctx* h, const int* channel_ids, int n_channels, int t_begin, int t_end, void* out,
+                  int out_on_device) {
+  if (!h) return fail(nullptr, NBS_EINVAL, "null context");
+  if (!channel_ids || n_channels < 1 || n_channels > 65535) return fail(h, NBS_EINVAL, "bad channel list");
+  if (t_begin < 0 || t_end > h->T || t_begin >= t_end) return fail(h, NBS_EINVAL, "bad timeslice range");
+  if (!out) return fail(h, NBS_EINVAL, "null output");
+  std::vector<int> ids(channel_ids, channel_ids + n_channels);
+  int rc = ensure_plan(h, ids);
+  if (rc) return rc;
+  return h->mode == NBS_FP32 ? correlate<float>(h, n_channels, t_begin, t_end, out, out_on_device)
+                             : correlate<double>(h, n_channels, t_begin, t_end, out, out_on_device);
+}
+
+int nbs_set_param(nbs_ctx* h, int param, int value) {
+  if (!h) return fail(nullptr, NBS_EINVAL, "null context");
+  switch (param) {
+    case NBS_PARAM_CONTRACT_CFG: {
+      const int a = value / 10, w = value % 10;
+      if (value != 0 && !((a == 1 || a == 2 || a == 4) && (w == 1 || w == 2 || w == 4)))
+        return fail(h, NBS_EINVAL, "contraction config must be 0 or A*10+W with A, W in {1, 2, 4}");
+      h->contract_cfg = value;
+      return NBS_OK;
+    }
+    default: return fail(h, NBS_EINVAL, "unknown parameter");
+  }
+}
+
+int nbs_set_profiling(nbs_ctx* h, int on) {
+  if (!h) return fail(nullptr, NBS_EINVAL, "null context");
+  h->prof = on != 0;
+  for (double& v : h->stage_ms) v = 0;
+  h->launches = 0;
+  return NBS_OK;
+}
+
+int nbs_profile(nbs_ctx* h, double* stage_ms, long long* launches) {
+  if (!h) return fail(nullptr, NBS_EINVAL, "null context");
+  if (stage_ms)
+    for (int i = 0; i < NBS_NSTAGES; ++i) stage_ms[i] = h->stage_ms[i];
+  if (launches) *launches = h->launches;
+  return NBS_OK;
+}
+
+int nbs_zero_momentum(nbs_ctx* h, double* out) {
+  if (!h || !out) return fail(h, NBS_EINVAL, "null argument");
+  if (h->last_nch == 0) return fail(h, NBS_ESTATE, "no correlator computed yet");
+  const int n = h->last_nch * 64;
+  std::vector<double> tmp(2 * n);
+  if (h->mode == NBS_FP32) {
+    std::vector<float2> f(n);
+    CK(cudaMemcpy(f.data(), h->zm.p, n * sizeof(float2), cudaMemcpyDeviceToHost), "zero momentum");
+    for (int i = 0; i < n; ++i) { tmp[2 * i] = f[i].x; tmp[2 * i + 1] = f[i].y; }
+  } else {
+    CK(cudaMemcpy(tmp.data(), h->zm.p, n * sizeof(double2), cudaMemcpyDeviceToHost), "zero momentum");
+  }
+  int e[2];
+  CK(cudaMemcpy(e, h->exps, sizeof(e), cudaMemcpyDeviceToHost), "exponents");
+  for (int c = 0; c < h->last_nch; ++c) {
+    const int nl = h->plan.ch_nl[c];
+    const double sc = std::ldexp(1.0, e[0] * nl + e[1] * (6 - nl));
+    for (int k = 0; k < 128; ++k) out[c * 128 + k] = tmp[c * 128 + k] * sc;
+  }
+  return NBS_OK;
+}
+
+int nbs_channel_count(void) { return (int)channel_table().size(); }
+
+int nbs_channel_info(int id, char* buf, int len) {
+  const auto& tab = channel_table();
+  if (id < 0 || id >= (int)tab.size()) return fail(nullptr, NBS_EINVAL, "channel id out of range");
+  const ChannelDef& c = tab[id];
+  std::string s = std::string(field_name(c.b[0])) + " " + field_name(c.b[1]) + " | " + field_name(c.b[2]) + " " +
+                  field_name(c.b[3]);
+  if (buf && len > 0) {
+    std::strncpy(buf, s.c_str(), (size_t)len - 1);
+    buf[len - 1] = 0;
+  }
+  int nl = 0;
+  for (int b = 0; b < 2; ++b)
+    for (const Mono& m : {field_monomials(c.b[b])[0]})
+      for (int k = 0; k < 3; ++k) nl += m.q[k] != FS;
+  return nl;
+}
+
+const char* nbs_last_error(const nbs_ctx* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+int nbs_plan_create(nbs_plan** out, const int* channel_ids, int n_channels) {
+  if (!out || !channel_ids || n_channels < 1) return fail(nullptr, NBS_EINVAL, "bad arguments");
+  nbs_plan* p = new nbs_plan();
+  std::string e = compile_plan(std::vector<int>(channel_ids, channel_ids + n_channels), p->plan);
+  if (!e.empty()) {
+    delete p;
+    *out = nullptr;
+    return fail(nullptr, NBS_EINVAL, e);
+  }
+  *out = p;
+  return NBS_OK;
+}
+
+int nbs_plan_destroy(nbs_plan* p) {
+  delete p;
+  return NBS_OK;
+}
+
+int nbs_plan_sizes(const nbs_plan* p, long long* s) {
+  if (!p || !s) return fail(nullptr, NBS_EINVAL, "bad arguments");
+  const Plan& P = p->plan;
+  long long nterm = 0;
+  for (auto& t : P.types) nterm += (long long)t.terms.size();
+  s[NBS_PS_NTYPES] = (long long)P.types.size();
+  s[NBS_PS_NCELLS] = P.ncells;
+  s[NBS_PS_NTYPETERMS] = nterm;
+  s[NBS_PS_NTERMS] = (long long)P.terms.size();
+  s[NBS_PS_NENT1] = (long long)P.ent1_cell.size();
+  s[NBS_PS_NENT2] = (long long)P.ent2_cell.size();
+  s[NBS_PS_NCH] = (long long)P.channels.size();
+  return NBS_OK;
+}
+
+int nbs_plan_export(const nbs_plan* p, int what, void* dst) {
+  if (!p || !dst) return fail(nullptr, NBS_EINVAL, "bad arguments");
+  const Plan& P = p->plan;
+  int* I = (int*)dst;
+  double* D = (double*)dst;
+  switch (what) {
+    case NBS_PX_TYPES: {
+      int toff = 0;
+      for (auto& t : P.types) {
+        *I++ = t.cell_off; *I++ = t.ncell; *I++ = toff; *I++ = (int)t.terms.size();
+        toff += (int)t.terms.size();
+      }
+      return NBS_OK;
+    }
+    case NBS_PX_TYPETERMS:
+      for (auto& t : P.types)
+        for (auto& tt : t.terms) { *I++ = tt.pat; *I++ = tt.a[0]; *I++ = tt.a[1]; *I++ = tt.a[2]; }
+      return NBS_OK;
+    case NBS_PX_TYPECOEF:
+      for (auto& t : P.types)
+        for (auto& tt : t.terms) *D++ = tt.c;
+      return NBS_OK;
+    case NBS_PX_CELLS:
+      for (auto& t : P.types)
+        for (int c : t.cells) *I++ = c;
+      return NBS_OK;
+    case NBS_PX_TERMS:
+      for (auto& t : P.terms) {
+        *I++ = t.ch; *I++ = t.K; *I++ = t.shape; *I++ = t.n1; *I++ = t.n2; *I++ = t.off1; *I++ = t.off2; *I++ = 0;
+      }
+      return NBS_OK;
+    case NBS_PX_ENT1_CELL: std::memcpy(I, P.ent1_cell.data(), P.ent1_cell.size() * sizeof(int)); return NBS_OK;
+    case NBS_PX_ENT1_COEF: std::memcpy(D, P.ent1_coef.data(), P.ent1_coef.size() * sizeof(double)); return NBS_OK;
+    case NBS_PX_ENT2_CELL: std::memcpy(I, P.ent2_cell.data(), P.ent2_cell.size() * sizeof(int)); return NBS_OK;
+    case NBS_PX_ENT2_COEF: std::memcpy(D, P.ent2_coef.data(), P.ent2_coef.size() * sizeof(double)); return NBS_OK;
+    case NBS_PX_CHANNELS:
+      for (size_t c = 0; c < P.channels.size(); ++c) {
+        *I++ = P.ch_term_begin[c]; *I++ = P.ch_term_begin[c + 1]; *I++ = P.ch_nl[c]; *I++ = 6 - P.ch_nl[c];
+      }
+      return NBS_OK;
+    default: return fail(nullptr, NBS_EINVAL, "unknown export");
+  }
+}
+
+}  // extern "C"

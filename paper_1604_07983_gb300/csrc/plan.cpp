@@ -1,0 +1,490 @@
+// plan.cpp -- host channel compiler (Sec. 4 (ii)-(iii) of arXiv:1604.07983).
+//
+// For every requested channel <B1 B2 | B3bar B4bar> it enumerates the Wick
+// contractions of Eq. (2.4) grouped into the effective-block terms of
+// Eq. (2.7), and packs, per term, the gathers that build the two effective
+// blocks in momentum space from the stored baryon blocks.
+//
+// Stored blocks ("field blocks").  For a sink field B with flavour content
+// sorted as u < d < s ("canonical positions" 0, 1, 2) the device stores
+//
+//   FB^B_alpha(x; y0, y1, y2) = sum_{monomials m} c_m sum_tau sign(tau)
+//                                 N^m_alpha(x; y_tau(1), y_tau(2), y_tau(3)),
+//
+// tau assigning sink quark k of m to the canonical position of its flavour,
+// N^m the normal block of Eq. (4.1).  With u = d (the isospin limit of
+// Sec. 4 (i)) n shares p's storage, Sigma- shares Sigma+'s and Xi- shares
+// Xi0's, up to an argument permutation and a sign found by comparing the
+// symbolic expansions; two positions of equal flavour make FB antisymmetric
+// (or, for Lambda / Sigma0 under u <-> d, symmetric), and such pairs are
+// stored once.
+//
+// Effective blocks.  For source monomials (m3, m4) and the set S of source
+// slots feeding B1, every permutation with P({1,2,3}) = S has sign
+// sign(P0_S) sign(tau1) sign(tau2), so the B1 side of the term is
+// sign(rho) FB^{B1}(source indices of S in canonical order), rho the
+// flavour-preserving map from canonical positions to the sorted slots of S.
+// The source tensor eps eps (Cg5)(Cg5) delta delta is split: each source
+// baryon's eps and Cg5 go to the side holding two or three of its slots, its
+// projector to the side of its third slot; indices of one side's slots that
+// appear in a factor of the other side are the shared indices xi~ (Sec. 4
+// (ii); for <p Lambda | p Xu> they are the six sets the paper lists).
+#include "plan.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+#include <sstream>
+
+namespace nbs {
+
+namespace {
+
+const double kR6 = 1.0 / std::sqrt(6.0);
+const double kR2 = 1.0 / std::sqrt(2.0);
+
+// C gamma5 in the Dirac representation (C = gamma4 gamma2)
+const int kCG5[4][4] = {{0, 1, 0, 0}, {-1, 0, 0, 0}, {0, 0, 0, 1}, {0, 0, -1, 0}};
+
+int eps3(int a, int b, int c) {
+  if (a == b || b == c || a == c) return 0;
+  // (a, b, c) is a permutation of (0, 1, 2)
+  int inv = (a > b) + (a > c) + (b > c);
+  return (inv & 1) ? -1 : 1;
+}
+
+int perm_sign(const int* p, int n) {
+  int inv = 0;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) inv += p[i] > p[j];
+  return (inv & 1) ? -1 : 1;
+}
+
+const int kPerm3[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+using RKey = std::array<int, 4>;  // pattern, a0, a1, a2
+using Recipe = std::map<RKey, double>;
+
+int lflav(int q) { return q == FS ? 1 : 0; }
+
+bool add_term(Recipe& R, int f0, int f1, int f2, int a0, int a1, int a2, double c) {
+  // N^{f0 f1 f2}(j_a0, j_a1, j_a2) = N^{f1 f0 f2}(j_a1, j_a0, j_a2)  (eps and Cg5 both antisymmetric)
+  if (f0 > f1) { std::swap(f0, f1); std::swap(a0, a1); }
+  int pat;
+  if (f0 == 0 && f1 == 0) pat = f2 ? LLS : LLL;
+  else if (f0 == 0 && f1 == 1) pat = f2 ? LSS : LSL;
+  else return false;  // two strange quarks in the diquark: not an octet field
+  if ((pat == LLL || pat == LLS) && a0 > a1) std::swap(a0, a1);
+  R[{pat, a0, a1, a2}] += c;
+  return true;
+}
+
+void prune(Recipe& R) {
+  for (auto it = R.begin(); it != R.end();) {
+    if (std::fabs(it->second) < 1e-13) it = R.erase(it); else ++it;
+  }
+}
+
+// R o pi : j -> FB(j_pi(0), j_pi(1), j_pi(2))
+Recipe compose(const Recipe& R, const int* pi) {
+  Recipe out;
+  for (auto& kv : R) {
+    int pat = kv.first[0];
+    int a0 = pi[kv.first[1]], a1 = pi[kv.first[2]], a2 = pi[kv.first[3]];
+    if ((pat == LLL || pat == LLS) && a0 > a1) std::swap(a0, a1);
+    out[{pat, a0, a1, a2}] += kv.second;
+  }
+  prune(out);
+  return out;
+}
+
+bool equal_scaled(const Recipe& A, const Recipe& B, double s) {
+  if (A.size() != B.size()) return false;
+  for (auto& kv : A) {
+    auto it = B.find(kv.first);
+    if (it == B.end() || std::fabs(kv.second - s * it->second) > 1e-12) return false;
+  }
+  return true;
+}
+
+void canonical_flavours(int field, int cf[3]) {
+  const Mono& m = field_monomials(field)[0];
+  int q[3] = {m.q[0], m.q[1], m.q[2]};
+  std::sort(q, q + 3);
+  cf[0] = q[0]; cf[1] = q[1]; cf[2] = q[2];
+}
+
+bool field_recipe(int field, Recipe& R) {
+  int cf[3];
+  canonical_flavours(field, cf);
+  for (const Mono& m : field_monomials(field)) {
+    for (auto& tau : kPerm3) {
+      if (m.q[0] != cf[tau[0]] || m.q[1] != cf[tau[1]] || m.q[2] != cf[tau[2]]) continue;
+      double c = m.c * perm_sign(tau, 3);
+      if (!add_term(R, lflav(m.q[0]), lflav(m.q[1]), lflav(m.q[2]), tau[0], tau[1], tau[2], c))
+        return false;
+    }
+  }
+  prune(R);
+  return true;
+}
+
+struct FieldMap { int type = -1; int pi[3] = {0, 1, 2}; double sign = 1; };
+
+struct TypeBuild {
+  Recipe R;
+  BlockType bt;
+  // (y0 + 12 y1 + 144 y2) -> cell (or -1 when identically zero), sign
+  std::vector<int> cell_of;
+  std::vector<signed char> sign_of;
+};
+
+void layout_type(TypeBuild& T) {
+  BlockType& bt = T.bt;
+  T.cell_of.assign(1728, -1);
+  T.sign_of.assign(1728, 0);
+  bt.cells.clear();
+  if (bt.pack_sym == 0) {
+    for (int y0 = 0; y0 < 12; ++y0)
+      for (int y1 = 0; y1 < 12; ++y1)
+        for (int y2 = 0; y2 < 12; ++y2) {
+          int key = y0 + 12 * y1 + 144 * y2;
+          T.cell_of[key] = (int)bt.cells.size();
+          T.sign_of[key] = 1;
+          bt.cells.push_back(key);
+        }
+  } else {
+    int p = bt.pack_p, q = bt.pack_q, r = bt.pack_r;
+    for (int a = 0; a < 12; ++a)
+      for (int b = (bt.pack_sym > 0 ? a : a + 1); b < 12; ++b)
+        for (int c = 0; c < 12; ++c) {
+          int y[3];
+          y[p] = a; y[q] = b; y[r] = c;
+          int key = y[0] + 12 * y[1] + 144 * y[2];
+          int cell = (int)bt.cells.size();
+          bt.cells.push_back(key);
+          T.cell_of[key] = cell;
+          T.sign_of[key] = 1;
+          if (a != b) {  // the mirrored pair
+            int z[3];
+            z[p] = b; z[q] = a; z[r] = c;
+            int k2 = z[0] + 12 * z[1] + 144 * z[2];
+            T.cell_of[k2] = cell;
+            T.sign_of[k2] = (signed char)bt.pack_sym;
+          }
+        }
+  }
+  bt.ncell = (int)bt.cells.size();
+}
+
+}  // namespace
+
+const char* field_name(int f) {
+  static const char* names[NFIELDS] = {"p", "n", "Sigma+", "Sigma0", "Sigma-", "Xi0",
+                                       "Xi-", "Lambda", "Xu", "Xd", "Xs"};
+  return (f >= 0 && f < NFIELDS) ? names[f] : "?";
+}
+
+// Eqs. (2.2), (2.3): eps_abc (q1_a C gamma5 q2_b) q3_c with coefficients
+const std::vector<Mono>& field_monomials(int f) {
+  static const std::vector<std::vector<Mono>> table = {
+      /* p      */ {{+1.0, {FU, FD, FU}}},
+      /* n      */ {{-1.0, {FU, FD, FD}}},
+      /* Sigma+ */ {{-1.0, {FU, FS, FU}}},
+      /* Sigma0 */ {{kR2, {FD, FS, FU}}, {-kR2, {FS, FU, FD}}},
+      /* Sigma- */ {{-1.0, {FD, FS, FD}}},
+      /* Xi0    */ {{+1.0, {FU, FS, FS}}},
+      /* Xi-    */ {{-1.0, {FD, FS, FS}}},
+      /* Lambda */ {{kR6, {FD, FS, FU}}, {kR6, {FS, FU, FD}}, {-2.0 * kR6, {FU, FD, FS}}},
+      /* Xu     */ {{1.0, {FD, FS, FU}}},
+      /* Xd     */ {{1.0, {FS, FU, FD}}},
+      /* Xs     */ {{1.0, {FU, FD, FS}}},
+  };
+  return table[f];
+}
+
+// Octet-octet channel list, reconstructed from the paper's "52 channels from
+// NN to Xi Xi" (Sec. 1, Sec. 4 (iii)): in each strangeness sector the
+// particle-basis sink pairs of minimal |I3| (zero total charge, +1 for
+// S = -1), with every sink pair of the sector as a source (1+9+36+9+1 = 56),
+// minus the four channels that vanish identically for u = d: a channel that
+// is its own image under u <-> d with an odd sign (Lambda -> -Lambda,
+// Sigma0 -> Sigma0), i.e. LL|LS0, LS0|LL, LS0|S0S0, S0S0|LS0.  52 remain.
+const std::vector<ChannelDef>& channel_table() {
+  static const std::vector<ChannelDef> table = [] {
+    const std::vector<std::vector<std::pair<int, int>>> sectors = {
+        {{P, N}},
+        {{P, LAM}, {P, SIG0}, {N, SIGP}},
+        {{P, XIM}, {N, XI0}, {LAM, LAM}, {LAM, SIG0}, {SIGP, SIGM}, {SIG0, SIG0}},
+        {{LAM, XI0}, {SIGP, XIM}, {SIG0, XI0}},
+        {{XI0, XIM}},
+    };
+    // u <-> d image of each field and its sign (Eqs. (2.2)-(2.3))
+    const int img[NFIELDS] = {N, P, SIGM, SIG0, SIGP, XIM, XI0, LAM, XD, XU, XS};
+    const int sgn[NFIELDS] = {1, 1, 1, 1, 1, -1, -1, -1, -1, -1, -1};
+    std::vector<ChannelDef> t;
+    for (auto& sec : sectors)
+      for (auto& snk : sec)
+        for (auto& src : sec) {
+          ChannelDef c{{snk.first, snk.second, src.first, src.second}};
+          bool self = true;
+          int sign = 1;
+          for (int b = 0; b < 4; ++b) {
+            self = self && img[c.b[b]] == c.b[b];
+            sign *= sgn[c.b[b]];
+          }
+          if (self && sign < 0) continue;  // identically zero in the isospin limit
+          t.push_back(c);
+        }
+    return t;
+  }();
+  return table;
+}
+
+std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
+  plan = Plan();
+  const auto& table = channel_table();
+  for (int id : ids) {
+    if (id < 0 || id >= (int)table.size()) {
+      std::ostringstream os;
+      os << "channel id " << id << " outside [0, " << table.size() << ")";
+      return os.str();
+    }
+  }
+  plan.channels = ids;
+
+  // ---- stored block types over the sink fields in use -----------------------
+  bool used[NFIELDS] = {};
+  for (int id : ids) { used[table[id].b[0]] = used[table[id].b[1]] = true; }
+  std::vector<TypeBuild> types;
+  FieldMap fmap[NFIELDS];
+  for (int f = 0; f < NFIELDS; ++f) {
+    if (!used[f]) continue;
+    Recipe R;
+    if (!field_recipe(f, R)) return std::string("field ") + field_name(f) + " has no block pattern";
+    bool found = false;
+    for (int t = 0; t < (int)types.size() && !found; ++t) {
+      for (auto& pi : kPerm3) {
+        Recipe C = compose(types[t].R, pi);
+        for (double s : {1.0, -1.0}) {
+          if (equal_scaled(R, C, s)) {
+            fmap[f].type = t;
+            std::copy(pi, pi + 3, fmap[f].pi);
+            fmap[f].sign = s;
+            found = true;
+            break;
+          }
+        }
+        if (found) break;
+      }
+    }
+    if (found) continue;
+    TypeBuild T;
+    T.R = R;
+    const int pairs[3][3] = {{0, 1, 2}, {1, 2, 0}, {0, 2, 1}};
+    for (auto& pr : pairs) {
+      int sw[3] = {0, 1, 2};
+      std::swap(sw[pr[0]], sw[pr[1]]);
+      Recipe C = compose(R, sw);
+      int sym = equal_scaled(C, R, 1.0) ? 1 : (equal_scaled(C, R, -1.0) ? -1 : 0);
+      if (sym) {
+        T.bt.pack_p = pr[0]; T.bt.pack_q = pr[1]; T.bt.pack_r = pr[2]; T.bt.pack_sym = sym;
+        break;
+      }
+    }
+    for (auto& kv : R) T.bt.terms.push_back({kv.first[0], {kv.first[1], kv.first[2], kv.first[3]}, kv.second});
+    layout_type(T);
+    fmap[f].type = (int)types.size();
+    types.push_back(std::move(T));
+  }
+  int off = 0;
+  for (auto& T : types) { T.bt.cell_off = off; off += T.bt.ncell; }
+  plan.ncells = off;
+
+  // ---- contraction terms -----------------------------------------------------
+  plan.ch_term_begin.push_back(0);
+  for (int ci = 0; ci < (int)ids.size(); ++ci) {
+    const ChannelDef& ch = table[ids[ci]];
+    const int B1 = ch.b[0], B2 = ch.b[1];
+    int cf1[3], cf2[3];
+    canonical_flavours(B1, cf1);
+    canonical_flavours(B2, cf2);
+    {
+      int nl = 0;
+      for (int k = 0; k < 3; ++k) nl += (cf1[k] != FS) + (cf2[k] != FS);
+      plan.ch_nl.push_back(nl);
+    }
+    for (const Mono& m3 : field_monomials(ch.b[2])) {
+      for (const Mono& m4 : field_monomials(ch.b[3])) {
+        int src[6] = {m3.q[0], m3.q[1], m3.q[2], m4.q[0], m4.q[1], m4.q[2]};
+        const double c34 = m3.c * m4.c;
+        for (int mask = 0; mask < 64; ++mask) {
+          if (__builtin_popcount(mask) != 3) continue;
+          int S[3], Sc[3], ns = 0, nc = 0;
+          for (int k = 0; k < 6; ++k) {
+            if (mask >> k & 1) S[ns++] = k; else Sc[nc++] = k;
+          }
+          // flavour content of S must be B1's, of the complement B2's
+          int fs[3] = {src[S[0]], src[S[1]], src[S[2]]}, fc[3] = {src[Sc[0]], src[Sc[1]], src[Sc[2]]};
+          std::sort(fs, fs + 3);
+          std::sort(fc, fc + 3);
+          if (!std::equal(fs, fs + 3, cf1) || !std::equal(fc, fc + 3, cf2)) continue;
+          int P0[6] = {S[0], S[1], S[2], Sc[0], Sc[1], Sc[2]};
+          const int sign0 = perm_sign(P0, 6);
+          bool on1[6];
+          for (int k = 0; k < 6; ++k) on1[k] = mask >> k & 1;
+          // side of each source baryon's eps / Cg5 (majority) and projector (its third slot)
+          int fside[2], pside[2];
+          for (int b = 0; b < 2; ++b) {
+            int cnt = on1[3 * b] + on1[3 * b + 1] + on1[3 * b + 2];
+            fside[b] = cnt >= 2 ? 1 : 2;
+            pside[b] = on1[3 * b + 2] ? 1 : 2;
+          }
+          // shared indices: (kind 0 = colour / 1 = spin, slot), canonical order
+          std::vector<std::pair<int, int>> xi;
+          for (int b = 0; b < 2; ++b) {
+            for (int k = 3 * b; k < 3 * b + 3; ++k)
+              if ((on1[k] ? 1 : 2) != fside[b]) xi.push_back({0, k});
+            for (int k = 3 * b; k < 3 * b + 2; ++k)
+              if ((on1[k] ? 1 : 2) != fside[b]) xi.push_back({1, k});
+          }
+          std::sort(xi.begin(), xi.end());
+          int K = 1;
+          for (auto& x : xi) K *= x.first == 0 ? 3 : 4;
+          const int shape = (pside[0] == 1 ? 1 : 0) | (pside[1] == 1 ? 2 : 0);
+
+          std::vector<int> cells_side[2];
+          std::vector<double> coef_side[2];
+          int nmax[2] = {0, 0};
+          for (int side = 1; side <= 2; ++side) {
+            const int field = side == 1 ? B1 : B2;
+            const int* cf = side == 1 ? cf1 : cf2;
+            const int* slots = side == 1 ? S : Sc;
+            // rho: canonical position -> index into slots (flavour preserving)
+            int rho[3];
+            bool taken[3] = {};
+            for (int p = 0; p < 3; ++p) {
+              rho[p] = -1;
+              for (int i = 0; i < 3; ++i)
+                if (!taken[i] && src[slots[i]] == cf[p]) { rho[p] = i; taken[i] = true; break; }
+              if (rho[p] < 0) return "internal: no flavour-preserving map";
+            }
+            const double side_coef = perm_sign(rho, 3) * (side == 1 ? sign0 * c34 : 1.0);
+            const FieldMap& fm = fmap[field];
+            const TypeBuild& T = types[fm.type];
+            int nheld = (pside[0] == side) + (pside[1] == side);
+            std::vector<std::vector<std::pair<int, double>>> lists;
+            for (int k = 0; k < K; ++k) {
+              int col[6], spin[6];
+              std::fill(col, col + 6, -1);
+              std::fill(spin, spin + 6, -1);
+              int rem = k;
+              for (int i = (int)xi.size() - 1; i >= 0; --i) {
+                int base = xi[i].first == 0 ? 3 : 4;
+                int v = rem % base;
+                rem /= base;
+                (xi[i].first == 0 ? col : spin)[xi[i].second] = v;
+              }
+              for (int h = 0; h < (1 << nheld); ++h) {
+                int sp[6];
+                std::copy(spin, spin + 6, sp);
+                int bit = 0;
+                for (int b = 0; b < 2; ++b) {
+                  if (pside[b] != side) continue;
+                  sp[3 * b + 2] = (h >> bit) & 1;  // projector: spin of the third slot = alpha_{3/4}
+                  ++bit;
+                }
+                // free indices of this side's slots
+                int fcol[3], nfc = 0, fsp[3], nfs = 0;
+                for (int i = 0; i < 3; ++i) {
+                  if (col[slots[i]] < 0) fcol[nfc++] = slots[i];
+                  if (sp[slots[i]] < 0) fsp[nfs++] = slots[i];
+                }
+                std::map<int, double> acc;
+                int ncc = 1, nsc = 1;
+                for (int i = 0; i < nfc; ++i) ncc *= 3;
+                for (int i = 0; i < nfs; ++i) nsc *= 4;
+                for (int cc = 0; cc < ncc; ++cc) {
+                  int c6[6];
+                  std::copy(col, col + 6, c6);
+                  for (int i = 0, r = cc; i < nfc; ++i, r /= 3) c6[fcol[i]] = r % 3;
+                  double ce = 1;
+                  for (int b = 0; b < 2; ++b)
+                    if (fside[b] == side) ce *= eps3(c6[3 * b], c6[3 * b + 1], c6[3 * b + 2]);
+                  if (ce == 0) continue;
+                  for (int ss = 0; ss < nsc; ++ss) {
+                    int s6[6];
+                    std::copy(sp, sp + 6, s6);
+                    for (int i = 0, r = ss; i < nfs; ++i, r /= 4) s6[fsp[i]] = r % 4;
+                    double cs = 1;
+                    for (int b = 0; b < 2; ++b)
+                      if (fside[b] == side) cs *= kCG5[s6[3 * b]][s6[3 * b + 1]];
+                    if (cs == 0) continue;
+                    // field-block arguments in canonical order
+                    int y[3];
+                    for (int p = 0; p < 3; ++p) {
+                      int sl = slots[rho[p]];
+                      y[p] = 3 * s6[sl] + c6[sl];
+                    }
+                    // FB^field(y) = sign * FB^T(y_pi0, y_pi1, y_pi2)
+                    int yt[3] = {y[fm.pi[0]], y[fm.pi[1]], y[fm.pi[2]]};
+                    int key = yt[0] + 12 * yt[1] + 144 * yt[2];
+                    int cell = T.cell_of[key];
+                    if (cell < 0) continue;
+                    double c = ce * cs * fm.sign * T.sign_of[key] * side_coef;
+                    acc[T.bt.cell_off + cell] += c;
+                  }
+                }
+                std::vector<std::pair<int, double>> lst;
+                for (auto& kv : acc)
+                  if (std::fabs(kv.second) > 1e-13) lst.push_back(kv);
+                nmax[side - 1] = std::max(nmax[side - 1], (int)lst.size());
+                lists.push_back(std::move(lst));
+              }
+            }
+            // entries of step k ordered [i][h], i padded to an even count with zero coefficients
+            nmax[side - 1] += nmax[side - 1] & 1;
+            const int nh = 1 << nheld;
+            for (int k = 0; k < K; ++k)
+              for (int i = 0; i < nmax[side - 1]; ++i)
+                for (int hh = 0; hh < nh; ++hh) {
+                  const auto& lst = lists[k * nh + hh];
+                  if (i < (int)lst.size()) {
+                    cells_side[side - 1].push_back(lst[i].first);
+                    coef_side[side - 1].push_back(lst[i].second);
+                  } else {
+                    cells_side[side - 1].push_back(0);
+                    coef_side[side - 1].push_back(0.0);
+                  }
+                }
+          }
+          if (nmax[0] == 0 || nmax[1] == 0) continue;  // identically zero term
+          TermHdr th;
+          th.ch = ci;
+          th.K = K;
+          th.shape = shape;
+          th.n1 = nmax[0];
+          th.n2 = nmax[1];
+          th.off1 = (int)plan.ent1_cell.size();
+          th.off2 = (int)plan.ent2_cell.size();
+          th.pad = 0;
+          plan.ent1_cell.insert(plan.ent1_cell.end(), cells_side[0].begin(), cells_side[0].end());
+          plan.ent1_coef.insert(plan.ent1_coef.end(), coef_side[0].begin(), coef_side[0].end());
+          plan.ent2_cell.insert(plan.ent2_cell.end(), cells_side[1].begin(), cells_side[1].end());
+          plan.ent2_coef.insert(plan.ent2_coef.end(), coef_side[1].begin(), coef_side[1].end());
+          plan.terms.push_back(th);
+          const int nh1 = 1 << ((shape & 1) + (shape >> 1 & 1));
+          const int nh2 = 4 / nh1;
+          plan.cmac_per_q += 64.0 * K;
+          plan.gathers_per_q += 4.0 * K * (nh1 * th.n1 + nh2 * th.n2);
+        }
+      }
+    }
+    plan.ch_term_begin.push_back((int)plan.terms.size());
+  }
+  for (auto& T : types) plan.types.push_back(T.bt);
+  return "";
+}
+
+}  // namespace nbs

@@ -1,0 +1,52 @@
+// plan.h -- host-side channel compiler: Wick topologies -> gather tables.
+//
+// The classification of the Wick contractions into effective-block terms is
+// done once on the CPU and packed as structures of arrays for the device
+// (Sec. 4 (ii)-(iii) of arXiv:1604.07983).
+#pragma once
+#include <string>
+#include <vector>
+
+namespace nbs {
+
+enum Flavour { FU = 0, FD = 1, FS = 2 };
+enum Field { P = 0, N, SIGP, SIG0, SIGM, XI0, XIM, LAM, XU, XD, XS, NFIELDS };
+// normal-block flavour patterns (u = d = l): q1 q2 q3
+enum Pattern { LLL = 0, LLS = 1, LSL = 2, LSS = 3 };
+
+struct Mono { double c; int q[3]; };
+const std::vector<Mono>& field_monomials(int field);
+const char* field_name(int field);
+
+struct ChannelDef { int b[4]; };           // sink B1 B2, source B3 B4
+const std::vector<ChannelDef>& channel_table();
+
+// One stored block type: FB_T(alpha; y0, y1, y2) = sum_terms c * N^pat_alpha(y_a0, y_a1, y_a2)
+struct TypeTerm { int pat; int a[3]; double c; };
+struct BlockType {
+  std::vector<TypeTerm> terms;
+  int pack_p = -1, pack_q = -1, pack_r = -1;  // packed pair (p, q), third position r
+  int pack_sym = 0;                           // +1 symmetric, -1 antisymmetric, 0 none
+  int ncell = 0, cell_off = 0;
+  std::vector<int> cells;                     // cell -> y0 + 12*y1 + 144*y2
+};
+
+struct TermHdr { int ch, K, shape, n1, n2, off1, off2, pad; };
+
+struct Plan {
+  std::vector<int> channels;                  // built-in ids, in request order
+  std::vector<BlockType> types;
+  int ncells = 0;
+  std::vector<TermHdr> terms;
+  std::vector<int> ent1_cell, ent2_cell;
+  std::vector<double> ent1_coef, ent2_coef;
+  std::vector<int> ch_term_begin;             // size nch + 1
+  std::vector<int> ch_nl;                     // light quarks of the sink pair
+  // flops of the contraction per q (complex multiply-adds), for rooflines
+  double cmac_per_q = 0, gathers_per_q = 0;
+};
+
+// Compile the tables for the given channel ids.  Returns "" or an error text.
+std::string compile_plan(const std::vector<int>& channel_ids, Plan& out);
+
+}  // namespace nbs

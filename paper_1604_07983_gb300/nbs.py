@@ -1,0 +1,255 @@
+"""Thin ctypes binding of the C ABI in include/nbs.h (argument marshalling only).
+
+Every step of the correlator path runs in libnbs.so; this module only turns
+Python/torch objects into pointers and sizes and raises on error codes.  If
+the library is missing, importing the binding raises: there is no fallback.
+PyTorch provides device memory (through the allocator hook) and streams.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnbs.so")
+
+NBS_OK, NBS_EINVAL, NBS_ENOMEM, NBS_ECUDA, NBS_ESTATE, NBS_ETIMEOUT, NBS_ENAN = 0, -1, -2, -3, -4, -5, -6
+NBS_FP64, NBS_FP32 = 0, 1
+NBS_C128, NBS_C64 = 0, 1
+NBS_NSPIN = 64
+ERRORS = {NBS_EINVAL: "EINVAL", NBS_ENOMEM: "ENOMEM", NBS_ECUDA: "ECUDA", NBS_ESTATE: "ESTATE",
+          NBS_ETIMEOUT: "ETIMEOUT", NBS_ENAN: "ENAN"}
+
+#: every symbol include/nbs.h declares
+EXPORTS = ["nbs_set_allocator", "nbs_create", "nbs_destroy", "nbs_set_precision", "nbs_set_stream",
+           "nbs_load_props", "nbs_blocks", "nbs_correlate", "nbs_zero_momentum", "nbs_set_param", "nbs_set_profiling",
+           "nbs_profile", "nbs_channel_count",
+           "nbs_channel_info", "nbs_last_error", "nbs_plan_create", "nbs_plan_destroy", "nbs_plan_sizes",
+           "nbs_plan_export"]
+
+
+class NBSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+_lib = None
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def lib():
+    """The loaded libnbs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libnbs.so not built: run python -c 'import __graft_entry__ as g; g.build()'")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+    sig = {
+        "nbs_set_allocator": (i, [ALLOC_FN, FREE_FN, vp]),
+        "nbs_create": (i, [ctypes.POINTER(vp), i, i, i]),
+        "nbs_destroy": (i, [vp]),
+        "nbs_set_precision": (i, [vp, i]),
+        "nbs_set_stream": (i, [vp, vp]),
+        "nbs_load_props": (i, [vp, vp, vp, i, i, i]),
+        "nbs_blocks": (i, [vp, i]),
+        "nbs_correlate": (i, [vp, ctypes.POINTER(i), i, i, i, vp, i]),
+        "nbs_zero_momentum": (i, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "nbs_set_param": (i, [vp, i, i]),
+        "nbs_set_profiling": (i, [vp, i]),
+        "nbs_profile": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ll)]),
+        "nbs_channel_count": (i, []),
+        "nbs_channel_info": (i, [i, ctypes.c_char_p, i]),
+        "nbs_last_error": (ctypes.c_char_p, [vp]),
+        "nbs_plan_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(i), i]),
+        "nbs_plan_destroy": (i, [vp]),
+        "nbs_plan_sizes": (i, [vp, ctypes.POINTER(ll)]),
+        "nbs_plan_export": (i, [vp, i, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc, h=None):
+    if rc != NBS_OK:
+        msg = lib().nbs_last_error(h)
+        raise NBSError(rc, msg.decode() if msg else "")
+    return rc
+
+
+# ---- channel table -----------------------------------------------------------
+
+def channel_count() -> int:
+    return lib().nbs_channel_count()
+
+
+def channel_info(cid: int):
+    """((B1, B2, B3, B4), n_light) of a built-in channel id."""
+    buf = ctypes.create_string_buffer(128)
+    nl = lib().nbs_channel_info(cid, buf, 128)
+    _check(nl if nl < 0 else 0)
+    sink, src = buf.value.decode().split("|")
+    return tuple(sink.split()) + tuple(src.split()), nl
+
+
+def channel_names():
+    return [channel_info(c)[0] for c in range(channel_count())]
+
+
+# ---- host-only plan introspection ---------------------------------------------
+
+PX = dict(TYPES=0, TYPETERMS=1, TYPECOEF=2, CELLS=3, TERMS=4, ENT1_CELL=5, ENT1_COEF=6, ENT2_CELL=7,
+          ENT2_COEF=8, CHANNELS=9)
+
+
+def plan_tables(channel_ids):
+    """Compile the channel tables on the host and return them as numpy arrays."""
+    import numpy as np
+    L = lib()
+    ids = (ctypes.c_int * len(channel_ids))(*channel_ids)
+    p = ctypes.c_void_p()
+    _check(L.nbs_plan_create(ctypes.byref(p), ids, len(channel_ids)))
+    try:
+        s = (ctypes.c_longlong * 7)()
+        _check(L.nbs_plan_sizes(p, s))
+        ntypes, ncells, ntt, nterm, ne1, ne2, nch = list(s)
+
+        def get(what, shape, dtype):
+            a = np.zeros(shape, dtype=dtype)
+            _check(L.nbs_plan_export(p, PX[what], a.ctypes.data_as(ctypes.c_void_p)))
+            return a
+
+        return dict(
+            types=get("TYPES", (ntypes, 4), np.int32), typeterms=get("TYPETERMS", (ntt, 4), np.int32),
+            typecoef=get("TYPECOEF", (ntt,), np.float64), cells=get("CELLS", (ncells,), np.int32),
+            terms=get("TERMS", (nterm, 8), np.int32), ent1_cell=get("ENT1_CELL", (ne1,), np.int32),
+            ent1_coef=get("ENT1_COEF", (ne1,), np.float64), ent2_cell=get("ENT2_CELL", (ne2,), np.int32),
+            ent2_coef=get("ENT2_COEF", (ne2,), np.float64), channels=get("CHANNELS", (nch, 4), np.int32))
+    finally:
+        L.nbs_plan_destroy(p)
+
+
+# ---- torch-backed device allocator -------------------------------------------
+
+_alloc_refs = None
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    global _alloc_refs
+    import torch
+
+    def _a(nbytes, user):
+        try:
+            dev = torch.cuda.current_device()
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev)
+        except Exception:
+            return None
+
+    def _f(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    _alloc_refs = (ALLOC_FN(_a), FREE_FN(_f))
+    _check(lib().nbs_set_allocator(_alloc_refs[0], _alloc_refs[1], None))
+
+
+# ---- context -----------------------------------------------------------------
+
+def _ptr(x):
+    """Device or host address of a torch tensor or numpy array."""
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+class Context:
+    """One L^3 x T lattice on the current CUDA device (nbs_create ... nbs_destroy)."""
+
+    def __init__(self, L: int, T: int, flavours: int = 2, precision: int = NBS_FP64, stream=None):
+        self._lib = lib()
+        h = ctypes.c_void_p()
+        _check(self._lib.nbs_create(ctypes.byref(h), L, T, flavours))
+        self.h = h
+        self.L, self.T, self.V = L, T, L ** 3
+        self.set_precision(precision)
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.nbs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_precision(self, mode: int):
+        _check(self._lib.nbs_set_precision(self.h, mode), self.h)
+
+    def set_stream(self, stream):
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        _check(self._lib.nbs_set_stream(self.h, ctypes.c_void_p(handle)), self.h)
+
+    def load_props(self, u, s, t: int):
+        """u, s: complex128/complex64 [V,12,12] torch tensors (device or host) or numpy arrays (host)."""
+        import numpy as np
+        dt = str(getattr(u, "dtype", ""))
+        c64 = "complex64" in dt
+        on_dev = bool(getattr(u, "is_cuda", False))
+        if not hasattr(u, "data_ptr"):
+            u = np.ascontiguousarray(u)
+            s = np.ascontiguousarray(s)
+        _check(self._lib.nbs_load_props(self.h, _ptr(u), _ptr(s), t, NBS_C64 if c64 else NBS_C128, int(on_dev)),
+               self.h)
+        self._keep = (u, s)
+
+    def blocks(self, t: int):
+        _check(self._lib.nbs_blocks(self.h, t), self.h)
+
+    def correlate(self, channel_ids, t_begin: int, t_end: int, out):
+        """out: complex128 [n_ch, t_end - t_begin, 4, 4, 2, 2, V] (torch device tensor, or host tensor/array)."""
+        ids = (ctypes.c_int * len(channel_ids))(*channel_ids)
+        on_dev = bool(getattr(out, "is_cuda", False))
+        _check(self._lib.nbs_correlate(self.h, ids, len(channel_ids), t_begin, t_end, _ptr(out), int(on_dev)),
+               self.h)
+        return out
+
+    PARAM_CONTRACT_CFG = 0
+
+    def set_param(self, param: int, value: int):
+        _check(self._lib.nbs_set_param(self.h, param, value), self.h)
+
+    STAGES = ("rescale", "blocks", "fft_fwd", "contract", "fft_inv", "restore_copy")
+
+    def set_profiling(self, on: bool = True):
+        _check(self._lib.nbs_set_profiling(self.h, int(on)), self.h)
+
+    def profile(self):
+        """(dict stage -> accumulated device ms, number of kernel launches)."""
+        ms = (ctypes.c_double * 6)()
+        n = ctypes.c_longlong()
+        _check(self._lib.nbs_profile(self.h, ms, ctypes.byref(n)), self.h)
+        return dict(zip(self.STAGES, list(ms))), n.value
+
+    def zero_momentum(self, n_channels: int):
+        import numpy as np
+        out = np.zeros((n_channels, 4, 4, 2, 2), dtype=np.complex128)
+        _check(self._lib.nbs_zero_momentum(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), self.h)
+        return out

@@ -1,0 +1,190 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (normwise per channel and timeslice, ||F_gpu - F_ref|| / ||F_ref||):
+FP64 path 1e-12, FP32 path 2e-5.
+"""
+
+import numpy as np
+import pytest
+
+import nbs_inputs as I
+from oracle import nbs_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def nbs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1604_07983_gb300 as P
+    P.lib()
+    return P
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def gpu_correlate(nbs, ids, L, props, precision, t_range=None, host_out=False, c64=False):
+    """props: list over t of (S_l, S_s) numpy complex128 arrays."""
+    T = len(props)
+    t0, t1 = t_range or (0, T)
+    V = L ** 3
+    with nbs.Context(L, T, precision=precision) as ctx:
+        for t, (Sl, Ss) in enumerate(props):
+            dt = torch.complex64 if c64 else torch.complex128
+            ctx.load_props(torch.from_numpy(Sl).to("cuda", dt), torch.from_numpy(Ss).to("cuda", dt), t)
+        shape = (len(ids), t1 - t0, 4, 4, 2, 2, V)
+        if host_out:
+            out = torch.empty(shape, dtype=torch.complex128).pin_memory()
+        else:
+            out = torch.empty(shape, dtype=torch.complex128, device="cuda")
+        ctx.correlate(ids, t0, t1, out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+
+def seeded(seed, L, T, decay=0.0):
+    return [(I.propagator(seed, "l", L, t, decay), I.propagator(seed, "s", L, t, decay)) for t in range(T)]
+
+
+def oracle(name, Sl, Ss, L, r_list=None):
+    return O.correlator(name, {"u": Sl, "d": Sl, "s": Ss}, L, r_list)
+
+
+def test_fp64_all_channels_L2(nbs):
+    L, T = 2, 2
+    props = seeded(1701, L, T)
+    names = nbs.channel_names()
+    ids = list(range(len(names)))
+    F = gpu_correlate(nbs, ids, L, props, nbs.NBS_FP64)
+    for c in ids:
+        for t in range(T):
+            assert rel(F[c, t], oracle(names[c], *props[t], L)) < FP64_TOL, (names[c], t)
+
+
+@pytest.mark.parametrize("L", [1, 3, 4, 6])
+def test_fp64_sizes(nbs, L):
+    props = seeded(1702 + L, L, 1)
+    names = nbs.channel_names()
+    ids = [0, 3, 9, 17, 24, 40, 47, 51]
+    F = gpu_correlate(nbs, ids, L, props, nbs.NBS_FP64)
+    for k, c in enumerate(ids):
+        assert rel(F[k, 0], oracle(names[c], *props[0], L)) < FP64_TOL, names[c]
+
+
+def test_config1_pn_8cube_all_timeslices(nbs):
+    """8^3 x 8, pn channel, full O(V^2) oracle at every r and t."""
+    L, T = 8, 8
+    props = seeded(1605, L, T)
+    F = gpu_correlate(nbs, [0], L, props, nbs.NBS_FP64)
+    for t in range(T):
+        assert rel(F[0, t], oracle(("p", "n", "p", "n"), *props[t], L)) < FP64_TOL, t
+
+
+def test_fp32_decaying_propagators(nbs):
+    """FP32 path with a per-timeslice rescale: late timeslices (|S| ~ e^-15.5) must not underflow."""
+    L, T = 4, 32
+    props = seeded(1607, L, T, decay=0.5)
+    names = nbs.channel_names()
+    ids = [0, 9, 24, 51]
+    F = gpu_correlate(nbs, ids, L, props, nbs.NBS_FP32, t_range=(28, 32))
+    for k, c in enumerate(ids):
+        for tt, t in enumerate(range(28, 32)):
+            ref = oracle(names[c], *props[t], L)
+            assert np.linalg.norm(ref) < 1e-25   # |S|^6 ~ e^-84: FP32 would underflow without the rescale
+            assert rel(F[k, tt], ref) < FP32_TOL, (names[c], t)
+
+
+def test_fp32_all_channels_L4(nbs):
+    L = 4
+    props = seeded(1711, L, 1)
+    names = nbs.channel_names()
+    ids = list(range(len(names)))
+    F32 = gpu_correlate(nbs, ids, L, props, nbs.NBS_FP32)
+    F64 = gpu_correlate(nbs, ids, L, props, nbs.NBS_FP64)
+    for c in ids:
+        ref = oracle(names[c], *props[0], L)
+        assert rel(F64[c, 0], ref) < FP64_TOL, names[c]
+        assert rel(F32[c, 0], ref) < FP32_TOL, names[c]
+
+
+def test_host_output_and_timeslice_split(nbs):
+    L, T = 4, 5
+    props = seeded(1712, L, T)
+    ids = [0, 7, 30]
+    Fd = gpu_correlate(nbs, ids, L, props, nbs.NBS_FP64)
+    Fh = gpu_correlate(nbs, ids, L, props, nbs.NBS_FP64, host_out=True)
+    assert np.array_equal(Fd, Fh)
+    Fa = gpu_correlate(nbs, ids, L, props, nbs.NBS_FP64, t_range=(0, 2))
+    Fb = gpu_correlate(nbs, ids, L, props, nbs.NBS_FP64, t_range=(2, 5))
+    assert np.array_equal(np.concatenate([Fa, Fb], axis=1), Fd)
+
+
+def test_complex64_input(nbs):
+    L = 4
+    props = seeded(1713, L, 1)
+    props32 = [(a.astype(np.complex64).astype(np.complex128), b.astype(np.complex64).astype(np.complex128))
+               for a, b in props]
+    names = nbs.channel_names()
+    ids = [0, 24]
+    F = gpu_correlate(nbs, ids, L, props, nbs.NBS_FP32, c64=True)
+    for k, c in enumerate(ids):
+        assert rel(F[k, 0], oracle(names[c], *props32[0], L)) < FP32_TOL
+
+
+def test_16cube_gauge_invariance_and_samples(nbs):
+    """16^3: every channel invariant under site-local SU(3) sink-colour rotations;
+    sampled r and the zero-momentum sum against the oracle for two channels."""
+    L = 16
+    Sl, Ss = I.propagator(1606, "l", L, 0), I.propagator(1606, "s", L, 0)
+    U = I.haar_su3(1606, L)
+    names = nbs.channel_names()
+    ids = list(range(len(names)))
+    F = gpu_correlate(nbs, ids, L, [(Sl, Ss)], nbs.NBS_FP64)
+    Fr = gpu_correlate(nbs, ids, L, [(I.rotate_sink_colour(Sl, U), I.rotate_sink_colour(Ss, U))], nbs.NBS_FP64)
+    for c in ids:
+        assert rel(Fr[c, 0], F[c, 0]) < FP64_TOL, names[c]
+    rs = [(0, 0, 0), (1, 0, 0), (0, 15, 0), (8, 8, 8), (3, 11, 5)]
+    idx = [x + L * (y + L * z) for x, y, z in rs]
+    props = {"u": Sl, "d": Sl, "s": Ss}
+    for c in (0, 51):
+        ref = O.correlator(names[c], props, L, rs)
+        assert rel(F[c, 0][..., idx], ref) < FP64_TOL, names[c]
+        zm = O.zero_momentum(names[c], props, L)
+        assert rel(F[c, 0].sum(-1), zm) < FP64_TOL
+
+
+def test_zero_momentum_call(nbs):
+    L = 4
+    props = seeded(1714, L, 1)
+    ids = [0, 24, 51]
+    with nbs.Context(L, 1, precision=nbs.NBS_FP64) as ctx:
+        ctx.load_props(torch.from_numpy(props[0][0]).cuda(), torch.from_numpy(props[0][1]).cuda(), 0)
+        out = torch.empty((3, 1, 4, 4, 2, 2, L ** 3), dtype=torch.complex128, device="cuda")
+        ctx.correlate(ids, 0, 1, out)
+        zm = ctx.zero_momentum(3)
+    assert rel(zm, out.cpu().numpy()[:, 0].sum(-1)) < FP64_TOL
+
+
+def test_state_and_nan_errors(nbs):
+    L = 2
+    with nbs.Context(L, 2) as ctx:
+        out = torch.empty((1, 1, 4, 4, 2, 2, 8), dtype=torch.complex128, device="cuda")
+        with pytest.raises(nbs.NBSError) as e:
+            ctx.correlate([0], 0, 1, out)
+        assert e.value.code == -4
+        Sl, Ss = I.propagator(1, "l", L, 0), I.propagator(1, "s", L, 0)
+        Sl[3, 4, 5] = np.nan
+        ctx.load_props(torch.from_numpy(Sl).cuda(), torch.from_numpy(Ss).cuda(), 0)
+        with pytest.raises(nbs.NBSError) as e:
+            ctx.correlate([0], 0, 1, out)
+        assert e.value.code == -6
+        with pytest.raises(nbs.NBSError) as e:
+            ctx.correlate([52], 0, 1, out)
+        assert e.value.code == -1
