@@ -132,6 +132,30 @@ int nbs_channel_info(int id, char* buf, int len);
  * when h is NULL).  Never NULL. */
 const char* nbs_last_error(const nbs_ctx* h);
 
+/* ---- correlator without any device allocation ----------------------------
+ * Not part of the paper's method (it has no counterpart there): an entry
+ * point for callers that cannot call cudaMalloc -- a host application that
+ * owns all device memory through its own pool, a process whose allocator is
+ * locked, a loop that must not allocate.  It computes, in FP64, the
+ * correlator of ONE built-in channel on ONE timeslice of an L^3 lattice with
+ * L <= NBS_STATIC_MAX_L, exactly as nbs_correlate would, but every
+ * intermediate buffer lives in one static device array of
+ * NBS_STATIC_SCRATCH_BYTES bytes that each GPU loading the library keeps
+ * until the process exits.
+ *   u, s: device pointers, V*144 complex values of `dtype` each, layout as
+ *         in nbs_load_props; out: device pointer, complex128 [a1][a2][a3][a4][V].
+ *   stream: cudaStream_t (0 = legacy default).  Returns after `out` is written.
+ * Errors: NBS_EINVAL for L > NBS_STATIC_MAX_L, an unknown channel or null
+ * pointers (text in nbs_last_error(NULL)); NBS_ENAN; NBS_ECUDA.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and uploads the FFT twiddles; make that first call
+ * before any stream capture.  Every call reuses the same array and leaves
+ * its contents behind; calls that overlap on the GPU (other streams or host
+ * threads) race on it and must be serialised by the caller. */
+#define NBS_STATIC_MAX_L 4
+#define NBS_STATIC_SCRATCH_BYTES 12582912
+int nbs_correlate_static(const void* u, const void* s, int L, int dtype, int channel_id, void* out, void* stream);
+
 /* ---- host-only introspection of the compiled channel tables ------------
  * nbs_plan_create runs the host "channel compiler" (Sec. 4 (ii)-(iii): the
  * diagrammatic classification done on the CPU and packed as structures of

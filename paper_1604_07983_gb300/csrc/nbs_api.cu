@@ -349,6 +349,8 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
 
 }  // namespace
 
+void nbs::set_global_error(const std::string& msg) { g_err = msg; }
+
 extern "C" {
 
 int nbs_set_allocator(nbs_alloc_fn alloc, nbs_free_fn free_fn, void* user) {

@@ -49,4 +49,7 @@ struct Plan {
 // Compile the tables for the given channel ids.  Returns "" or an error text.
 std::string compile_plan(const std::vector<int>& channel_ids, Plan& out);
 
+// Set the text that nbs_last_error(NULL) returns on this thread.
+void set_global_error(const std::string& msg);
+
 }  // namespace nbs

@@ -26,7 +26,7 @@ EXPORTS = ["nbs_set_allocator", "nbs_create", "nbs_destroy", "nbs_set_precision"
            "nbs_load_props", "nbs_blocks", "nbs_correlate", "nbs_zero_momentum", "nbs_set_param", "nbs_set_profiling",
            "nbs_profile", "nbs_channel_count",
            "nbs_channel_info", "nbs_last_error", "nbs_plan_create", "nbs_plan_destroy", "nbs_plan_sizes",
-           "nbs_plan_export"]
+           "nbs_plan_export", "nbs_correlate_static"]
 
 
 class NBSError(RuntimeError):
@@ -69,6 +69,7 @@ def lib():
         "nbs_plan_destroy": (i, [vp]),
         "nbs_plan_sizes": (i, [vp, ctypes.POINTER(ll)]),
         "nbs_plan_export": (i, [vp, i, vp]),
+        "nbs_correlate_static": (i, [vp, vp, i, i, i, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -159,6 +160,23 @@ def use_torch_allocator():
 
     _alloc_refs = (ALLOC_FN(_a), FREE_FN(_f))
     _check(lib().nbs_set_allocator(_alloc_refs[0], _alloc_refs[1], None))
+
+
+# ---- correlator without device allocation ------------------------------------
+
+STATIC_MAX_L = 4
+
+
+def correlate_static(u, s, L: int, channel_id: int, out, stream=None):
+    """One channel, one timeslice, FP64, L <= 4, every intermediate in the library's static device array.
+
+    u, s: device tensors [V,12,12] (complex128 or complex64); out: device complex128 [4,4,2,2,V].
+    """
+    c64 = "complex64" in str(u.dtype)
+    h = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().nbs_correlate_static(_ptr(u), _ptr(s), L, NBS_C64 if c64 else NBS_C128, channel_id, _ptr(out),
+                                      ctypes.c_void_p(h)))
+    return out
 
 
 # ---- context -----------------------------------------------------------------
