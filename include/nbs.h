@@ -102,10 +102,13 @@ int nbs_correlate(nbs_ctx* h, const int* channel_ids, int n_channels,
  * sum_r F(r) = F~(q = 0), complex128 [n_channels][64] on the host. */
 int nbs_zero_momentum(nbs_ctx* h, double* out);
 
-/* Launch-shape parameters (for tuning; results do not depend on them).
- * NBS_PARAM_CONTRACT_CFG: A*10 + W, A = sink spins alpha1 per thread of the
- * contraction (1, 2 or 4), W = warps per block (1, 2 or 4); 0 = default
- * (42 for FP32, 21 for FP64).  NBS_EINVAL for any other value. */
+/* Launch-shape parameters (for tuning; results agree to rounding).
+ * NBS_PARAM_CONTRACT_CFG selects the contraction kernel: 0 = default
+ * (thread-per-momentum kernel, A = 4, W = 2 in FP32; A = 2, W = 1 in FP64);
+ * 1 = the momentum-slab kernel (one block per momentum and channel group,
+ * stored blocks staged in shared memory); A*10 + W = the thread-per-momentum
+ * kernel with A sink spins alpha1 per thread (1, 2 or 4) and W warps per
+ * block (1, 2 or 4).  NBS_EINVAL for any other value. */
 #define NBS_PARAM_CONTRACT_CFG 0
 int nbs_set_param(nbs_ctx* h, int param, int value);
 
@@ -171,19 +174,25 @@ int nbs_plan_destroy(nbs_plan* p);
 #define NBS_PS_NENT1      4   /* side-1 gather entries                       */
 #define NBS_PS_NENT2      5   /* side-2 gather entries                       */
 #define NBS_PS_NCH        6   /* channels                                    */
-#define NBS_PLAN_NSIZES   7
+#define NBS_PS_NGROUPS    7   /* slab groups                                 */
+#define NBS_PS_NITEMS     8   /* slab work items                             */
+#define NBS_PLAN_NSIZES   9
 int nbs_plan_sizes(const nbs_plan* p, long long* sizes);
 /* what: NBS_PX_* ; dst must hold the documented number of int32/double */
 #define NBS_PX_TYPES      0   /* int32 [ntypes][4]: cell_off, ncell, term_off, nterm   */
 #define NBS_PX_TYPETERMS  1   /* int32 [nterms][4]: pattern, a0, a1, a2                */
 #define NBS_PX_TYPECOEF   2   /* double [nterms]                                        */
 #define NBS_PX_CELLS      3   /* int32 [ncells]: y0 + 12*y1 + 144*y2                    */
-#define NBS_PX_TERMS      4   /* int32 [nterm][8]: ch, K, shape, n1, n2, off1, off2, 0  */
+#define NBS_PX_TERMS      4   /* int32 [nterm][8]: ch, K, shape, n1, n2, off1, off2, slot in group */
 #define NBS_PX_ENT1_CELL  5   /* int32 [nent1]  */
 #define NBS_PX_ENT1_COEF  6   /* double [nent1] */
 #define NBS_PX_ENT2_CELL  7   /* int32 [nent2]  */
 #define NBS_PX_ENT2_COEF  8   /* double [nent2] */
 #define NBS_PX_CHANNELS   9   /* int32 [nch][4]: term_begin, term_end, n_l, n_s         */
+#define NBS_PX_GROUPS    10   /* int32 [ngroups][24]: base1, ncell1, base2, ncell2, ch_off, nch,
+                                 item_off, nslot, warp_off[5], out_base[5], cfirst[4], 0, 0 */
+#define NBS_PX_GROUPCH   11   /* int32 [sum of nch]: request-order channel of each group slot */
+#define NBS_PX_ITEMS     12   /* int32 [nitems][2]: term, first shared index                 */
 int nbs_plan_export(const nbs_plan* p, int what, void* dst);
 
 #ifdef __cplusplus

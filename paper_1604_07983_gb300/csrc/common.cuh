@@ -75,6 +75,13 @@ cudaError_t fft3d_inverse(C<T>* data, long long nbatch, int L, cudaStream_t st);
 template <typename T>
 cudaError_t launch_contract(const C<T>* FB, int L, const DevTerm* terms, const int* ch_tb, int nch,
                             const Ent<T>* e1, const Ent<T>* e2, C<T>* Ft, int cfg, cudaStream_t st);
+// momentum-slab contraction; groups points to GroupHdr[ngroups] (plan.h)
+template <typename T>
+cudaError_t launch_contract_slab(const C<T>* FB, int L, int ngroups, const void* groups, const int* group_ch,
+                                 const int* items, const DevTerm* terms, const Ent<T>* e1, const Ent<T>* e2, int st1,
+                                 int st2, int max_nch, C<T>* Ft, cudaStream_t st);
+template <typename T>
+size_t slab_smem_bytes(int st1, int st2, int max_nch);
 template <typename T>
 cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_nl, const int* exps,
                            double2* out, long long ch_stride, cudaStream_t st);

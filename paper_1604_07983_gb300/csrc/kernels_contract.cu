@@ -13,6 +13,7 @@
 // and accumulates F~[alpha1][alpha2][alpha3][alpha4](q) += e1 * e2, the
 // held spins (h1, h2) carrying alpha3 / alpha4 as the term's shape says.
 #include "common.cuh"
+#include "plan.h"
 
 #include <algorithm>
 
@@ -157,6 +158,273 @@ __global__ void __launch_bounds__(NT) k_contract(const C<T>* __restrict__ FB, in
       }
 }
 
+// ---- momentum-slab contraction ----------------------------------------------
+//
+// One CTA per (q, group of channels that read the same two stored block
+// types).  The CTA first copies the two momentum slabs it needs -- every cell
+// of B1's type at q and of B2's type at -q, four spins each -- from HBM into
+// shared memory with cp.async, so that the ~100 reads of every stored value
+// that the effective blocks of all terms make are served from shared memory.
+// The slab of a type is stored as planes of 16 bytes per cell (FP32: spins
+// 0,1 | 2,3; FP64: one spin per plane) so that random cells spread over the
+// banks.  Warps take items (term, 32 consecutive shared indices xi~): lane j
+// forms the two effective blocks of shared index k0 + j and accumulates its
+// 64 products in registers; a warp reduce-scatter then leaves two of the 64
+// sums per lane, and the per-warp partials are added in a fixed order.
+
+template <typename T> struct SlabTraits;
+template <> struct SlabTraits<float> { static constexpr int NP = 2; };   // planes of float4
+template <> struct SlabTraits<double> { static constexpr int NP = 4; };  // planes of double2
+
+template <typename T>
+__device__ __forceinline__ void slab_load(const uint4* S, int stride, int cell, C<T> (&x)[4]);
+template <>
+__device__ __forceinline__ void slab_load<float>(const uint4* S, int stride, int cell, float2 (&x)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(S + cell);
+  const float4 b = *reinterpret_cast<const float4*>(S + stride + cell);
+  x[0] = make_float2(a.x, a.y);
+  x[1] = make_float2(a.z, a.w);
+  x[2] = make_float2(b.x, b.y);
+  x[3] = make_float2(b.z, b.w);
+}
+template <>
+__device__ __forceinline__ void slab_load<double>(const uint4* S, int stride, int cell, double2 (&x)[4]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) x[a] = *reinterpret_cast<const double2*>(S + a * stride + cell);
+}
+
+// A1 sink spins alpha1 per lane: lane = ag * KPW + kk, alpha1 = ag * A1 + a'
+template <typename T, int A1>
+__device__ __forceinline__ void slab_load_a1(const uint4* S, int stride, int cell, int ag, C<T> (&x)[A1]);
+template <>
+__device__ __forceinline__ void slab_load_a1<float, 2>(const uint4* S, int stride, int cell, int ag, float2 (&x)[2]) {
+  const float4 a = *reinterpret_cast<const float4*>(S + ag * stride + cell);
+  x[0] = make_float2(a.x, a.y);
+  x[1] = make_float2(a.z, a.w);
+}
+template <>
+__device__ __forceinline__ void slab_load_a1<float, 4>(const uint4* S, int stride, int cell, int ag, float2 (&x)[4]) {
+  slab_load<float>(S, stride, cell, x);
+}
+template <>
+__device__ __forceinline__ void slab_load_a1<double, 1>(const uint4* S, int stride, int cell, int ag, double2 (&x)[1]) {
+  x[0] = *reinterpret_cast<const double2*>(S + ag * stride + cell);
+}
+template <>
+__device__ __forceinline__ void slab_load_a1<double, 2>(const uint4* S, int stride, int cell, int ag, double2 (&x)[2]) {
+  x[0] = *reinterpret_cast<const double2*>(S + (2 * ag) * stride + cell);
+  x[1] = *reinterpret_cast<const double2*>(S + (2 * ag + 1) * stride + cell);
+}
+
+// N gather entries (N even) from a 16-byte aligned run: cell - base and coefficient
+template <typename T, int N>
+__device__ __forceinline__ void load_entries(const Ent<T>* p, int base, int (&cell)[N], T (&coef)[N]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int j = 0; j < N; j += 2) {
+      const int4 w = __ldg(reinterpret_cast<const int4*>(p + j));
+      cell[j] = w.x - base;
+      coef[j] = __int_as_float(w.y);
+      cell[j + 1] = w.z - base;
+      coef[j + 1] = __int_as_float(w.w);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const int4 w = __ldg(reinterpret_cast<const int4*>(p + j));
+      cell[j] = w.x - base;
+      coef[j] = __hiloint2double(w.w, w.z);
+    }
+  }
+}
+
+template <typename T, int A1, int SHAPE>
+__device__ __forceinline__ void slab_item(const DevTerm& h, int k, bool active, int ag, const uint4* S1, int st1,
+                                          int base1, const uint4* S2, int st2, int base2,
+                                          const Ent<T>* __restrict__ E1, const Ent<T>* __restrict__ E2,
+                                          T (&acc)[A1 * 32]) {
+  constexpr int NH1 = 1 << ((SHAPE & 1) + ((SHAPE >> 1) & 1));
+  constexpr int NH2 = 4 / NH1;
+  C<T> v1[NH1][A1], v2[NH2][4];
+#pragma unroll
+  for (int hh = 0; hh < NH1; ++hh)
+#pragma unroll
+    for (int a = 0; a < A1; ++a) v1[hh][a] = czero<T>();
+#pragma unroll
+  for (int hh = 0; hh < NH2; ++hh)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) v2[hh][a] = czero<T>();
+  if (active) {
+    const Ent<T>* p1 = E1 + h.off1 + (long long)k * NH1 * h.n1;
+    for (int i = 0; i < h.n1; i += 2, p1 += 2 * NH1) {
+      int cell[2 * NH1];
+      T coef[2 * NH1];
+      load_entries<T, 2 * NH1>(p1, base1, cell, coef);
+#pragma unroll
+      for (int j = 0; j < 2 * NH1; ++j) {
+        C<T> x[A1];
+        slab_load_a1<T, A1>(S1, st1, cell[j], ag, x);
+#pragma unroll
+        for (int a = 0; a < A1; ++a) crfma<T>(v1[j % NH1][a], coef[j], x[a]);
+      }
+    }
+    const Ent<T>* p2 = E2 + h.off2 + (long long)k * NH2 * h.n2;
+    for (int i = 0; i < h.n2; i += 2, p2 += 2 * NH2) {
+      int cell[2 * NH2];
+      T coef[2 * NH2];
+      load_entries<T, 2 * NH2>(p2, base2, cell, coef);
+#pragma unroll
+      for (int j = 0; j < 2 * NH2; ++j) {
+        C<T> x[4];
+        slab_load<T>(S2, st2, cell[j], x);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) crfma<T>(v2[j % NH2][b], coef[j], x[b]);
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < A1; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int h1 = 0; h1 < NH1; ++h1)
+#pragma unroll
+        for (int h2 = 0; h2 < NH2; ++h2) {
+          int s;  // alpha3 + 2 alpha4
+          if (SHAPE == 0) s = h2;
+          else if (SHAPE == 3) s = h1;
+          else if (SHAPE == 1) s = h1 + 2 * h2;
+          else s = h2 + 2 * h1;
+          const int m = (a * 4 + b) * 4 + s;
+          C<T> z = cmake<T>(acc[2 * m], acc[2 * m + 1]);
+          cfma<T>(z, v1[h1][a], v2[h2][b]);
+          acc[2 * m] = z.x;
+          acc[2 * m + 1] = z.y;
+        }
+}
+
+// Sum acc over the KPW lanes that share a spin group (lane bits below KPW);
+// lane kk ends with the sums of acc[4 kk .. 4 kk + 3] in acc[0..3].  One
+// stage per lane bit, from the highest: keep the half selected by the bit,
+// send the other half to the partner lane.
+template <typename T, int LEN, int S>
+struct ReduceScatter {
+  static __device__ __forceinline__ void run(T (&acc)[LEN], int lane) {
+    if constexpr (S >= 1) {
+      constexpr int n = 2 * S;  // live length after this stage = 4 * S; before it 8 * S
+      const bool up = lane & S;
+#pragma unroll
+      for (int j = 0; j < 2 * n; ++j) {
+        const T keep = up ? acc[2 * n + j] : acc[j];
+        const T give = up ? acc[j] : acc[2 * n + j];
+        acc[j] = keep + __shfl_xor_sync(0xffffffffu, give, S);
+      }
+      ReduceScatter<T, LEN, S / 2>::run(acc, lane);
+    }
+  }
+};
+template <typename T, int LEN, int KPW>
+__device__ __forceinline__ void warp_reduce_scatter(T (&acc)[LEN], int lane) {
+  static_assert(LEN == 4 * KPW, "four values per lane remain");
+  ReduceScatter<T, LEN, KPW / 2>::run(acc, lane);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+template <typename T, int NW, int A1>
+__global__ void __launch_bounds__(NW * 32) k_contract_slab(const C<T>* __restrict__ FB, int L, int ngroups,
+                                                          const GroupHdr* __restrict__ groups,
+                                                          const int* __restrict__ group_ch, const int* __restrict__ items,
+                                                          const DevTerm* __restrict__ terms,
+                                                          const Ent<T>* __restrict__ E1, const Ent<T>* __restrict__ E2,
+                                                          int st1, int st2, int max_slot, C<T>* __restrict__ Ft) {
+  constexpr int NP = SlabTraits<T>::NP;
+  constexpr int NT = NW * 32;
+  constexpr int KPW = 32 * A1 / 4;      // shared indices per warp pass
+  constexpr int LEN = A1 * 32;          // accumulator values per lane
+  static_assert(LEN / KPW == 4, "reduce-scatter leaves two complex sums per lane");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint4* S1 = reinterpret_cast<uint4*>(smem_raw);
+  uint4* S2 = S1 + NP * st1;
+  C<T>* OUT = reinterpret_cast<C<T>*>(S2 + NP * st2);
+  const long long V = (long long)L * L * L;
+  const int q = blockIdx.x / ngroups;
+  const int g = blockIdx.x % ngroups;
+  const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
+  const int qm = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
+  const GroupHdr& gh = groups[g];
+  const int base1 = gh.base1, n1 = gh.ncell1, base2 = gh.base2, n2 = gh.ncell2, nch = gh.nch, nslot = gh.nslot;
+  // slabs: cell c, plane p = 16 bytes at ((base + c) * V + q) * 4 complex + 16 p bytes
+  for (int i = threadIdx.x; i < NP * n1; i += NT) {
+    const int c = i / NP, p = i % NP;
+    cp_async16(S1 + p * st1 + c, reinterpret_cast<const char*>(FB + ((long long)(base1 + c) * V + q) * 4) + 16 * p);
+  }
+  for (int i = threadIdx.x; i < NP * n2; i += NT) {
+    const int c = i / NP, p = i % NP;
+    cp_async16(S2 + p * st2 + c, reinterpret_cast<const char*>(FB + ((long long)(base2 + c) * V + qm) * 4) + 16 * p);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (int i = threadIdx.x; i < nslot * 64; i += NT) OUT[i] = czero<T>();
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ag = lane / KPW, kk = lane % KPW;
+  T acc[LEN];
+#pragma unroll
+  for (int j = 0; j < LEN; ++j) acc[j] = T(0);
+  int cur = -1;
+  const int it0 = gh.item_off + gh.warp_off[w], it1 = gh.item_off + gh.warp_off[w + 1];
+  for (int it = it0; it < it1; ++it) {
+    const int term = items[2 * it], k0 = items[2 * it + 1];
+    const DevTerm h = terms[term];
+    if (h.pad != cur) {
+      if (cur >= 0) {
+        warp_reduce_scatter<T, LEN, KPW>(acc, lane);
+        // lane (ag, kk) holds products 2 kk, 2 kk + 1 of spin group ag
+        C<T>* o = OUT + (gh.out_base[w] + cur - gh.cfirst[w]) * 64 + ag * (A1 * 16) + 2 * kk;
+        o[0] = cadd<T>(o[0], cmake<T>(acc[0], acc[1]));
+        o[1] = cadd<T>(o[1], cmake<T>(acc[2], acc[3]));
+#pragma unroll
+        for (int j = 0; j < LEN; ++j) acc[j] = T(0);
+      }
+      cur = h.pad;
+    }
+    for (int kb = 0; kb < 32 && k0 + kb < h.K; kb += KPW) {
+      const int k = k0 + kb + kk;
+      const bool active = (kb + kk < 32) && k < h.K;
+      switch (h.shape) {
+        case 0: slab_item<T, A1, 0>(h, k, active, ag, S1, st1, base1, S2, st2, base2, E1, E2, acc); break;
+        case 1: slab_item<T, A1, 1>(h, k, active, ag, S1, st1, base1, S2, st2, base2, E1, E2, acc); break;
+        case 2: slab_item<T, A1, 2>(h, k, active, ag, S1, st1, base1, S2, st2, base2, E1, E2, acc); break;
+        default: slab_item<T, A1, 3>(h, k, active, ag, S1, st1, base1, S2, st2, base2, E1, E2, acc); break;
+      }
+    }
+  }
+  if (cur >= 0) {
+    warp_reduce_scatter<T, LEN, KPW>(acc, lane);
+    C<T>* o = OUT + (gh.out_base[w] + cur - gh.cfirst[w]) * 64 + ag * (A1 * 16) + 2 * kk;
+    o[0] = cadd<T>(o[0], cmake<T>(acc[0], acc[1]));
+    o[1] = cadd<T>(o[1], cmake<T>(acc[2], acc[3]));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nch * 64; i += NT) {
+    const int c = i / 64, m = i % 64;
+    C<T> sum = czero<T>();
+#pragma unroll
+    for (int ww = 0; ww < NW; ++ww) {  // fixed order: the result does not depend on scheduling
+      const int r = c - gh.cfirst[ww];
+      if (r >= 0 && r < gh.out_base[ww + 1] - gh.out_base[ww]) sum = cadd<T>(sum, OUT[(gh.out_base[ww] + r) * 64 + m]);
+    }
+    // m = (alpha1*4 + alpha2)*4 + alpha3 + 2 alpha4  ->  output [alpha1][alpha2][alpha3][alpha4]
+    const int spin = (m & ~3) + 2 * (m & 1) + ((m >> 1) & 1);
+    Ft[((long long)group_ch[gh.ch_off + c] * 64 + spin) * V + q] = sum;
+  }
+}
+
 // out[ch * ch_stride + c*V + r] = Ft[ch][c][r] * 2^(e_l n_l + e_s n_s) / V   (FP64)
 template <typename T>
 __global__ void __launch_bounds__(256) k_restore(const C<T>* __restrict__ Ft, long long V, const int* __restrict__ ch_nl,
@@ -185,7 +453,7 @@ cudaError_t launch_contract_cfg(const C<T>* FB, int L, const DevTerm* terms, con
   return cudaGetLastError();
 }
 
-// cfg: alpha1 values per thread (1, 2, 4) x 10 + threads per block / 32 (1, 2, 4); 0 = default
+// cfg: alpha1 values per thread (1, 2, 4) x 10 + threads per block / 32 (1, 2, 4)
 template <typename T>
 cudaError_t launch_contract(const C<T>* FB, int L, const DevTerm* terms, const int* ch_tb, int nch, const Ent<T>* e1,
                             const Ent<T>* e2, C<T>* Ft, int cfg, cudaStream_t st) {
@@ -203,6 +471,27 @@ cudaError_t launch_contract(const C<T>* FB, int L, const DevTerm* terms, const i
 }
 
 template <typename T>
+size_t slab_smem_bytes(int st1, int st2, int max_slot) {
+  return (size_t)SlabTraits<T>::NP * 16 * (st1 + st2) + (size_t)max_slot * 64 * sizeof(C<T>);
+}
+
+template <typename T>
+cudaError_t launch_contract_slab(const C<T>* FB, int L, int ngroups, const void* groups, const int* group_ch,
+                                 const int* items, const DevTerm* terms, const Ent<T>* e1, const Ent<T>* e2, int st1,
+                                 int st2, int max_slot, C<T>* Ft, cudaStream_t st) {
+  const long long V = (long long)L * L * L;
+  const size_t sm = slab_smem_bytes<T>(st1, st2, max_slot);
+  auto kern = k_contract_slab<T, NBS_SLAB_WARPS, sizeof(T) == 4 ? 2 : 1>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const long long nblk = V * ngroups;
+  if (nblk > 2147483647LL) return cudaErrorInvalidValue;
+  kern<<<(unsigned)nblk, NBS_SLAB_WARPS * 32, sm, st>>>(FB, L, ngroups, (const GroupHdr*)groups, group_ch, items,
+                                                       terms, e1, e2, st1, st2, max_slot, Ft);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_nl, const int* exps, double2* out,
                            long long ch_stride, cudaStream_t st) {
   long long n = 64LL * V;
@@ -216,6 +505,14 @@ template cudaError_t launch_contract<float>(const float2*, int, const DevTerm*, 
                                             const Ent<float>*, float2*, int, cudaStream_t);
 template cudaError_t launch_contract<double>(const double2*, int, const DevTerm*, const int*, int, const Ent<double>*,
                                              const Ent<double>*, double2*, int, cudaStream_t);
+template cudaError_t launch_contract_slab<float>(const float2*, int, int, const void*, const int*, const int*,
+                                                 const DevTerm*, const Ent<float>*, const Ent<float>*, int, int, int,
+                                                 float2*, cudaStream_t);
+template cudaError_t launch_contract_slab<double>(const double2*, int, int, const void*, const int*, const int*,
+                                                  const DevTerm*, const Ent<double>*, const Ent<double>*, int, int, int,
+                                                  double2*, cudaStream_t);
+template size_t slab_smem_bytes<float>(int, int, int);
+template size_t slab_smem_bytes<double>(int, int, int);
 template cudaError_t launch_restore<float>(const float2*, int, int, const int*, const int*, double2*, long long,
                                            cudaStream_t);
 template cudaError_t launch_restore<double>(const double2*, int, int, const int*, const int*, double2*, long long,

@@ -81,7 +81,8 @@ struct nbs_ctx {
   std::vector<int> plan_ids;
   Plan plan;
   int plan_gen = 0;
-  DevBuf d_terms, d_chtb, d_chnl, d_e1, d_e2, d_cells;
+  DevBuf d_terms, d_chtb, d_chnl, d_e1, d_e2, d_cells, d_groups, d_gch, d_items;
+  int slab_st1 = 0, slab_st2 = 0, slab_nch = 0;
   int tables_mode = -1;
   TypeRecipeSet recipes;
 
@@ -174,8 +175,20 @@ int upload_tables(nbs_ctx* h) {
   std::vector<DevTerm> terms(P.terms.size());
   for (size_t i = 0; i < P.terms.size(); ++i) {
     const TermHdr& t = P.terms[i];
-    terms[i] = {t.ch, t.K, t.shape, t.n1, t.n2, t.off1, t.off2, 0};
+    terms[i] = {t.ch, t.K, t.shape, t.n1, t.n2, t.off1, t.off2, t.pad};
   }
+  h->slab_st1 = h->slab_st2 = h->slab_nch = 0;
+  for (const GroupHdr& g : P.groups) {
+    h->slab_st1 = std::max(h->slab_st1, g.ncell1);
+    h->slab_st2 = std::max(h->slab_st2, g.ncell2);
+    h->slab_nch = std::max(h->slab_nch, g.nslot);
+  }
+  if ((rc = ensure(h, h->d_groups, std::max<size_t>(P.groups.size(), 1) * sizeof(GroupHdr), "groups"))) return rc;
+  if ((rc = ensure(h, h->d_gch, std::max<size_t>(P.group_ch.size(), 1) * sizeof(int), "group channels"))) return rc;
+  if ((rc = ensure(h, h->d_items, std::max<size_t>(P.items.size(), 1) * sizeof(int), "work items"))) return rc;
+  CK(cudaMemcpyAsync(h->d_groups.p, P.groups.data(), P.groups.size() * sizeof(GroupHdr), cudaMemcpyHostToDevice, h->st), "upload groups");
+  CK(cudaMemcpyAsync(h->d_gch.p, P.group_ch.data(), P.group_ch.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload group channels");
+  CK(cudaMemcpyAsync(h->d_items.p, P.items.data(), P.items.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload items");
   if ((rc = ensure(h, h->d_terms, std::max<size_t>(terms.size(), 1) * sizeof(DevTerm), "terms"))) return rc;
   if ((rc = ensure(h, h->d_chtb, P.ch_term_begin.size() * sizeof(int), "term ranges"))) return rc;
   if ((rc = ensure(h, h->d_chnl, std::max<size_t>(P.ch_nl.size(), 1) * sizeof(int), "flavour content"))) return rc;
@@ -303,9 +316,18 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
       if ((rc = build_blocks<T>(h, t))) return rc;
     }
     cudaEvent_t e3 = stage_begin(h);
-    CK(launch_contract<T>((const C<T>*)h->FB.p, h->L, (const DevTerm*)h->d_terms.p, (const int*)h->d_chtb.p, nch,
-                          (const Ent<T>*)h->d_e1.p, (const Ent<T>*)h->d_e2.p, (C<T>*)h->Ft.p, h->contract_cfg, h->st),
-       "contraction");
+    if (h->contract_cfg == 1) {
+      CK(launch_contract_slab<T>((const C<T>*)h->FB.p, h->L, (int)h->plan.groups.size(), h->d_groups.p,
+                                 (const int*)h->d_gch.p, (const int*)h->d_items.p, (const DevTerm*)h->d_terms.p,
+                                 (const Ent<T>*)h->d_e1.p, (const Ent<T>*)h->d_e2.p, h->slab_st1, h->slab_st2,
+                                 h->slab_nch, (C<T>*)h->Ft.p, h->st),
+         "contraction");
+    } else {
+      CK(launch_contract<T>((const C<T>*)h->FB.p, h->L, (const DevTerm*)h->d_terms.p, (const int*)h->d_chtb.p, nch,
+                            (const Ent<T>*)h->d_e1.p, (const Ent<T>*)h->d_e2.p, (C<T>*)h->Ft.p, h->contract_cfg,
+                            h->st),
+         "contraction");
+    }
     stage_end(h, 3, e3);
     h->launches += 1 + (h->L > 1 ? 3 : 0) + 1;
     if (t == t1 - 1) {
@@ -411,7 +433,8 @@ int nbs_destroy(nbs_ctx* h) {
   cudaStreamSynchronize(h->st);
   if (h->cst) cudaStreamSynchronize(h->cst);
   DevBuf* bufs[] = {&h->props, &h->propsT, &h->Q, &h->FB, &h->Ft, &h->zm, &h->small, &h->stage[0], &h->stage[1],
-                    &h->d_terms, &h->d_chtb, &h->d_chnl, &h->d_e1, &h->d_e2, &h->d_cells};
+                    &h->d_terms, &h->d_chtb, &h->d_chnl, &h->d_e1, &h->d_e2, &h->d_cells, &h->d_groups,
+                    &h->d_gch, &h->d_items};
   for (DevBuf* b : bufs) dev_free(b->p, h->free_fn, h->free_user);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   for (int b = 0; b < 2; ++b) {
@@ -485,8 +508,8 @@ int nbs_set_param(nbs_ctx* h, int param, int value) {
   switch (param) {
     case NBS_PARAM_CONTRACT_CFG: {
       const int a = value / 10, w = value % 10;
-      if (value != 0 && !((a == 1 || a == 2 || a == 4) && (w == 1 || w == 2 || w == 4)))
-        return fail(h, NBS_EINVAL, "contraction config must be 0 or A*10+W with A, W in {1, 2, 4}");
+      if (value != 0 && value != 1 && !((a == 1 || a == 2 || a == 4) && (w == 1 || w == 2 || w == 4)))
+        return fail(h, NBS_EINVAL, "contraction config must be 0, 1 or A*10+W with A, W in {1, 2, 4}");
       h->contract_cfg = value;
       return NBS_OK;
     }
@@ -583,6 +606,8 @@ int nbs_plan_sizes(const nbs_plan* p, long long* s) {
   s[NBS_PS_NENT1] = (long long)P.ent1_cell.size();
   s[NBS_PS_NENT2] = (long long)P.ent2_cell.size();
   s[NBS_PS_NCH] = (long long)P.channels.size();
+  s[NBS_PS_NGROUPS] = (long long)P.groups.size();
+  s[NBS_PS_NITEMS] = (long long)P.items.size() / 2;
   return NBS_OK;
 }
 
@@ -614,7 +639,7 @@ int nbs_plan_export(const nbs_plan* p, int what, void* dst) {
       return NBS_OK;
     case NBS_PX_TERMS:
       for (auto& t : P.terms) {
-        *I++ = t.ch; *I++ = t.K; *I++ = t.shape; *I++ = t.n1; *I++ = t.n2; *I++ = t.off1; *I++ = t.off2; *I++ = 0;
+        *I++ = t.ch; *I++ = t.K; *I++ = t.shape; *I++ = t.n1; *I++ = t.n2; *I++ = t.off1; *I++ = t.off2; *I++ = t.pad;
       }
       return NBS_OK;
     case NBS_PX_ENT1_CELL: std::memcpy(I, P.ent1_cell.data(), P.ent1_cell.size() * sizeof(int)); return NBS_OK;
@@ -626,6 +651,12 @@ int nbs_plan_export(const nbs_plan* p, int what, void* dst) {
         *I++ = P.ch_term_begin[c]; *I++ = P.ch_term_begin[c + 1]; *I++ = P.ch_nl[c]; *I++ = 6 - P.ch_nl[c];
       }
       return NBS_OK;
+    case NBS_PX_GROUPS:
+      static_assert(sizeof(GroupHdr) == 24 * sizeof(int), "group header layout");
+      std::memcpy(I, P.groups.data(), P.groups.size() * sizeof(GroupHdr));
+      return NBS_OK;
+    case NBS_PX_GROUPCH: std::memcpy(I, P.group_ch.data(), P.group_ch.size() * sizeof(int)); return NBS_OK;
+    case NBS_PX_ITEMS: std::memcpy(I, P.items.data(), P.items.size() * sizeof(int)); return NBS_OK;
     default: return fail(nullptr, NBS_EINVAL, "unknown export");
   }
 }

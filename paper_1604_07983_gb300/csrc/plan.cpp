@@ -454,7 +454,8 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
                     cells_side[side - 1].push_back(lst[i].first);
                     coef_side[side - 1].push_back(lst[i].second);
                   } else {
-                    cells_side[side - 1].push_back(0);
+                    // padding: zero coefficient on a cell of the same stored type
+                    cells_side[side - 1].push_back(T.bt.cell_off);
                     coef_side[side - 1].push_back(0.0);
                   }
                 }
@@ -484,6 +485,71 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
     plan.ch_term_begin.push_back((int)plan.terms.size());
   }
   for (auto& T : types) plan.types.push_back(T.bt);
+
+  // ---- slab groups for the momentum-slab contraction -------------------------
+  {
+    std::map<std::pair<int, int>, std::vector<int>> by_types;  // (type B1, type B2) -> channels
+    for (int ci = 0; ci < (int)ids.size(); ++ci) {
+      const ChannelDef& ch = table[ids[ci]];
+      by_types[{fmap[ch.b[0]].type, fmap[ch.b[1]].type}].push_back(ci);
+    }
+    for (auto& kv : by_types) {
+      GroupHdr g = {};
+      const BlockType& t1 = types[kv.first.first].bt;
+      const BlockType& t2 = types[kv.first.second].bt;
+      g.base1 = t1.cell_off; g.ncell1 = t1.ncell;
+      g.base2 = t2.cell_off; g.ncell2 = t2.ncell;
+      g.ch_off = (int)plan.group_ch.size();
+      g.nch = (int)kv.second.size();
+      g.item_off = (int)plan.items.size() / 2;
+      // items in channel order, with their cost
+      std::vector<std::pair<int, int>> its;
+      std::vector<double> cost;
+      for (int local = 0; local < g.nch; ++local) {
+        const int ci = kv.second[local];
+        plan.group_ch.push_back(ci);
+        for (int t = plan.ch_term_begin[ci]; t < plan.ch_term_begin[ci + 1]; ++t) {
+          TermHdr& th = plan.terms[t];
+          th.pad = local;
+          const int nh1 = 1 << ((th.shape & 1) + (th.shape >> 1 & 1)), nh2 = 4 / nh1;
+          for (int k0 = 0; k0 < th.K; k0 += 32) {
+            its.push_back({t, k0});
+            cost.push_back(64.0 + 4.0 * (nh1 * th.n1 + nh2 * th.n2));
+          }
+        }
+      }
+      double total = 0;
+      for (double c : cost) total += c;
+      // contiguous split into NBS_SLAB_WARPS ranges of about equal cost
+      int w = 0;
+      double acc = 0;
+      g.warp_off[0] = 0;
+      for (size_t i = 0; i < its.size(); ++i) {
+        acc += cost[i];
+        if (w < NBS_SLAB_WARPS - 1 && acc >= total * (w + 1) / NBS_SLAB_WARPS) g.warp_off[++w] = (int)i + 1;
+      }
+      while (w < NBS_SLAB_WARPS) g.warp_off[++w] = (int)its.size();
+      // each warp's items span a contiguous range of group channels: one slot each
+      g.out_base[0] = 0;
+      for (int ww = 0; ww < NBS_SLAB_WARPS; ++ww) {
+        int n = 0;
+        g.cfirst[ww] = 0;
+        if (g.warp_off[ww + 1] > g.warp_off[ww]) {
+          const int c0 = plan.terms[its[g.warp_off[ww]].first].pad;
+          const int c1 = plan.terms[its[g.warp_off[ww + 1] - 1].first].pad;
+          g.cfirst[ww] = c0;
+          n = c1 - c0 + 1;
+        }
+        g.out_base[ww + 1] = g.out_base[ww] + n;
+      }
+      g.nslot = g.out_base[NBS_SLAB_WARPS];
+      for (auto& it : its) {
+        plan.items.push_back(it.first);
+        plan.items.push_back(it.second);
+      }
+      plan.groups.push_back(g);
+    }
+  }
   return "";
 }
 

@@ -31,7 +31,24 @@ struct BlockType {
   std::vector<int> cells;                     // cell -> y0 + 12*y1 + 144*y2
 };
 
+// pad = index of the term's channel inside its slab group
 struct TermHdr { int ch, K, shape, n1, n2, off1, off2, pad; };
+
+// Channels that read the same two stored block types (B1's at q, B2's at -q)
+// form a group; one CTA of the momentum-slab contraction handles one
+// (q, group).  Its work is split into items (term, first shared index of a
+// 32-wide chunk), assigned to NBS_SLAB_WARPS warps with balanced cost.
+#define NBS_SLAB_WARPS 4
+struct GroupHdr {
+  int base1, ncell1, base2, ncell2;   // cell ranges of the two types
+  int ch_off, nch;                    // into Plan::group_ch (request-order channel indices)
+  int item_off;                       // into Plan::items (pairs)
+  int nslot;                          // partial-sum slots of all warps
+  int warp_off[NBS_SLAB_WARPS + 1];   // item ranges per warp, relative to item_off
+  int out_base[NBS_SLAB_WARPS + 1];   // first partial-sum slot of each warp
+  int cfirst[NBS_SLAB_WARPS];         // first group channel each warp touches
+  int pad[2];
+};
 
 struct Plan {
   std::vector<int> channels;                  // built-in ids, in request order
@@ -42,6 +59,9 @@ struct Plan {
   std::vector<double> ent1_coef, ent2_coef;
   std::vector<int> ch_term_begin;             // size nch + 1
   std::vector<int> ch_nl;                     // light quarks of the sink pair
+  std::vector<GroupHdr> groups;
+  std::vector<int> group_ch;
+  std::vector<int> items;                     // pairs (term, k0)
   // flops of the contraction per q (complex multiply-adds), for rooflines
   double cmac_per_q = 0, gathers_per_q = 0;
 };

@@ -108,7 +108,7 @@ def channel_names():
 # ---- host-only plan introspection ---------------------------------------------
 
 PX = dict(TYPES=0, TYPETERMS=1, TYPECOEF=2, CELLS=3, TERMS=4, ENT1_CELL=5, ENT1_COEF=6, ENT2_CELL=7,
-          ENT2_COEF=8, CHANNELS=9)
+          ENT2_COEF=8, CHANNELS=9, GROUPS=10, GROUPCH=11, ITEMS=12)
 
 
 def plan_tables(channel_ids):
@@ -119,9 +119,9 @@ def plan_tables(channel_ids):
     p = ctypes.c_void_p()
     _check(L.nbs_plan_create(ctypes.byref(p), ids, len(channel_ids)))
     try:
-        s = (ctypes.c_longlong * 7)()
+        s = (ctypes.c_longlong * 9)()
         _check(L.nbs_plan_sizes(p, s))
-        ntypes, ncells, ntt, nterm, ne1, ne2, nch = list(s)
+        ntypes, ncells, ntt, nterm, ne1, ne2, nch, ngr, nit = list(s)
 
         def get(what, shape, dtype):
             a = np.zeros(shape, dtype=dtype)
@@ -133,7 +133,9 @@ def plan_tables(channel_ids):
             typecoef=get("TYPECOEF", (ntt,), np.float64), cells=get("CELLS", (ncells,), np.int32),
             terms=get("TERMS", (nterm, 8), np.int32), ent1_cell=get("ENT1_CELL", (ne1,), np.int32),
             ent1_coef=get("ENT1_COEF", (ne1,), np.float64), ent2_cell=get("ENT2_CELL", (ne2,), np.int32),
-            ent2_coef=get("ENT2_COEF", (ne2,), np.float64), channels=get("CHANNELS", (nch, 4), np.int32))
+            ent2_coef=get("ENT2_COEF", (ne2,), np.float64), channels=get("CHANNELS", (nch, 4), np.int32),
+            groups=get("GROUPS", (ngr, 24), np.int32), items=get("ITEMS", (nit, 2), np.int32),
+            group_ch=get("GROUPCH", (nch,), np.int32))
     finally:
         L.nbs_plan_destroy(p)
 

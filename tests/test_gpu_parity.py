@@ -30,12 +30,13 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-def gpu_correlate(nbs, ids, L, props, precision, t_range=None, host_out=False, c64=False):
+def gpu_correlate(nbs, ids, L, props, precision, t_range=None, host_out=False, c64=False, cfg=0):
     """props: list over t of (S_l, S_s) numpy complex128 arrays."""
     T = len(props)
     t0, t1 = t_range or (0, T)
     V = L ** 3
     with nbs.Context(L, T, precision=precision) as ctx:
+        ctx.set_param(ctx.PARAM_CONTRACT_CFG, cfg)
         for t, (Sl, Ss) in enumerate(props):
             dt = torch.complex64 if c64 else torch.complex128
             ctx.load_props(torch.from_numpy(Sl).to("cuda", dt), torch.from_numpy(Ss).to("cuda", dt), t)
@@ -112,6 +113,21 @@ def test_fp32_all_channels_L4(nbs):
         ref = oracle(names[c], *props[0], L)
         assert rel(F64[c, 0], ref) < FP64_TOL, names[c]
         assert rel(F32[c, 0], ref) < FP32_TOL, names[c]
+
+
+@pytest.mark.parametrize("cfg", [1, 22, 11])
+def test_contraction_variants_all_channels(nbs, cfg):
+    """Every contraction kernel and launch shape against the oracle, FP64 and FP32, all 52 channels."""
+    L = 3
+    props = seeded(1721, L, 1)
+    names = nbs.channel_names()
+    ids = list(range(len(names)))
+    F64 = gpu_correlate(nbs, ids, L, props, nbs.NBS_FP64, cfg=cfg)
+    F32 = gpu_correlate(nbs, ids, L, props, nbs.NBS_FP32, cfg=cfg)
+    for c in ids:
+        ref = oracle(names[c], *props[0], L)
+        assert rel(F64[c, 0], ref) < FP64_TOL, (cfg, names[c])
+        assert rel(F32[c, 0], ref) < FP32_TOL, (cfg, names[c])
 
 
 def test_host_output_and_timeslice_split(nbs):

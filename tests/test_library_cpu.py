@@ -70,6 +70,60 @@ def test_block_types_share_isospin_partners(lib):
     assert 4 * len(tb["cells"]) == 16416
 
 
+def test_gather_entries_stay_inside_their_slabs(lib):
+    """Every gather entry (padding included) reads a cell of its side's stored type."""
+    names = nbs.channel_names()
+    tb = nbs.plan_tables(list(range(52)))
+    types = tb["types"]
+    tpl = nbs.plan_tables([0])   # p/n type is type 0 in every plan
+    assert tpl["types"][0][0] == 0
+    # the stored type of each sink field, from a one-channel plan per field pair
+    for c, (ch, K, shape, n1, n2, off1, off2, local) in enumerate(tb["terms"]):
+        nh1 = 1 << ((shape & 1) + ((shape >> 1) & 1))
+        nh2 = 4 // nh1
+        cells1 = tb["ent1_cell"][off1:off1 + K * nh1 * n1]
+        cells2 = tb["ent2_cell"][off2:off2 + K * nh2 * n2]
+        for cells in (cells1, cells2):
+            t = np.searchsorted(types[:, 0], cells, side="right") - 1
+            assert (t == t[0]).all(), names[ch]
+            assert ((cells >= types[t, 0]) & (cells < types[t, 0] + types[t, 1])).all()
+        assert n1 % 2 == 0 and n2 % 2 == 0
+
+
+@pytest.mark.parametrize("ids", [list(range(52)), [0], [3, 17, 40]])
+def test_slab_work_split_covers_every_term_once(lib, ids):
+    """Re-run, on the host, the bookkeeping of the momentum-slab contraction:
+    every shared index of every term is visited once, by a warp whose
+    partial-sum slot range holds the term's channel, and every read stays
+    inside the group's two slabs."""
+    tb = nbs.plan_tables(ids)
+    W = 4
+    terms, items, groups, gch = tb["terms"], tb["items"], tb["groups"], tb["group_ch"]
+    seen = np.zeros(len(terms), dtype=int)
+    assert sorted(gch.tolist()) == list(range(len(ids)))
+    for g in groups:
+        base1, n1, base2, n2, ch_off, nch, item_off, nslot = g[:8]
+        warp_off, out_base, cfirst = g[8:13], g[13:18], g[18:22]
+        assert warp_off[0] == 0 and (np.diff(warp_off) >= 0).all() and out_base[W] == nslot
+        for w in range(W):
+            for it in range(item_off + warp_off[w], item_off + warp_off[w + 1]):
+                t, k0 = items[it]
+                ch, K, shape, nn1, nn2, off1, off2, local = terms[t]
+                assert gch[ch_off + local] == ch and 0 <= local < nch
+                r = local - cfirst[w]
+                assert 0 <= r < out_base[w + 1] - out_base[w]
+                assert k0 % 32 == 0 and k0 < K
+                seen[t] += min(32, K - k0)
+                nh1 = 1 << ((shape & 1) + ((shape >> 1) & 1))
+                nh2 = 4 // nh1
+                c1 = tb["ent1_cell"][off1 + k0 * nh1 * nn1: off1 + min(K, k0 + 32) * nh1 * nn1]
+                c2 = tb["ent2_cell"][off2 + k0 * nh2 * nn2: off2 + min(K, k0 + 32) * nh2 * nn2]
+                assert ((c1 >= base1) & (c1 < base1 + n1)).all()
+                assert ((c2 >= base2) & (c2 < base2 + n2)).all()
+                assert off1 % 2 == 0 and off2 % 2 == 0
+    assert (seen == terms[:, 1]).all()
+
+
 def test_worked_counts_pn(lib):
     tb = nbs.plan_tables([0])
     terms = tb["terms"]
