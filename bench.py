@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--T", type=int, default=T_DEFAULT)
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--contract-cfg", type=int, default=0, help="NBS_PARAM_CONTRACT_CFG (kernel / launch shape)")
+    ap.add_argument("--qblock", type=int, default=0, help="NBS_PARAM_CHUNK_QBLOCK (0 = library default)")
     return ap.parse_args()
 
 
@@ -243,6 +245,9 @@ def run_ours(args, rank, world, local_rank):
     host_props = make_props_host(L, T, seed)
 
     ctx = P.Context(L, T, precision=prec)
+    ctx.set_param(ctx.PARAM_CONTRACT_CFG, args.contract_cfg)
+    if args.qblock:
+        ctx.set_param(ctx.PARAM_CHUNK_QBLOCK, args.qblock)
     for t, (Sl, Ss) in enumerate(host_props):
         ctx.load_props(torch.from_numpy(Sl).cuda(), torch.from_numpy(Ss).cuda(), t)
     out = torch.empty((nch, 1, 4, 4, 2, 2, V), dtype=torch.complex128, device="cuda")

@@ -103,13 +103,20 @@ int nbs_correlate(nbs_ctx* h, const int* channel_ids, int n_channels,
 int nbs_zero_momentum(nbs_ctx* h, double* out);
 
 /* Launch-shape parameters (for tuning; results agree to rounding).
- * NBS_PARAM_CONTRACT_CFG selects the contraction kernel: 0 = default
- * (thread-per-momentum kernel, A = 4, W = 2 in FP32; A = 2, W = 1 in FP64);
- * 1 = the momentum-slab kernel (one block per momentum and channel group,
- * stored blocks staged in shared memory); A*10 + W = the thread-per-momentum
- * kernel with A sink spins alpha1 per thread (1, 2 or 4) and W warps per
- * block (1, 2 or 4).  NBS_EINVAL for any other value. */
+ * NBS_PARAM_CONTRACT_CFG selects the contraction kernel:
+ *   0 = default: the chunk kernel in FP32 (when the channel tables fit its
+ *       shared memory), the thread-per-momentum kernel (A = 2, W = 1) in FP64;
+ *   1 = the momentum-slab kernel (one block per momentum and channel group,
+ *       stored blocks staged in shared memory);
+ *   2 = the chunk kernel (FP32; persistent blocks that keep a chunk of
+ *       channels' compressed gather tables in shared memory and sweep a block
+ *       of momenta with double-buffered slabs), else the default;
+ *   A*10 + W = the thread-per-momentum kernel with A sink spins alpha1 per
+ *       thread (1, 2 or 4) and W warps per block (1, 2 or 4).
+ * NBS_EINVAL for any other value. */
 #define NBS_PARAM_CONTRACT_CFG 0
+/* NBS_PARAM_CHUNK_QBLOCK: momenta per block of the chunk contraction (default 64). */
+#define NBS_PARAM_CHUNK_QBLOCK 1
 int nbs_set_param(nbs_ctx* h, int param, int value);
 
 /* Profiling (stage timing with CUDA events on the context's stream).
@@ -176,7 +183,10 @@ int nbs_plan_destroy(nbs_plan* p);
 #define NBS_PS_NCH        6   /* channels                                    */
 #define NBS_PS_NGROUPS    7   /* slab groups                                 */
 #define NBS_PS_NITEMS     8   /* slab work items                             */
-#define NBS_PLAN_NSIZES   9
+#define NBS_PS_NCHUNKS    9   /* table chunks (0 when the chunk kernel cannot run) */
+#define NBS_PS_NCHUNKTAB 10   /* 16-bit chunk-table entries                  */
+#define NBS_PS_NCHUNKITEMS 11 /* chunk work items                            */
+#define NBS_PLAN_NSIZES  12
 int nbs_plan_sizes(const nbs_plan* p, long long* sizes);
 /* what: NBS_PX_* ; dst must hold the documented number of int32/double */
 #define NBS_PX_TYPES      0   /* int32 [ntypes][4]: cell_off, ncell, term_off, nterm   */
@@ -193,6 +203,13 @@ int nbs_plan_sizes(const nbs_plan* p, long long* sizes);
                                  item_off, nslot, warp_off[5], out_base[5], cfirst[4], 0, 0 */
 #define NBS_PX_GROUPCH   11   /* int32 [sum of nch]: request-order channel of each group slot */
 #define NBS_PX_ITEMS     12   /* int32 [nitems][2]: term, first shared index                 */
+#define NBS_PX_CHUNKS    13   /* int32 [nchunks][40]: base1, ncell1, base2, ncell2, ch_off, nch,
+                                 tab_off, tab_len, item_off, nslot, warp_off[9], out_base[9],
+                                 cfirst[8], ch_local0, 0, 0, 0 */
+#define NBS_PX_CHUNKTAB  14   /* uint16 [nchunktab]: cell - base | sign << 10 | code << 11   */
+#define NBS_PX_CHUNKITEMS 15  /* int32 [nchunkitems][2]: term, first shared index            */
+#define NBS_PX_TERMTABOFF 16  /* int32 [nterms][2]: side-1, side-2 offset in the chunk table */
+#define NBS_PX_CODES     17   /* double [32]: |coefficient| of each code (code 31 = 0)       */
 int nbs_plan_export(const nbs_plan* p, int what, void* dst);
 
 #ifdef __cplusplus

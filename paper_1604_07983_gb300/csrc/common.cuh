@@ -82,6 +82,13 @@ cudaError_t launch_contract_slab(const C<T>* FB, int L, int ngroups, const void*
                                  int st2, int max_nch, C<T>* Ft, cudaStream_t st);
 template <typename T>
 size_t slab_smem_bytes(int st1, int st2, int max_nch);
+// persistent chunk contraction (FP32); chunks points to ChunkHdr[nchunks] (plan.h),
+// codes: device array of 32 floats (|coefficient| per code, code 31 = 0)
+size_t chunk_smem_bytes(int st1, int st2, int max_slot, int max_tab);
+cudaError_t launch_contract_chunk(const float2* FB, int L, int nchunks, int qb, const void* chunks, const int* group_ch,
+                                  const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
+                                  const float* codes, int st1, int st2, int max_slot, int max_tab, float2* Ft,
+                                  cudaStream_t st);
 template <typename T>
 cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_nl, const int* exps,
                            double2* out, long long ch_stride, cudaStream_t st);

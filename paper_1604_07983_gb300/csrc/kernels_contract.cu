@@ -425,6 +425,237 @@ __global__ void __launch_bounds__(NW * 32) k_contract_slab(const C<T>* __restric
   }
 }
 
+// ---- persistent chunk contraction (FP32) -----------------------------------------
+//
+// A CTA owns one chunk (whole channels of a slab group whose gather tables,
+// 16 bits per entry, fit in shared memory) and a block of consecutive
+// momenta.  It loads the chunk's table once, then for each momentum waits for
+// the two slabs (prefetched with cp.async into the other half of a double
+// buffer while the previous momentum was being contracted), builds the
+// effective blocks from shared memory and accumulates their products.
+// Lane l owns shared index k0 + (l >> 1) and the sink spins alpha1 of pair
+// (l & 1), so the two lanes reading the same B2 cell sit in one quarter-warp
+// and their loads are one broadcast.
+
+template <int NH>
+__device__ __forceinline__ void load_codes(const unsigned short* p, unsigned (&e)[2 * NH]) {
+  if constexpr (NH == 1) {
+    const unsigned w = *reinterpret_cast<const unsigned*>(p);
+    e[0] = w & 0xffffu; e[1] = w >> 16;
+  } else if constexpr (NH == 2) {
+    const uint2 w = *reinterpret_cast<const uint2*>(p);
+    e[0] = w.x & 0xffffu; e[1] = w.x >> 16; e[2] = w.y & 0xffffu; e[3] = w.y >> 16;
+  } else {
+    const uint4 w = *reinterpret_cast<const uint4*>(p);
+    e[0] = w.x & 0xffffu; e[1] = w.x >> 16; e[2] = w.y & 0xffffu; e[3] = w.y >> 16;
+    e[4] = w.z & 0xffffu; e[5] = w.z >> 16; e[6] = w.w & 0xffffu; e[7] = w.w >> 16;
+  }
+}
+
+__device__ __forceinline__ float decode_coef(unsigned e, const float* codes) {
+  const float a = codes[e >> 11];
+  return (e & 1024u) ? -a : a;
+}
+
+template <int SHAPE>
+__device__ __forceinline__ void chunk_item(const DevTerm& h, int k, bool active, int ag, const unsigned short* T1,
+                                           const unsigned short* T2, const uint4* S1, int st1, const uint4* S2,
+                                           int st2, const float* cc, float (&acc)[64]) {
+  constexpr int NH1 = 1 << ((SHAPE & 1) + ((SHAPE >> 1) & 1));
+  constexpr int NH2 = 4 / NH1;
+  float2 v1[NH1][2], v2[NH2][4];
+#pragma unroll
+  for (int hh = 0; hh < NH1; ++hh) v1[hh][0] = v1[hh][1] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int hh = 0; hh < NH2; ++hh)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) v2[hh][b] = make_float2(0.f, 0.f);
+  if (active) {
+    const unsigned short* p1 = T1 + k * NH1 * h.n1;
+    for (int i = 0; i < h.n1; i += 2, p1 += 2 * NH1) {
+      unsigned e[2 * NH1];
+      load_codes<NH1>(p1, e);
+#pragma unroll
+      for (int j = 0; j < 2 * NH1; ++j) {
+        const float c = decode_coef(e[j], cc);
+        const float4 x = *reinterpret_cast<const float4*>(S1 + ag * st1 + (e[j] & 1023u));
+        v1[j % NH1][0].x = fmaf(c, x.x, v1[j % NH1][0].x);
+        v1[j % NH1][0].y = fmaf(c, x.y, v1[j % NH1][0].y);
+        v1[j % NH1][1].x = fmaf(c, x.z, v1[j % NH1][1].x);
+        v1[j % NH1][1].y = fmaf(c, x.w, v1[j % NH1][1].y);
+      }
+    }
+    const unsigned short* p2 = T2 + k * NH2 * h.n2;
+    for (int i = 0; i < h.n2; i += 2, p2 += 2 * NH2) {
+      unsigned e[2 * NH2];
+      load_codes<NH2>(p2, e);
+#pragma unroll
+      for (int j = 0; j < 2 * NH2; ++j) {
+        const float c = decode_coef(e[j], cc);
+        const unsigned cell = e[j] & 1023u;
+        const float4 x = *reinterpret_cast<const float4*>(S2 + cell);
+        const float4 y = *reinterpret_cast<const float4*>(S2 + st2 + cell);
+        crfma<float>(v2[j % NH2][0], c, make_float2(x.x, x.y));
+        crfma<float>(v2[j % NH2][1], c, make_float2(x.z, x.w));
+        crfma<float>(v2[j % NH2][2], c, make_float2(y.x, y.y));
+        crfma<float>(v2[j % NH2][3], c, make_float2(y.z, y.w));
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int h1 = 0; h1 < NH1; ++h1)
+#pragma unroll
+        for (int h2 = 0; h2 < NH2; ++h2) {
+          int s;  // alpha3 + 2 alpha4
+          if (SHAPE == 0) s = h2;
+          else if (SHAPE == 3) s = h1;
+          else if (SHAPE == 1) s = h1 + 2 * h2;
+          else s = h2 + 2 * h1;
+          const int m = (a * 4 + b) * 4 + s;
+          float2 z = make_float2(acc[2 * m], acc[2 * m + 1]);
+          cfma<float>(z, v1[h1][a], v2[h2][b]);
+          acc[2 * m] = z.x;
+          acc[2 * m + 1] = z.y;
+        }
+}
+
+// reduce 64 values over the 16 lanes of one spin pair (xor masks 16, 8, 4, 2);
+// lane l ends with the sums of acc[4 (l >> 1) .. 4 (l >> 1) + 3]
+template <int M>
+__device__ __forceinline__ void pair_reduce_stage(float (&acc)[64], int lane) {
+  if constexpr (M >= 2) {
+    constexpr int n = 2 * M;  // kept length after this stage
+    const bool up = lane & M;
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+      const float keep = up ? acc[n + j] : acc[j];
+      const float give = up ? acc[j] : acc[n + j];
+      acc[j] = keep + __shfl_xor_sync(0xffffffffu, give, M);
+    }
+    pair_reduce_stage<M / 2>(acc, lane);
+  }
+}
+
+__device__ __forceinline__ void cp_async16b(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, 1) k_contract_chunk(
+    const float2* __restrict__ FB, int L, int nchunks, int qb, const ChunkHdr* __restrict__ chunks,
+    const int* __restrict__ group_ch, const int* __restrict__ items, const DevTerm* __restrict__ terms,
+    const int* __restrict__ tab_off, const unsigned short* __restrict__ tab, const float* __restrict__ codes, int st1,
+    int st2,
+    int max_slot, int max_tab, float2* __restrict__ Ft) {
+  constexpr int NT = NW * 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned short* TAB = reinterpret_cast<unsigned short*>(smem_raw);
+  uint4* SB = reinterpret_cast<uint4*>(smem_raw + (size_t)max_tab * 2);  // max_tab is a multiple of 8
+  const int slab = 2 * st1 + 2 * st2;                                     // uint4 per buffer
+  float2* OUT = reinterpret_cast<float2*>(SB + 2 * slab);
+  float* CODES = reinterpret_cast<float*>(OUT + max_slot * 64);
+  if (threadIdx.x < 32) CODES[threadIdx.x] = codes[threadIdx.x];
+  const long long V = (long long)L * L * L;
+  const int ci = blockIdx.x % nchunks;
+  const long long q_begin = (long long)(blockIdx.x / nchunks) * qb;
+  const long long q_end = min(V, q_begin + qb);
+  const ChunkHdr& ck = chunks[ci];
+  const int base1 = ck.base1, n1 = ck.ncell1, base2 = ck.base2, n2 = ck.ncell2;
+
+  auto issue_slabs = [&](long long q, uint4* S) {
+    const int qx = (int)(q % L), qy = (int)((q / L) % L), qz = (int)(q / ((long long)L * L));
+    const long long qm = (L - qx) % L + L * ((L - qy) % L + (long long)L * ((L - qz) % L));
+    for (int i = threadIdx.x; i < 2 * n1; i += NT) {
+      const int c = i >> 1, p = i & 1;
+      cp_async16b(S + p * st1 + c, reinterpret_cast<const char*>(FB + ((long long)(base1 + c) * V + q) * 4) + 16 * p);
+    }
+    uint4* S2 = S + 2 * st1;
+    for (int i = threadIdx.x; i < 2 * n2; i += NT) {
+      const int c = i >> 1, p = i & 1;
+      cp_async16b(S2 + p * st2 + c, reinterpret_cast<const char*>(FB + ((long long)(base2 + c) * V + qm) * 4) + 16 * p);
+    }
+  };
+
+  for (int i = threadIdx.x; i < ck.tab_len / 8; i += NT)
+    cp_async16b(TAB + 8 * i, tab + ck.tab_off + 8 * i);
+  if (q_begin < q_end) issue_slabs(q_begin, SB);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (int i = threadIdx.x; i < ck.nslot * 64; i += NT) OUT[i] = make_float2(0.f, 0.f);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ag = lane & 1, kk = lane >> 1;
+  const int it0 = ck.item_off + ck.warp_off[w], it1 = ck.item_off + ck.warp_off[w + 1];
+  for (long long q = q_begin; q < q_end; ++q) {
+    uint4* S = SB + ((q - q_begin) & 1) * slab;
+    if (q + 1 < q_end) issue_slabs(q + 1, SB + ((q + 1 - q_begin) & 1) * slab);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    const uint4* S1 = S;
+    const uint4* S2 = S + 2 * st1;
+    float acc[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+    int cur = -1;
+    for (int it = it0; it < it1; ++it) {
+      const int term = items[2 * it], k0 = items[2 * it + 1];
+      const DevTerm h = terms[term];
+      const int local = h.pad - ck.ch_local0;
+      if (local != cur) {
+        if (cur >= 0) {
+          pair_reduce_stage<16>(acc, lane);
+          float2* o = OUT + (ck.out_base[w] + cur - ck.cfirst[w]) * 64 + ag * 32 + 2 * kk;
+          o[0].x += acc[0]; o[0].y += acc[1]; o[1].x += acc[2]; o[1].y += acc[3];
+#pragma unroll
+          for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+        }
+        cur = local;
+      }
+      const unsigned short* T1 = TAB + tab_off[2 * term];
+      const unsigned short* T2 = TAB + tab_off[2 * term + 1];
+      for (int kb = 0; kb < 32 && k0 + kb < h.K; kb += 16) {
+        const int k = k0 + kb + kk;
+        const bool active = k < h.K;
+        switch (h.shape) {
+          case 0: chunk_item<0>(h, k, active, ag, T1, T2, S1, st1, S2, st2, CODES, acc); break;
+          case 1: chunk_item<1>(h, k, active, ag, T1, T2, S1, st1, S2, st2, CODES, acc); break;
+          case 2: chunk_item<2>(h, k, active, ag, T1, T2, S1, st1, S2, st2, CODES, acc); break;
+          default: chunk_item<3>(h, k, active, ag, T1, T2, S1, st1, S2, st2, CODES, acc); break;
+        }
+      }
+    }
+    if (cur >= 0) {
+      pair_reduce_stage<16>(acc, lane);
+      float2* o = OUT + (ck.out_base[w] + cur - ck.cfirst[w]) * 64 + ag * 32 + 2 * kk;
+      o[0].x += acc[0]; o[0].y += acc[1]; o[1].x += acc[2]; o[1].y += acc[3];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ck.nch * 64; i += NT) {
+      const int c = i / 64, m = i % 64;
+      float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int ww = 0; ww < NW; ++ww) {  // fixed order
+        const int r = c - ck.cfirst[ww];
+        if (r >= 0 && r < ck.out_base[ww + 1] - ck.out_base[ww]) {
+          float2& v = OUT[(ck.out_base[ww] + r) * 64 + m];
+          sum.x += v.x;
+          sum.y += v.y;
+          v = make_float2(0.f, 0.f);
+        }
+      }
+      const int spin = (m & ~3) + 2 * (m & 1) + ((m >> 1) & 1);
+      Ft[((long long)group_ch[ck.ch_off + c] * 64 + spin) * V + q] = sum;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+  }
+}
+
 // out[ch * ch_stride + c*V + r] = Ft[ch][c][r] * 2^(e_l n_l + e_s n_s) / V   (FP64)
 template <typename T>
 __global__ void __launch_bounds__(256) k_restore(const C<T>* __restrict__ Ft, long long V, const int* __restrict__ ch_nl,
@@ -488,6 +719,27 @@ cudaError_t launch_contract_slab(const C<T>* FB, int L, int ngroups, const void*
   if (nblk > 2147483647LL) return cudaErrorInvalidValue;
   kern<<<(unsigned)nblk, NBS_SLAB_WARPS * 32, sm, st>>>(FB, L, ngroups, (const GroupHdr*)groups, group_ch, items,
                                                        terms, e1, e2, st1, st2, max_slot, Ft);
+  return cudaGetLastError();
+}
+
+size_t chunk_smem_bytes(int st1, int st2, int max_slot, int max_tab) {
+  return (size_t)max_tab * 2 + (size_t)2 * (2 * st1 + 2 * st2) * 16 + (size_t)max_slot * 64 * sizeof(float2) + 128;
+}
+
+cudaError_t launch_contract_chunk(const float2* FB, int L, int nchunks, int qb, const void* chunks, const int* group_ch,
+                                  const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
+                                  const float* codes, int st1, int st2, int max_slot, int max_tab, float2* Ft,
+                                  cudaStream_t st) {
+  const long long V = (long long)L * L * L;
+  const size_t sm = chunk_smem_bytes(st1, st2, max_slot, max_tab);
+  auto kern = k_contract_chunk<NBS_CHUNK_WARPS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const long long nqb = (V + qb - 1) / qb;
+  if (nqb * nchunks > 2147483647LL || max_tab % 8) return cudaErrorInvalidValue;
+  kern<<<(unsigned)(nqb * nchunks), NBS_CHUNK_WARPS * 32, sm, st>>>(FB, L, nchunks, qb, (const ChunkHdr*)chunks,
+                                                                    group_ch, items, terms, tab_off, tab, codes, st1, st2,
+                                                                    max_slot, max_tab, Ft);
   return cudaGetLastError();
 }
 

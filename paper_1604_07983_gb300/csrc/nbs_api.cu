@@ -83,6 +83,9 @@ struct nbs_ctx {
   int plan_gen = 0;
   DevBuf d_terms, d_chtb, d_chnl, d_e1, d_e2, d_cells, d_groups, d_gch, d_items;
   int slab_st1 = 0, slab_st2 = 0, slab_nch = 0;
+  DevBuf d_chunks, d_ctab, d_citems, d_ctoff, d_codes;
+  int chunk_st1 = 0, chunk_st2 = 0, chunk_slot = 0, chunk_tab = 0;
+  int chunk_qb = 64;
   int tables_mode = -1;
   TypeRecipeSet recipes;
 
@@ -186,6 +189,28 @@ int upload_tables(nbs_ctx* h) {
   if ((rc = ensure(h, h->d_groups, std::max<size_t>(P.groups.size(), 1) * sizeof(GroupHdr), "groups"))) return rc;
   if ((rc = ensure(h, h->d_gch, std::max<size_t>(P.group_ch.size(), 1) * sizeof(int), "group channels"))) return rc;
   if ((rc = ensure(h, h->d_items, std::max<size_t>(P.items.size(), 1) * sizeof(int), "work items"))) return rc;
+  if (P.chunks_ok) {
+    h->chunk_st1 = h->chunk_st2 = h->chunk_slot = h->chunk_tab = 0;
+    for (const ChunkHdr& c : P.chunks) {
+      h->chunk_st1 = std::max(h->chunk_st1, c.ncell1);
+      h->chunk_st2 = std::max(h->chunk_st2, c.ncell2);
+      h->chunk_slot = std::max(h->chunk_slot, c.nslot);
+      h->chunk_tab = std::max(h->chunk_tab, c.tab_len);
+    }
+    float codes[32] = {};
+    for (size_t i = 0; i < P.coef_codes.size() && i < 31; ++i) codes[i] = (float)P.coef_codes[i];
+    if ((rc = ensure(h, h->d_chunks, std::max<size_t>(P.chunks.size(), 1) * sizeof(ChunkHdr), "chunks"))) return rc;
+    if ((rc = ensure(h, h->d_ctab, std::max<size_t>(P.chunk_tab.size(), 8) * 2, "chunk tables"))) return rc;
+    if ((rc = ensure(h, h->d_citems, std::max<size_t>(P.chunk_items.size(), 1) * sizeof(int), "chunk items"))) return rc;
+    if ((rc = ensure(h, h->d_ctoff, std::max<size_t>(P.term_tab_off.size(), 1) * sizeof(int), "table offsets"))) return rc;
+    if ((rc = ensure(h, h->d_codes, sizeof(codes), "coefficient codes"))) return rc;
+    CK(cudaMemcpyAsync(h->d_chunks.p, P.chunks.data(), P.chunks.size() * sizeof(ChunkHdr), cudaMemcpyHostToDevice, h->st), "upload chunks");
+    CK(cudaMemcpyAsync(h->d_ctab.p, P.chunk_tab.data(), P.chunk_tab.size() * 2, cudaMemcpyHostToDevice, h->st), "upload chunk tables");
+    CK(cudaMemcpyAsync(h->d_citems.p, P.chunk_items.data(), P.chunk_items.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload chunk items");
+    CK(cudaMemcpyAsync(h->d_ctoff.p, P.term_tab_off.data(), P.term_tab_off.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload table offsets");
+    CK(cudaMemcpyAsync(h->d_codes.p, codes, sizeof(codes), cudaMemcpyHostToDevice, h->st), "upload codes");
+    CK(cudaStreamSynchronize(h->st), "upload sync");
+  }
   CK(cudaMemcpyAsync(h->d_groups.p, P.groups.data(), P.groups.size() * sizeof(GroupHdr), cudaMemcpyHostToDevice, h->st), "upload groups");
   CK(cudaMemcpyAsync(h->d_gch.p, P.group_ch.data(), P.group_ch.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload group channels");
   CK(cudaMemcpyAsync(h->d_items.p, P.items.data(), P.items.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload items");
@@ -316,16 +341,26 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
       if ((rc = build_blocks<T>(h, t))) return rc;
     }
     cudaEvent_t e3 = stage_begin(h);
-    if (h->contract_cfg == 1) {
+    // default in FP32: the chunk kernel when the tables fit; FP64: the thread-per-momentum kernel
+    const bool use_chunk = (h->contract_cfg == 2 || h->contract_cfg == 0) && sizeof(T) == 4 && h->plan.chunks_ok;
+    if (use_chunk) {
+      CK(launch_contract_chunk((const float2*)h->FB.p, h->L, (int)h->plan.chunks.size(), h->chunk_qb, h->d_chunks.p,
+                               (const int*)h->d_gch.p, (const int*)h->d_citems.p, (const DevTerm*)h->d_terms.p,
+                               (const int*)h->d_ctoff.p, (const unsigned short*)h->d_ctab.p,
+                               (const float*)h->d_codes.p, h->chunk_st1, h->chunk_st2, h->chunk_slot, h->chunk_tab,
+                               (float2*)h->Ft.p, h->st),
+         "contraction");
+    } else if (h->contract_cfg == 1) {
       CK(launch_contract_slab<T>((const C<T>*)h->FB.p, h->L, (int)h->plan.groups.size(), h->d_groups.p,
                                  (const int*)h->d_gch.p, (const int*)h->d_items.p, (const DevTerm*)h->d_terms.p,
                                  (const Ent<T>*)h->d_e1.p, (const Ent<T>*)h->d_e2.p, h->slab_st1, h->slab_st2,
                                  h->slab_nch, (C<T>*)h->Ft.p, h->st),
          "contraction");
     } else {
+      // configs 1 and 2 name other kernels; where the chunk kernel cannot run (FP64) use the default shape
+      const int cfg = h->contract_cfg <= 2 ? 0 : h->contract_cfg;
       CK(launch_contract<T>((const C<T>*)h->FB.p, h->L, (const DevTerm*)h->d_terms.p, (const int*)h->d_chtb.p, nch,
-                            (const Ent<T>*)h->d_e1.p, (const Ent<T>*)h->d_e2.p, (C<T>*)h->Ft.p, h->contract_cfg,
-                            h->st),
+                            (const Ent<T>*)h->d_e1.p, (const Ent<T>*)h->d_e2.p, (C<T>*)h->Ft.p, cfg, h->st),
          "contraction");
     }
     stage_end(h, 3, e3);
@@ -434,7 +469,7 @@ int nbs_destroy(nbs_ctx* h) {
   if (h->cst) cudaStreamSynchronize(h->cst);
   DevBuf* bufs[] = {&h->props, &h->propsT, &h->Q, &h->FB, &h->Ft, &h->zm, &h->small, &h->stage[0], &h->stage[1],
                     &h->d_terms, &h->d_chtb, &h->d_chnl, &h->d_e1, &h->d_e2, &h->d_cells, &h->d_groups,
-                    &h->d_gch, &h->d_items};
+                    &h->d_gch, &h->d_items, &h->d_chunks, &h->d_ctab, &h->d_citems, &h->d_ctoff, &h->d_codes};
   for (DevBuf* b : bufs) dev_free(b->p, h->free_fn, h->free_user);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   for (int b = 0; b < 2; ++b) {
@@ -508,11 +543,15 @@ int nbs_set_param(nbs_ctx* h, int param, int value) {
   switch (param) {
     case NBS_PARAM_CONTRACT_CFG: {
       const int a = value / 10, w = value % 10;
-      if (value != 0 && value != 1 && !((a == 1 || a == 2 || a == 4) && (w == 1 || w == 2 || w == 4)))
-        return fail(h, NBS_EINVAL, "contraction config must be 0, 1 or A*10+W with A, W in {1, 2, 4}");
+      if (value != 0 && value != 1 && value != 2 && !((a == 1 || a == 2 || a == 4) && (w == 1 || w == 2 || w == 4)))
+        return fail(h, NBS_EINVAL, "contraction config must be 0, 1, 2 or A*10+W with A, W in {1, 2, 4}");
       h->contract_cfg = value;
       return NBS_OK;
     }
+    case NBS_PARAM_CHUNK_QBLOCK:
+      if (value < 1 || value > (1 << 20)) return fail(h, NBS_EINVAL, "momentum block must be in [1, 2^20]");
+      h->chunk_qb = value;
+      return NBS_OK;
     default: return fail(h, NBS_EINVAL, "unknown parameter");
   }
 }
@@ -608,6 +647,9 @@ int nbs_plan_sizes(const nbs_plan* p, long long* s) {
   s[NBS_PS_NCH] = (long long)P.channels.size();
   s[NBS_PS_NGROUPS] = (long long)P.groups.size();
   s[NBS_PS_NITEMS] = (long long)P.items.size() / 2;
+  s[NBS_PS_NCHUNKS] = P.chunks_ok ? (long long)P.chunks.size() : 0;
+  s[NBS_PS_NCHUNKTAB] = (long long)P.chunk_tab.size();
+  s[NBS_PS_NCHUNKITEMS] = (long long)P.chunk_items.size() / 2;
   return NBS_OK;
 }
 
@@ -657,6 +699,16 @@ int nbs_plan_export(const nbs_plan* p, int what, void* dst) {
       return NBS_OK;
     case NBS_PX_GROUPCH: std::memcpy(I, P.group_ch.data(), P.group_ch.size() * sizeof(int)); return NBS_OK;
     case NBS_PX_ITEMS: std::memcpy(I, P.items.data(), P.items.size() * sizeof(int)); return NBS_OK;
+    case NBS_PX_CHUNKS:
+      static_assert(sizeof(ChunkHdr) == 40 * sizeof(int), "chunk header layout");
+      if (P.chunks_ok) std::memcpy(I, P.chunks.data(), P.chunks.size() * sizeof(ChunkHdr));
+      return NBS_OK;
+    case NBS_PX_CHUNKTAB: std::memcpy(dst, P.chunk_tab.data(), P.chunk_tab.size() * 2); return NBS_OK;
+    case NBS_PX_CHUNKITEMS: std::memcpy(I, P.chunk_items.data(), P.chunk_items.size() * sizeof(int)); return NBS_OK;
+    case NBS_PX_TERMTABOFF: std::memcpy(I, P.term_tab_off.data(), P.term_tab_off.size() * sizeof(int)); return NBS_OK;
+    case NBS_PX_CODES:
+      for (int i = 0; i < 32; ++i) D[i] = i < (int)P.coef_codes.size() && i < 31 ? P.coef_codes[i] : 0.0;
+      return NBS_OK;
     default: return fail(nullptr, NBS_EINVAL, "unknown export");
   }
 }

@@ -242,6 +242,123 @@ const std::vector<ChannelDef>& channel_table() {
   return table;
 }
 
+namespace {
+
+// Split every slab group into chunks of whole channels whose compressed
+// tables fit NBS_CHUNK_ENTRIES, and balance each chunk's items over warps.
+void build_chunks(Plan& plan) {
+  plan.chunks.clear();
+  plan.chunk_tab.clear();
+  plan.chunk_items.clear();
+  plan.term_tab_off.assign(2 * plan.terms.size(), 0);
+  plan.coef_codes.clear();
+  plan.chunks_ok = false;
+  auto code_of = [&](double c) -> int {
+    const double a = std::fabs(c);
+    for (size_t i = 0; i < plan.coef_codes.size(); ++i)
+      if (std::fabs(plan.coef_codes[i] - a) <= 1e-12 * std::max(1.0, a)) return (int)i;
+    plan.coef_codes.push_back(a);
+    return (int)plan.coef_codes.size() - 1;
+  };
+  auto term_entries = [&](const TermHdr& th) {
+    const int nh1 = 1 << ((th.shape & 1) + (th.shape >> 1 & 1)), nh2 = 4 / nh1;
+    auto pad8 = [](int n) { return (n + 7) / 8 * 8; };
+    return pad8(th.K * nh1 * th.n1) + pad8(th.K * nh2 * th.n2);
+  };
+  for (const GroupHdr& g : plan.groups) {
+    if (g.ncell1 > 1024 || g.ncell2 > 1024) return;
+    int c = 0;
+    while (c < g.nch) {
+      // take whole channels while the table fits
+      int c_end = c, len = 0;
+      while (c_end < g.nch) {
+        const int ci = plan.group_ch[g.ch_off + c_end];
+        int n = 0;
+        for (int t = plan.ch_term_begin[ci]; t < plan.ch_term_begin[ci + 1]; ++t) n += term_entries(plan.terms[t]);
+        if (len + n > NBS_CHUNK_ENTRIES) break;
+        len += n;
+        ++c_end;
+      }
+      if (c_end == c) return;  // one channel alone exceeds a chunk
+      ChunkHdr ck = {};
+      ck.base1 = g.base1; ck.ncell1 = g.ncell1; ck.base2 = g.base2; ck.ncell2 = g.ncell2;
+      ck.ch_off = g.ch_off + c;
+      ck.nch = c_end - c;
+      ck.ch_local0 = c;
+      ck.tab_off = (int)plan.chunk_tab.size();
+      ck.item_off = (int)plan.chunk_items.size() / 2;
+      std::vector<std::pair<int, int>> its;
+      std::vector<double> cost;
+      for (int local = c; local < c_end; ++local) {
+        const int ci = plan.group_ch[g.ch_off + local];
+        for (int t = plan.ch_term_begin[ci]; t < plan.ch_term_begin[ci + 1]; ++t) {
+          const TermHdr& th = plan.terms[t];
+          const int nh1 = 1 << ((th.shape & 1) + (th.shape >> 1 & 1)), nh2 = 4 / nh1;
+          for (int side = 0; side < 2; ++side) {
+            const int n = side == 0 ? th.K * nh1 * th.n1 : th.K * nh2 * th.n2;
+            const int off = side == 0 ? th.off1 : th.off2;
+            const int base = side == 0 ? g.base1 : g.base2;
+            const auto& cells = side == 0 ? plan.ent1_cell : plan.ent2_cell;
+            const auto& coefs = side == 0 ? plan.ent1_coef : plan.ent2_coef;
+            plan.term_tab_off[2 * t + side] = (int)plan.chunk_tab.size() - ck.tab_off;
+            for (int i = 0; i < n; ++i) {
+              const int cell = cells[off + i] - base;
+              const double cf = coefs[off + i];
+              if (cell < 0 || cell >= 1024) return;
+              int code = 31;  // code 31: zero coefficient (padding)
+              if (cf != 0.0) {
+                code = code_of(cf);
+                if (code >= 31) return;
+              }
+              plan.chunk_tab.push_back((unsigned short)(cell | ((cf < 0) << 10) | (code << 11)));
+            }
+            while ((plan.chunk_tab.size() - ck.tab_off) % 8) plan.chunk_tab.push_back((unsigned short)(0x1F << 11));
+          }
+          for (int k0 = 0; k0 < th.K; k0 += 32) {
+            its.push_back({t, k0});
+            cost.push_back(64.0 + 4.0 * (nh1 * th.n1 + nh2 * th.n2));
+          }
+        }
+      }
+      ck.tab_len = (int)plan.chunk_tab.size() - ck.tab_off;
+      double total = 0;
+      for (double x : cost) total += x;
+      int w = 0;
+      double acc = 0;
+      ck.warp_off[0] = 0;
+      for (size_t i = 0; i < its.size(); ++i) {
+        acc += cost[i];
+        if (w < NBS_CHUNK_WARPS - 1 && acc >= total * (w + 1) / NBS_CHUNK_WARPS) ck.warp_off[++w] = (int)i + 1;
+      }
+      while (w < NBS_CHUNK_WARPS) ck.warp_off[++w] = (int)its.size();
+      ck.out_base[0] = 0;
+      for (int ww = 0; ww < NBS_CHUNK_WARPS; ++ww) {
+        int n = 0;
+        ck.cfirst[ww] = 0;
+        if (ck.warp_off[ww + 1] > ck.warp_off[ww]) {
+          const int c0 = plan.terms[its[ck.warp_off[ww]].first].pad - c;
+          const int c1 = plan.terms[its[ck.warp_off[ww + 1] - 1].first].pad - c;
+          ck.cfirst[ww] = c0;
+          n = c1 - c0 + 1;
+        }
+        ck.out_base[ww + 1] = ck.out_base[ww] + n;
+      }
+      ck.nslot = ck.out_base[NBS_CHUNK_WARPS];
+      for (auto& it : its) {
+        plan.chunk_items.push_back(it.first);
+        plan.chunk_items.push_back(it.second);
+      }
+      plan.chunks.push_back(ck);
+      c = c_end;
+    }
+  }
+  // code 31 is reserved for zero coefficients
+  if (plan.coef_codes.size() > 31) return;
+  plan.chunks_ok = true;
+}
+
+}  // namespace
+
 std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
   plan = Plan();
   const auto& table = channel_table();
@@ -550,6 +667,7 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
       plan.groups.push_back(g);
     }
   }
+  build_chunks(plan);
   return "";
 }
 

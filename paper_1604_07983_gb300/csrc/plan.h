@@ -50,6 +50,25 @@ struct GroupHdr {
   int pad[2];
 };
 
+// Persistent slab contraction: the channels of a group are split into chunks
+// whose gather tables, compressed to 16 bits per entry (cell - type base in
+// bits 0..9, sign in bit 10, coefficient code in bits 11..15), fit in shared
+// memory; a CTA keeps one chunk's table and sweeps a block of momenta.
+#define NBS_CHUNK_WARPS 8
+#define NBS_CHUNK_ENTRIES 45056
+#define NBS_MAX_COEF_CODES 32
+struct ChunkHdr {
+  int base1, ncell1, base2, ncell2;   // the group's two stored types
+  int ch_off, nch;                    // into Plan::group_ch
+  int tab_off, tab_len;               // 16-bit entries, into Plan::chunk_tab
+  int item_off, nslot;                // into Plan::chunk_items (pairs)
+  int warp_off[NBS_CHUNK_WARPS + 1];
+  int out_base[NBS_CHUNK_WARPS + 1];
+  int cfirst[NBS_CHUNK_WARPS];
+  int ch_local0;                      // group-local index of the chunk's first channel
+  int pad[3];
+};
+
 struct Plan {
   std::vector<int> channels;                  // built-in ids, in request order
   std::vector<BlockType> types;
@@ -62,6 +81,12 @@ struct Plan {
   std::vector<GroupHdr> groups;
   std::vector<int> group_ch;
   std::vector<int> items;                     // pairs (term, k0)
+  bool chunks_ok = false;                     // every channel fits one chunk, <= 32 coefficient codes
+  std::vector<ChunkHdr> chunks;
+  std::vector<unsigned short> chunk_tab;
+  std::vector<int> chunk_items;               // pairs (term, k0)
+  std::vector<int> term_tab_off;              // per term: side-1, side-2 offsets inside its chunk's table
+  std::vector<double> coef_codes;             // |coefficient| of each code
   // flops of the contraction per q (complex multiply-adds), for rooflines
   double cmac_per_q = 0, gathers_per_q = 0;
 };

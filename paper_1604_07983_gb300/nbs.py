@@ -108,7 +108,8 @@ def channel_names():
 # ---- host-only plan introspection ---------------------------------------------
 
 PX = dict(TYPES=0, TYPETERMS=1, TYPECOEF=2, CELLS=3, TERMS=4, ENT1_CELL=5, ENT1_COEF=6, ENT2_CELL=7,
-          ENT2_COEF=8, CHANNELS=9, GROUPS=10, GROUPCH=11, ITEMS=12)
+          ENT2_COEF=8, CHANNELS=9, GROUPS=10, GROUPCH=11, ITEMS=12, CHUNKS=13, CHUNKTAB=14, CHUNKITEMS=15,
+          TERMTABOFF=16, CODES=17)
 
 
 def plan_tables(channel_ids):
@@ -119,9 +120,9 @@ def plan_tables(channel_ids):
     p = ctypes.c_void_p()
     _check(L.nbs_plan_create(ctypes.byref(p), ids, len(channel_ids)))
     try:
-        s = (ctypes.c_longlong * 9)()
+        s = (ctypes.c_longlong * 12)()
         _check(L.nbs_plan_sizes(p, s))
-        ntypes, ncells, ntt, nterm, ne1, ne2, nch, ngr, nit = list(s)
+        ntypes, ncells, ntt, nterm, ne1, ne2, nch, ngr, nit, nck, nctab, ncit = list(s)
 
         def get(what, shape, dtype):
             a = np.zeros(shape, dtype=dtype)
@@ -135,7 +136,9 @@ def plan_tables(channel_ids):
             ent1_coef=get("ENT1_COEF", (ne1,), np.float64), ent2_cell=get("ENT2_CELL", (ne2,), np.int32),
             ent2_coef=get("ENT2_COEF", (ne2,), np.float64), channels=get("CHANNELS", (nch, 4), np.int32),
             groups=get("GROUPS", (ngr, 24), np.int32), items=get("ITEMS", (nit, 2), np.int32),
-            group_ch=get("GROUPCH", (nch,), np.int32))
+            group_ch=get("GROUPCH", (nch,), np.int32), chunks=get("CHUNKS", (nck, 40), np.int32),
+            chunk_tab=get("CHUNKTAB", (max(nctab, 1),), np.uint16), chunk_items=get("CHUNKITEMS", (ncit, 2), np.int32),
+            term_tab_off=get("TERMTABOFF", (nterm, 2), np.int32), codes=get("CODES", (32,), np.float64))
     finally:
         L.nbs_plan_destroy(p)
 
@@ -252,6 +255,7 @@ class Context:
         return out
 
     PARAM_CONTRACT_CFG = 0
+    PARAM_CHUNK_QBLOCK = 1
 
     def set_param(self, param: int, value: int):
         _check(self._lib.nbs_set_param(self.h, param, value), self.h)

@@ -115,7 +115,7 @@ def test_fp32_all_channels_L4(nbs):
         assert rel(F32[c, 0], ref) < FP32_TOL, names[c]
 
 
-@pytest.mark.parametrize("cfg", [1, 22, 11])
+@pytest.mark.parametrize("cfg", [1, 2, 22, 11])
 def test_contraction_variants_all_channels(nbs, cfg):
     """Every contraction kernel and launch shape against the oracle, FP64 and FP32, all 52 channels."""
     L = 3

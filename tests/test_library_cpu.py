@@ -124,6 +124,49 @@ def test_slab_work_split_covers_every_term_once(lib, ids):
     assert (seen == terms[:, 1]).all()
 
 
+@pytest.mark.parametrize("ids", [list(range(52)), [0], [24, 25, 51]])
+def test_chunk_tables_decode_to_the_gather_tables(lib, ids):
+    """The 16-bit shared-memory tables of the chunk contraction decode to the
+    full gather tables, every read stays in its slab, every shared index of
+    every term is visited once, and the shared memory fits a GB300 block."""
+    tb = nbs.plan_tables(ids)
+    chunks, ctab, items, toff, codes = tb["chunks"], tb["chunk_tab"], tb["chunk_items"], tb["term_tab_off"], tb["codes"]
+    terms = tb["terms"]
+    assert len(chunks) > 0 and codes[31] == 0
+    seen = np.zeros(len(terms), dtype=int)
+    for ck in chunks:
+        base1, n1, base2, n2, ch_off, nch, tab_off, tab_len, item_off, nslot = ck[:10]
+        warp_off, out_base, cfirst, local0 = ck[10:19], ck[19:28], ck[28:36], ck[36]
+        assert tab_off % 8 == 0 and tab_len % 8 == 0 and tab_len <= 45056
+        assert out_base[8] == nslot
+        smem = tab_len * 2 + 2 * (2 * 936 + 2 * 936) * 16 + nslot * 64 * 8 + 128
+        assert smem <= 227 * 1024
+        for w in range(8):
+            for it in range(item_off + warp_off[w], item_off + warp_off[w + 1]):
+                t, k0 = items[it]
+                ch, K, shape, nn1, nn2, off1, off2, gl = terms[t]
+                r = gl - local0 - cfirst[w]
+                assert 0 <= gl - local0 < nch and 0 <= r < out_base[w + 1] - out_base[w]
+                seen[t] += min(32, K - k0)
+        for t in set(int(x) for x in items[item_off:item_off + warp_off[8], 0]):
+            ch, K, shape, nn1, nn2, off1, off2, gl = terms[t]
+            nh1 = 1 << ((shape & 1) + ((shape >> 1) & 1))
+            nh2 = 4 // nh1
+            for side, (n, off, base, ncell) in enumerate([(K * nh1 * nn1, off1, base1, n1), (K * nh2 * nn2, off2, base2, n2)]):
+                o = toff[t, side]
+                assert o % 8 == 0 and o + n <= tab_len
+                e = ctab[tab_off + o: tab_off + o + n].astype(np.int64)
+                cell = (e & 1023) + base
+                coef = codes[e >> 11] * np.where(e & 1024, -1.0, 1.0)
+                want_cell = tb["ent%d_cell" % (side + 1)][off: off + n]
+                want_coef = tb["ent%d_coef" % (side + 1)][off: off + n]
+                assert ((e & 1023) < ncell).all()
+                nz = want_coef != 0
+                assert (cell[nz] == want_cell[nz]).all()
+                assert np.allclose(coef, want_coef, rtol=1e-6, atol=0)
+    assert (seen == terms[:, 1]).all()
+
+
 def test_worked_counts_pn(lib):
     tb = nbs.plan_tables([0])
     terms = tb["terms"]
