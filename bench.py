@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=32)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "bf16x3"], default="fp32")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--L", type=int, default=L_DEFAULT)
     ap.add_argument("--T", type=int, default=T_DEFAULT)
@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--contract-cfg", type=int, default=0, help="NBS_PARAM_CONTRACT_CFG (kernel / launch shape)")
     ap.add_argument("--qblock", type=int, default=0, help="NBS_PARAM_CHUNK_QBLOCK (0 = library default)")
+    ap.add_argument("--c64", action="store_true", help="store the propagators as complex64 (the 48^3 x 64 config)")
+    ap.add_argument("--decay", type=float, default=DECAY)
+    ap.add_argument("--autotune", action="store_true", help="pick the contraction shape with the autotuner first")
+    ap.add_argument("--workload", choices=["single", "batched"], default="single",
+                    help="batched: six configurations 2x16^3x32, 2x24^3x48, 2x32^3x32, every timeslice")
     return ap.parse_args()
 
 
@@ -209,9 +214,12 @@ def run_reference(args, rank):
 
 # ---- the GPU arm ---------------------------------------------------------------------------
 
-def make_props_host(L, T, seed):
+def make_props_host(L, T, seed, decay=DECAY, c64=False):
+    import numpy as np
     import nbs_inputs as I
-    return [(I.propagator(seed, "l", L, t, DECAY), I.propagator(seed, "s", L, t, DECAY)) for t in range(T)]
+    dt = np.complex64 if c64 else np.complex128
+    return [(I.propagator(seed, "l", L, t, decay).astype(dt), I.propagator(seed, "s", L, t, decay).astype(dt))
+            for t in range(T)]
 
 
 def contraction_flops(ids):
@@ -238,11 +246,14 @@ def run_ours(args, rank, world, local_rank):
 
     L, T = args.L, args.T
     V = L ** 3
-    prec = P.NBS_FP32 if args.precision == "fp32" else P.NBS_FP64
+    prec = {"fp32": P.NBS_FP32, "fp64": P.NBS_FP64, "bf16x3": P.NBS_BF16X3}[args.precision]
     ids = list(range(P.channel_count()))
     nch = len(ids)
     seed = SEED + rank
-    host_props = make_props_host(L, T, seed)
+    if args.workload == "batched":
+        run_batched(args, rank, world, P, prec, ids)
+        return
+    host_props = make_props_host(L, T, seed, args.decay, args.c64)
 
     ctx = P.Context(L, T, precision=prec)
     ctx.set_param(ctx.PARAM_CONTRACT_CFG, args.contract_cfg)
@@ -252,6 +263,10 @@ def run_ours(args, rank, world, local_rank):
         ctx.load_props(torch.from_numpy(Sl).cuda(), torch.from_numpy(Ss).cuda(), t)
     out = torch.empty((nch, 1, 4, 4, 2, 2, V), dtype=torch.complex128, device="cuda")
     torch.cuda.synchronize()
+    tuned = None
+    if args.autotune:
+        from paper_1604_07983_gb300 import autotune
+        tuned = autotune.tune(ctx, ids, prec, t=0, use_cache=False)
 
     for k in range(args.warmup):
         ctx.correlate(ids, k % T, k % T + 1, out)
@@ -315,10 +330,18 @@ def run_ours(args, rank, world, local_rank):
     fl, tb = contraction_flops(ids)
     flops_per_launch = fl * V
     ncomp = 4 * len(tb["cells"])
-    csz = 8 if prec == P.NBS_FP32 else 16
+    csz = 16 if prec == P.NBS_FP64 else 8
     dominant = max(stages, key=lambda k: stages[k])
     per_launch_ms = {k: v / args.steps for k, v in stages.items()}
-    if dominant == "contract":
+    if dominant == "contract" and prec == P.NBS_BF16X3:
+        peak = peaks.get("bf16_tflops", 1900.0)
+        ach = 3 * flops_per_launch / (per_launch_ms["contract"] / 1e3) / 1e12
+        roof = {"kernel": "k_contract_tc", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)" if "bf16_tflops" in peaks else "fallback",
+                "work_per_launch": "3 bf16 products x 8 flop x 64 x sum|xi~| (=%d) x V complex MACs of Eq. (4.3)"
+                                   % int(tb["terms"][:, 1].sum())}
+    elif dominant == "contract":
         if prec == P.NBS_FP32:
             peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
             peak_src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
@@ -326,7 +349,9 @@ def run_ours(args, rank, world, local_rank):
             peak = 1.25
             peak_src = "nominal GB300 FP64 1.25 TFLOP/s"
         ach = flops_per_launch / (per_launch_ms["contract"] / 1e3) / 1e12
-        roof = {"kernel": "k_contract", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+        kname = ("k_contract_chunk" if prec == P.NBS_FP32 and args.contract_cfg in (0, 2) else
+                 "k_contract_slab" if args.contract_cfg == 1 else "k_contract")
+        roof = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None, "peak_source": peak_src,
                 "work_per_launch": "8 flop x 64 x sum|xi~| (=%d) x V complex MACs of Eq. (4.3)"
                                    % int(tb["terms"][:, 1].sum())}
@@ -347,15 +372,20 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if prec == P.NBS_FP32 else "f64",
+        "vs_baseline": None, "dtype": {P.NBS_FP32: "f32", P.NBS_FP64: "f64", P.NBS_BF16X3: "bf16x3"}[prec],
         "data": "synthetic seeded Gaussian propagators, exp(-0.5 t) decay",
-        "config": {"workload": "%d^3 x %d lattice, all %d channels, one timeslice per step" % (L, T, nch),
-                   "precision": "fp64 rescale -> fp32 blocks/FFT/contraction -> fp64 restore"
-                   if prec == P.NBS_FP32 else "fp64", "l2": "inputs larger than L2 (blocks %.2f GB/step)"
+        "config": {"workload": "%d^3 x %d lattice, all %d channels, one timeslice per step%s"
+                               % (L, T, nch, ", complex64 propagator storage" if args.c64 else ""),
+                   "precision": {P.NBS_FP32: "fp64 rescale -> fp32 blocks/FFT/contraction -> fp64 restore",
+                                 P.NBS_FP64: "fp64",
+                                 P.NBS_BF16X3: "fp64 rescale -> fp32 blocks/FFT -> split-bf16x3 tensor-core "
+                                               "contraction (fp32 accumulate) -> fp64 restore"}[prec], "l2": "inputs larger than L2 (blocks %.2f GB/step)"
                    % (ncomp * V * csz / 1e9), "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": roof,
         "stages_ms_per_step": {k: round(v, 4) for k, v in per_launch_ms.items()},
         "gpu_launches": int(launches),
+        "contraction_shape": {"cfg": tuned["cfg"], "qb": tuned["qb"], "timings": tuned["timings"]} if tuned else
+                             {"cfg": args.contract_cfg, "qb": args.qblock},
         "clocks": clocks.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
@@ -365,6 +395,47 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+BATCH = [(16, 32), (16, 32), (24, 48), (24, 48), (32, 32), (32, 32)]
+
+
+def run_batched(args, rank, world, P, prec, ids):
+    """Six configurations of uneven size (seeds 1608..1613), every timeslice of each, one
+    context per configuration; a step is one timeslice of one configuration."""
+    import torch
+    nch = len(ids)
+    ctxs, outs, jobs = [], [], []
+    for ci, (L, T) in enumerate(BATCH):
+        ctx = P.Context(L, T, precision=prec)
+        ctx.set_param(ctx.PARAM_CONTRACT_CFG, args.contract_cfg)
+        for t, (Sl, Ss) in enumerate(make_props_host(L, T, 1608 + ci + 6 * rank, args.decay)):
+            ctx.load_props(torch.from_numpy(Sl).cuda(), torch.from_numpy(Ss).cuda(), t)
+        ctxs.append(ctx)
+        outs.append(torch.empty((nch, 1, 4, 4, 2, 2, L ** 3), dtype=torch.complex128, device="cuda"))
+        jobs += [(ci, t) for t in range(T)]
+    for ci in range(len(BATCH)):  # warm-up: one timeslice per configuration
+        ctxs[ci].correlate(ids, 0, 1, outs[ci])
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clocks:
+        start.record()
+        for ci, t in jobs:
+            ctxs[ci].correlate(ids, t, t + 1, outs[ci])
+        stop.record()
+        torch.cuda.synchronize()
+    ms = start.elapsed_time(stop)
+    value = nch * len(jobs) * world / (ms / 1e3)
+    for c in ctxs:
+        c.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC + " (batched: 2x16^3x32, 2x24^3x48, 2x32^3x32)", "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": len(jobs), "warmup": len(BATCH), "ms_per_step": ms / len(jobs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec != P.NBS_FP64 else "f64", "data": "synthetic, seeds 1608-1613",
+            "config": {"workload": "6 configurations, %d timeslices, all %d channels" % (len(jobs), nch)},
+            "clocks": clocks.summary()}), flush=True)
 
 
 def main():

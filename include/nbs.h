@@ -44,6 +44,8 @@ extern "C" {
 /* ---- precision modes (nbs_set_precision) ------------------------------- */
 #define NBS_FP64   0   /* blocks, FFTs and contraction in complex FP64           */
 #define NBS_FP32   1   /* FP64 rescale -> FP32 blocks/FFT/contraction -> FP64 restore */
+#define NBS_BF16X3 2   /* as NBS_FP32, with the effective-block product on the tensor
+                          cores: split-BF16 x 3 (hi*hi + hi*lo + lo*hi), FP32 accumulation */
 
 /* ---- propagator element types (nbs_load_props) ------------------------- */
 #define NBS_C128   0   /* interleaved complex double */
@@ -69,7 +71,7 @@ int nbs_set_allocator(nbs_alloc_fn alloc, nbs_free_fn free_fn, void* user);
 int nbs_create(nbs_ctx** out, int L, int T, int flavours);
 int nbs_destroy(nbs_ctx* h);
 
-/* Select the arithmetic of the path (NBS_FP64 default, or NBS_FP32). */
+/* Select the arithmetic of the path (NBS_FP64 default, NBS_FP32 or NBS_BF16X3). */
 int nbs_set_precision(nbs_ctx* h, int mode);
 
 /* Run every later call of the context on this cudaStream_t (0 = legacy default). */

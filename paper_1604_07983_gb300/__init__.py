@@ -4,5 +4,5 @@ The compute path is the CUDA library libnbs.so (C ABI in include/nbs.h); this
 package only builds it (build.py) and binds it (nbs.py).
 """
 
-from .nbs import (NBS_C64, NBS_C128, NBS_FP32, NBS_FP64, NBS_NSPIN, Context, NBSError, channel_count,  # noqa: F401
+from .nbs import (NBS_BF16X3, NBS_C64, NBS_C128, NBS_FP32, NBS_FP64, NBS_NSPIN, Context, NBSError, channel_count,  # noqa: F401
                   channel_info, channel_names, lib, plan_tables, use_torch_allocator)

@@ -1,0 +1,83 @@
+"""Launch-shape autotuner for the contraction (the dominant kernel of the path).
+
+For a context with propagators loaded, it times each candidate kernel / launch
+shape of the effective-block contraction on one timeslice with the library's
+own CUDA-event stage timing (nbs_set_profiling / nbs_profile), keeps the
+fastest, and caches the choice in a JSON file keyed by (GPU name, L,
+precision, channel set).  Results do not depend on the choice beyond
+rounding; every candidate is covered by the parity tests.
+"""
+
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+from .nbs import NBS_BF16X3, NBS_FP32, NBS_FP64, Context
+
+CACHE = os.path.join(os.path.expanduser("~"), ".cache", "nbs_gb300", "autotune.json")
+
+#: (contraction config, momentum block) candidates per precision mode
+CANDIDATES = {
+    NBS_FP32: [(0, 32), (0, 64), (0, 128), (42, 0), (22, 0), (1, 0)],
+    NBS_BF16X3: [(0, 32), (0, 64), (0, 128)],
+    NBS_FP64: [(21, 0), (12, 0), (22, 0), (11, 0), (1, 0)],
+}
+
+
+def _key(ctx: Context, ids, precision: int) -> str:
+    import torch
+    name = torch.cuda.get_device_name()
+    h = hashlib.sha1(",".join(map(str, ids)).encode()).hexdigest()[:12]
+    return "%s|L=%d|prec=%d|ch=%s" % (name, ctx.L, precision, h)
+
+
+def _load():
+    try:
+        with open(CACHE) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _apply(ctx: Context, cfg: int, qb: int):
+    ctx.set_param(Context.PARAM_CONTRACT_CFG, cfg)
+    if qb:
+        ctx.set_param(Context.PARAM_CHUNK_QBLOCK, qb)
+
+
+def tune(ctx: Context, ids, precision: int, t: int = 0, reps: int = 2, use_cache: bool = True) -> dict:
+    """Pick the fastest contraction shape for (ctx.L, precision, ids) and apply it to ctx.
+
+    Propagators for timeslice t must be loaded.  Returns {"cfg", "qb", "ms", "timings"}.
+    """
+    import torch
+    key = _key(ctx, ids, precision)
+    cache = _load() if use_cache else {}
+    if key in cache:
+        best = cache[key]
+        _apply(ctx, best["cfg"], best["qb"])
+        return best
+    out = torch.empty((len(ids), 1, 4, 4, 2, 2, ctx.V), dtype=torch.complex128, device="cuda")
+    timings = []
+    for cfg, qb in CANDIDATES[precision]:
+        _apply(ctx, cfg, qb)
+        ctx.correlate(ids, t, t + 1, out)  # warm-up (and block build)
+        ctx.set_profiling(True)
+        for _ in range(reps):
+            ctx.correlate(ids, t, t + 1, out)
+        stages, _ = ctx.profile()
+        ctx.set_profiling(False)
+        timings.append({"cfg": cfg, "qb": qb, "ms": stages["contract"] / reps})
+    best = dict(min(timings, key=lambda r: r["ms"]))
+    best["timings"] = timings
+    _apply(ctx, best["cfg"], best["qb"])
+    if use_cache:
+        cache[key] = best
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        tmp = CACHE + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(cache, fh, indent=1)
+        os.replace(tmp, CACHE)
+    return best

@@ -89,6 +89,12 @@ cudaError_t launch_contract_chunk(const float2* FB, int L, int nchunks, int qb, 
                                   const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
                                   const float* codes, int st1, int st2, int max_slot, int max_tab, float2* Ft,
                                   cudaStream_t st);
+// the same on the tensor cores, split-BF16 x 3 (kernels_tc.cu)
+size_t tc_smem_bytes(int st1, int st2, int max_slot, int max_tab);
+cudaError_t launch_contract_tc(const float2* FB, int L, int nchunks, int qb, const void* chunks, const int* group_ch,
+                               const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
+                               const float* codes, int st1, int st2, int max_slot, int max_tab, float2* Ft,
+                               cudaStream_t st);
 template <typename T>
 cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_nl, const int* exps,
                            double2* out, long long ch_stride, cudaStream_t st);

@@ -170,7 +170,8 @@ int ensure(nbs_ctx* h, DevBuf& b, size_t bytes, const char* what) {
   return NBS_OK;
 }
 
-size_t csize(int mode) { return mode == NBS_FP32 ? sizeof(float2) : sizeof(double2); }
+// FP32 and BF16X3 share the FP32 blocks and FFTs
+bool is_f32(int mode) { return mode == NBS_FP32 || mode == NBS_BF16X3; }
 
 int upload_tables(nbs_ctx* h) {
   const Plan& P = h->plan;
@@ -244,7 +245,7 @@ int upload_tables(nbs_ctx* h) {
   }
   // gather entries in the arithmetic of the current mode
   const size_t n1 = P.ent1_cell.size(), n2 = P.ent2_cell.size();
-  if (h->mode == NBS_FP32) {
+  if (is_f32(h->mode)) {
     std::vector<Ent<float>> a(n1), b(n2);
     for (size_t i = 0; i < n1; ++i) a[i] = {P.ent1_cell[i], (float)P.ent1_coef[i]};
     for (size_t i = 0; i < n2; ++i) b[i] = {P.ent2_cell[i], (float)P.ent2_coef[i]};
@@ -343,7 +344,14 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
     cudaEvent_t e3 = stage_begin(h);
     // default in FP32: the chunk kernel when the tables fit; FP64: the thread-per-momentum kernel
     const bool use_chunk = (h->contract_cfg == 2 || h->contract_cfg == 0) && sizeof(T) == 4 && h->plan.chunks_ok;
-    if (use_chunk) {
+    if (h->mode == NBS_BF16X3) {
+      if (!h->plan.chunks_ok) return fail(h, NBS_EINVAL, "BF16X3 needs channel tables that fit the chunk kernel");
+      CK(launch_contract_tc((const float2*)h->FB.p, h->L, (int)h->plan.chunks.size(), h->chunk_qb, h->d_chunks.p,
+                            (const int*)h->d_gch.p, (const int*)h->d_citems.p, (const DevTerm*)h->d_terms.p,
+                            (const int*)h->d_ctoff.p, (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
+                            h->chunk_st1, h->chunk_st2, h->chunk_slot, h->chunk_tab, (float2*)h->Ft.p, h->st),
+         "contraction (tensor cores)");
+    } else if (use_chunk) {
       CK(launch_contract_chunk((const float2*)h->FB.p, h->L, (int)h->plan.chunks.size(), h->chunk_qb, h->d_chunks.p,
                                (const int*)h->d_gch.p, (const int*)h->d_citems.p, (const DevTerm*)h->d_terms.p,
                                (const int*)h->d_ctoff.p, (const unsigned short*)h->d_ctab.p,
@@ -484,7 +492,7 @@ int nbs_destroy(nbs_ctx* h) {
 
 int nbs_set_precision(nbs_ctx* h, int mode) {
   if (!h) return fail(nullptr, NBS_EINVAL, "null context");
-  if (mode != NBS_FP64 && mode != NBS_FP32) return fail(h, NBS_EINVAL, "unknown precision mode");
+  if (mode != NBS_FP64 && mode != NBS_FP32 && mode != NBS_BF16X3) return fail(h, NBS_EINVAL, "unknown precision mode");
   h->mode = mode;
   return NBS_OK;
 }
@@ -517,7 +525,7 @@ int nbs_blocks(nbs_ctx* h, int t) {
   int rc;
   if (!h->plan_ok && (rc = ensure_plan(h, all_channels()))) return rc;
   if (h->tables_mode != h->mode && (rc = upload_tables(h))) return rc;
-  rc = h->mode == NBS_FP32 ? build_blocks<float>(h, t) : build_blocks<double>(h, t);
+  rc = is_f32(h->mode) ? build_blocks<float>(h, t) : build_blocks<double>(h, t);
   if (rc) return rc;
   CK(cudaStreamSynchronize(h->st), "sync");
   prof_resolve(h);
@@ -534,8 +542,8 @@ int nbs_correlate(nbs_ctx* h, const int* channel_ids, int n_channels, int t_begi
   std::vector<int> ids(channel_ids, channel_ids + n_channels);
   int rc = ensure_plan(h, ids);
   if (rc) return rc;
-  return h->mode == NBS_FP32 ? correlate<float>(h, n_channels, t_begin, t_end, out, out_on_device)
-                             : correlate<double>(h, n_channels, t_begin, t_end, out, out_on_device);
+  return is_f32(h->mode) ? correlate<float>(h, n_channels, t_begin, t_end, out, out_on_device)
+                         : correlate<double>(h, n_channels, t_begin, t_end, out, out_on_device);
 }
 
 int nbs_set_param(nbs_ctx* h, int param, int value) {
@@ -577,7 +585,7 @@ int nbs_zero_momentum(nbs_ctx* h, double* out) {
   if (h->last_nch == 0) return fail(h, NBS_ESTATE, "no correlator computed yet");
   const int n = h->last_nch * 64;
   std::vector<double> tmp(2 * n);
-  if (h->mode == NBS_FP32) {
+  if (is_f32(h->mode)) {
     std::vector<float2> f(n);
     CK(cudaMemcpy(f.data(), h->zm.p, n * sizeof(float2), cudaMemcpyDeviceToHost), "zero momentum");
     for (int i = 0; i < n; ++i) { tmp[2 * i] = f[i].x; tmp[2 * i + 1] = f[i].y; }

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnbs.so")
 
 NBS_OK, NBS_EINVAL, NBS_ENOMEM, NBS_ECUDA, NBS_ESTATE, NBS_ETIMEOUT, NBS_ENAN = 0, -1, -2, -3, -4, -5, -6
-NBS_FP64, NBS_FP32 = 0, 1
+NBS_FP64, NBS_FP32, NBS_BF16X3 = 0, 1, 2
 NBS_C128, NBS_C64 = 0, 1
 NBS_NSPIN = 64
 ERRORS = {NBS_EINVAL: "EINVAL", NBS_ENOMEM: "ENOMEM", NBS_ECUDA: "ECUDA", NBS_ESTATE: "ESTATE",

@@ -130,6 +130,40 @@ def test_contraction_variants_all_channels(nbs, cfg):
         assert rel(F32[c, 0], ref) < FP32_TOL, (cfg, names[c])
 
 
+def test_bf16x3_tensor_core_path_all_channels(nbs):
+    """Split-BF16 x 3 contraction on the tensor cores: every channel against the oracle at 2e-5."""
+    L = 4
+    props = seeded(1722, L, 2, decay=0.5)
+    names = nbs.channel_names()
+    ids = list(range(len(names)))
+    F = gpu_correlate(nbs, ids, L, props, nbs.NBS_BF16X3)
+    for c in ids:
+        for t in range(2):
+            assert rel(F[c, t], oracle(names[c], *props[t], L)) < FP32_TOL, (names[c], t)
+
+
+def test_precision_table_32cube(nbs, capsys):
+    """Per-channel normwise error of FP32 and split-BF16 x 3 against the FP64 GPU path at 32^3
+    (decaying propagators, a late timeslice), each within 2e-5.  The FP64 GPU path is pinned to the
+    oracle by the other tests (all channels at small L, every r at 8^3, sampled r at 16^3)."""
+    L, t = 32, 12
+    Sl, Ss = I.propagator(1607, "l", L, t, 0.5), I.propagator(1607, "s", L, t, 0.5)
+    names = nbs.channel_names()
+    ids = list(range(len(names)))
+    F64 = gpu_correlate(nbs, ids, L, [(Sl, Ss)], nbs.NBS_FP64)
+    rows = []
+    for mode in (nbs.NBS_FP32, nbs.NBS_BF16X3):
+        F = gpu_correlate(nbs, ids, L, [(Sl, Ss)], mode)
+        errs = [rel(F[c, 0], F64[c, 0]) for c in ids]
+        rows.append(errs)
+        assert max(errs) < FP32_TOL, (mode, names[int(np.argmax(errs))], max(errs))
+    with capsys.disabled():
+        print("\nprecision table 32^3 t=%d: channel, FP32 err, BF16x3 err" % t)
+        for c in ids:
+            print("%-32s %.3e %.3e" % (" ".join(names[c]), rows[0][c], rows[1][c]))
+        print("max FP32 %.3e  max BF16x3 %.3e" % (max(rows[0]), max(rows[1])))
+
+
 def test_host_output_and_timeslice_split(nbs):
     L, T = 4, 5
     props = seeded(1712, L, T)
