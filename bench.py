@@ -212,6 +212,32 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---- host logic of the multi-rank (replica) path --------------------------------------------
+
+def rank_seed(rank):
+    """Seed of the lattice a rank processes: every rank runs its own configuration (weak scaling)."""
+    return SEED + rank
+
+
+def batched_seed(ci, rank, nconf=6):
+    return 1608 + ci + nconf * rank
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest of the ranks' values of x (the job ends when its slowest rank does)."""
+    if dist is None:
+        return float(x)
+    import torch
+    tt = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the max-over-ranks time."""
+    return units_per_rank * world / seconds
+
+
 # ---- the GPU arm ---------------------------------------------------------------------------
 
 def make_props_host(L, T, seed, decay=DECAY, c64=False):
@@ -249,9 +275,11 @@ def run_ours(args, rank, world, local_rank):
     prec = {"fp32": P.NBS_FP32, "fp64": P.NBS_FP64, "bf16x3": P.NBS_BF16X3}[args.precision]
     ids = list(range(P.channel_count()))
     nch = len(ids)
-    seed = SEED + rank
+    seed = rank_seed(rank)
     if args.workload == "batched":
-        run_batched(args, rank, world, P, prec, ids)
+        run_batched(args, rank, world, P, prec, ids, dist)
+        if dist:
+            dist.destroy_process_group()
         return
     host_props = make_props_host(L, T, seed, args.decay, args.c64)
 
@@ -286,13 +314,9 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-    ms = start.elapsed_time(stop)
+    ms = max_over_ranks(start.elapsed_time(stop), dist, "cuda")
     stages, launches = ctx.profile()
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = nch * args.steps * world / (ms / 1e3)
+    value = job_rate(nch * args.steps, world, ms / 1e3)
 
     # ---- end to end through the public API with host buffers ----
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
@@ -310,12 +334,8 @@ def run_ours(args, rank, world, local_rank):
         ctx.load_props(pin_u[k], pin_s[k], k)
         ctx.correlate(ids, k, k + 1, out_h)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_value = nch * e2e_steps * world / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = job_rate(nch * e2e_steps, world, e2e_s)
     h2d = 2 * V * 144 * 16
     d2h = nch * 64 * V * 16
     ctx.close()
@@ -400,7 +420,7 @@ def run_ours(args, rank, world, local_rank):
 BATCH = [(16, 32), (16, 32), (24, 48), (24, 48), (32, 32), (32, 32)]
 
 
-def run_batched(args, rank, world, P, prec, ids):
+def run_batched(args, rank, world, P, prec, ids, dist=None):
     """Six configurations of uneven size (seeds 1608..1613), every timeslice of each, one
     context per configuration; a step is one timeslice of one configuration."""
     import torch
@@ -409,7 +429,7 @@ def run_batched(args, rank, world, P, prec, ids):
     for ci, (L, T) in enumerate(BATCH):
         ctx = P.Context(L, T, precision=prec)
         ctx.set_param(ctx.PARAM_CONTRACT_CFG, args.contract_cfg)
-        for t, (Sl, Ss) in enumerate(make_props_host(L, T, 1608 + ci + 6 * rank, args.decay)):
+        for t, (Sl, Ss) in enumerate(make_props_host(L, T, batched_seed(ci, rank), args.decay)):
             ctx.load_props(torch.from_numpy(Sl).cuda(), torch.from_numpy(Ss).cuda(), t)
         ctxs.append(ctx)
         outs.append(torch.empty((nch, 1, 4, 4, 2, 2, L ** 3), dtype=torch.complex128, device="cuda"))
@@ -419,13 +439,18 @@ def run_batched(args, rank, world, P, prec, ids):
     torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clocks:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
         start.record()
         for ci, t in jobs:
             ctxs[ci].correlate(ids, t, t + 1, outs[ci])
         stop.record()
         torch.cuda.synchronize()
-    ms = start.elapsed_time(stop)
-    value = nch * len(jobs) * world / (ms / 1e3)
+        if dist:
+            dist.barrier()
+    ms = max_over_ranks(start.elapsed_time(stop), dist, "cuda")
+    value = job_rate(nch * len(jobs), world, ms / 1e3)
     for c in ctxs:
         c.close()
     if rank == 0:
