@@ -656,20 +656,66 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_chunk(
   }
 }
 
-// out[ch * ch_stride + c*V + r] = Ft[ch][c][r] * 2^(e_l n_l + e_s n_s) / V   (FP64)
+// f * 2^ex as a double, by integer operations on the bit pattern (exact): a
+// normal FP32 value keeps its sign and mantissa and gets the FP64 exponent
+// E - 127 + 1023 + ex; zeros stay zeros; FP32 subnormals, infinities, NaNs
+// and results outside the FP64 normal range go through ldexp.
+__device__ __forceinline__ double scaled_double(float f, int ex) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned E = (b >> 23) & 255u;
+  const int DE = (int)E + (1023 - 127) + ex;
+  if (E - 1u < 254u && DE > 0 && DE < 2047) {
+    // high word: sign, 11-bit exponent, top 20 mantissa bits; low word: last 3 mantissa bits
+    const unsigned hi = (b & 0x80000000u) | ((unsigned)DE << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+  }
+  if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  return ldexp((double)f, ex);
+}
+
+// out[ch * ch_stride + c*V + r] = Ft[ch][c][r] * 2^(e_l n_l + e_s n_s) / V
+// FP32 input: 1/V applied in FP32, the power of two added to the exponent
+// (no FP64 arithmetic, which is scarce on GB300); two complex values per
+// 16-byte load and RS independent loads in flight per thread.  FP64 input:
+// FP64 multiply.
 template <typename T>
 __global__ void __launch_bounds__(256) k_restore(const C<T>* __restrict__ Ft, long long V, const int* __restrict__ ch_nl,
                                                  const int* __restrict__ exps, double2* __restrict__ out,
                                                  long long ch_stride) {
   const int ch = blockIdx.y;
   const int nl = ch_nl[ch];
-  const double scale = ldexp(1.0, exps[0] * nl + exps[1] * (6 - nl)) / (double)V;
+  const int ex = exps[0] * nl + exps[1] * (6 - nl);
   const long long n = 64 * V;
   const C<T>* src = Ft + ch * n;
   double2* dst = out + ch * ch_stride;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    C<T> z = src[i];
-    dst[i] = make_double2((double)z.x * scale, (double)z.y * scale);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if constexpr (sizeof(T) == 4) {
+    constexpr int RS = 4;
+    const float inv = 1.0f / (float)V;
+    const float4* s4 = reinterpret_cast<const float4*>(src);  // n is even, Ft 16-byte aligned
+    const long long n2 = n / 2;
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n2; i0 += RS * stride) {
+      float4 z[RS];
+#pragma unroll
+      for (int u = 0; u < RS; ++u) {
+        const long long i = i0 + u * stride;
+        z[u] = i < n2 ? __ldcs(s4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < RS; ++u) {
+        const long long i = i0 + u * stride;
+        if (i < n2) {
+          dst[2 * i] = make_double2(scaled_double(z[u].x * inv, ex), scaled_double(z[u].y * inv, ex));
+          dst[2 * i + 1] = make_double2(scaled_double(z[u].z * inv, ex), scaled_double(z[u].w * inv, ex));
+        }
+      }
+    }
+  } else {
+    const double scale = ldexp(1.0, ex) / (double)V;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      const C<T> z = src[i];
+      dst[i] = make_double2((double)z.x * scale, (double)z.y * scale);
+    }
   }
 }
 
@@ -747,7 +793,8 @@ template <typename T>
 cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_nl, const int* exps, double2* out,
                            long long ch_stride, cudaStream_t st) {
   long long n = 64LL * V;
-  int bx = (int)std::min<long long>((n + 255) / 256, 4096);
+  if (sizeof(T) == 4) n /= 8;  // 16-byte loads, four per thread per pass
+  int bx = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096));
   dim3 grid(bx, nch);
   k_restore<T><<<grid, 256, 0, st>>>(Ft, (long long)V, ch_nl, exps, out, ch_stride);
   return cudaGetLastError();
