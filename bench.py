@@ -33,6 +33,10 @@ L_DEFAULT, T_DEFAULT, DECAY, SEED = 32, 32, 0.5, 1607
 METRIC = "52-channel NBS correlators/sec/timeslice at 32^3"
 UNIT = "correlators/s"
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# DRAM bytes per momentum of the FP32 contraction kernels, from one ncu capture of
+# `python bench.py --L 16 --T 2 --steps 1 --warmup 1 --e2e-steps 1 --no-cpu-baseline`
+# (dram__bytes_read.sum + dram__bytes_write.sum / 4096 momenta; profiles/k_contract_16cube_fp32.md)
+DRAM_BYTES_PER_Q = {"k_contract_quad": 1.199122e9 / 4096}
 
 
 def parse():
@@ -369,10 +373,18 @@ def run_ours(args, rank, world, local_rank):
             peak = 1.25
             peak_src = "nominal GB300 FP64 1.25 TFLOP/s"
         ach = flops_per_launch / (per_launch_ms["contract"] / 1e3) / 1e12
-        kname = ("k_contract_chunk" if prec == P.NBS_FP32 and args.contract_cfg in (0, 2) else
-                 "k_contract_slab" if args.contract_cfg == 1 else "k_contract")
+        cfg = tuned["cfg"] if tuned else args.contract_cfg
+        kname = {0: "k_contract_quad", 5: "k_contract_quad", 2: "k_contract_chunk", 3: "k_contract_chunk2",
+                 1: "k_contract_slab"}.get(cfg, "k_contract") if prec == P.NBS_FP32 else \
+            ("k_contract_slab" if cfg == 1 else "k_contract")
+        traffic = None
+        if kname in DRAM_BYTES_PER_Q and prec == P.NBS_FP32:
+            traffic = DRAM_BYTES_PER_Q[kname] * V
         roof = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "peak_source": peak_src,
+                "frac": ach / peak, "traffic": traffic, "traffic_unit": "DRAM bytes per launch",
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at 16^3, "
+                                   "scaled by V" if traffic else None),
+                "peak_source": peak_src,
                 "work_per_launch": "8 flop x 64 x sum|xi~| (=%d) x V complex MACs of Eq. (4.3)"
                                    % int(tb["terms"][:, 1].sum())}
     else:

@@ -106,18 +106,24 @@ int nbs_zero_momentum(nbs_ctx* h, double* out);
 
 /* Launch-shape parameters (for tuning; results agree to rounding).
  * NBS_PARAM_CONTRACT_CFG selects the contraction kernel:
- *   0 = default: the chunk kernel in FP32 (when the channel tables fit its
- *       shared memory), the thread-per-momentum kernel (A = 2, W = 1) in FP64;
+ *   0 = default: the quad-lane chunk kernel (5) in FP32 when the channel
+ *       tables fit its shared memory, the thread-per-momentum kernel
+ *       (A = 2, W = 1) in FP64;
  *   1 = the momentum-slab kernel (one block per momentum and channel group,
  *       stored blocks staged in shared memory);
  *   2 = the chunk kernel (FP32; persistent blocks that keep a chunk of
  *       channels' compressed gather tables in shared memory and sweep a block
- *       of momenta with double-buffered slabs), else the default;
+ *       of momenta with double-buffered slabs; two lanes per shared index),
+ *       else the default;
+ *   3 = the chunk kernel's second form (FP32; same work split, cheaper inner
+ *       loops: signed coefficient table, no divergence), else the default;
+ *   5 = the quad-lane chunk kernel (FP32; four lanes per shared index, one
+ *       sink spin each, 16 warps per block), else the default;
  *   A*10 + W = the thread-per-momentum kernel with A sink spins alpha1 per
  *       thread (1, 2 or 4) and W warps per block (1, 2 or 4).
  * NBS_EINVAL for any other value. */
 #define NBS_PARAM_CONTRACT_CFG 0
-/* NBS_PARAM_CHUNK_QBLOCK: momenta per block of the chunk contraction (default 64). */
+/* NBS_PARAM_CHUNK_QBLOCK: momenta per block of the chunk contractions (default 32). */
 #define NBS_PARAM_CHUNK_QBLOCK 1
 int nbs_set_param(nbs_ctx* h, int param, int value);
 

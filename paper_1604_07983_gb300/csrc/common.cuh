@@ -91,6 +91,20 @@ cudaError_t launch_contract_chunk(const float2* FB, int L, int nchunks, int qb, 
                                   cudaStream_t st);
 // the same on the tensor cores, split-BF16 x 3 (kernels_tc.cu)
 size_t tc_smem_bytes(int st1, int st2, int max_slot, int max_tab);
+// second form of the chunk contraction (cheaper inner loops); max_row = the
+// largest gather row (n * held spins) of any term, at most 128
+size_t chunk2_smem_bytes(int st1, int st2, int max_slot, int max_tab);
+cudaError_t launch_contract_chunk2(const float2* FB, int L, int nchunks, int qb, const void* chunks,
+                                   const int* group_ch, const int* items, const DevTerm* terms, const int* tab_off,
+                                   const unsigned short* tab, const float* codes, int st1, int st2, int max_slot,
+                                   int max_tab, int max_row, float2* Ft, cudaStream_t st);
+// quad-lane chunk contraction (FP32): chunks points to QuadChunkHdr[nchunks]
+// (plan.h); max_cells = the largest stored type's cell count (<= 944)
+size_t quad_smem_bytes(int max_slot, int max_tab);
+cudaError_t launch_contract_quad(const float2* FB, int L, int nchunks, int qb, const void* chunks, const int* group_ch,
+                                 const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
+                                 const float* codes, int max_cells, int max_slot, int max_tab, int max_row, float2* Ft,
+                                 cudaStream_t st);
 cudaError_t launch_contract_tc(const float2* FB, int L, int nchunks, int qb, const void* chunks, const int* group_ch,
                                const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
                                const float* codes, int st1, int st2, int max_slot, int max_tab, float2* Ft,

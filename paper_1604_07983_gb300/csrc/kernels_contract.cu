@@ -656,6 +656,206 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_chunk(
   }
 }
 
+// ---- persistent chunk contraction, second form (FP32) -------------------------------------
+//
+// Same work split and output order as k_contract_chunk; the inner loops are
+// cheaper per table entry:
+//  * the coefficient comes from a 64-entry signed table indexed by the top six
+//    bits of the entry (code * 2 + sign), one shared load and no select;
+//  * the two 16-byte halves of a cell's four spins sit next to each other in
+//    the slab, so one base address serves both;
+//  * lanes past the end of a term read a row of zero-coefficient entries
+//    instead of branching, so the warp never diverges.
+
+constexpr int CHUNK2_ZROW = 128;  // zero-coefficient entries (>= max over terms of n * held spins)
+// slab plane stride (16-byte units): a compile-time constant so that the second
+// plane of a cell is an immediate offset; >= the cells of any stored type, and 4
+// mod 8 so that the two planes of one cell fall in different bank groups
+constexpr int CHUNK2_ST = 948;
+
+template <int SHAPE>
+__device__ __forceinline__ void chunk2_item(int n1, int n2, const unsigned short* p1, const unsigned short* p2,
+                                            const uint4* S1a, const uint4* S2, const float* sc, float (&acc)[64]) {
+  constexpr int NH1 = 1 << ((SHAPE & 1) + ((SHAPE >> 1) & 1));
+  constexpr int NH2 = 4 / NH1;
+  float2 v1[NH1][2], v2[NH2][4];
+#pragma unroll
+  for (int hh = 0; hh < NH1; ++hh) v1[hh][0] = v1[hh][1] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int hh = 0; hh < NH2; ++hh)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) v2[hh][b] = make_float2(0.f, 0.f);
+  for (int i = 0; i < n1; i += 2, p1 += 2 * NH1) {
+    unsigned e[2 * NH1];
+    load_codes<NH1>(p1, e);
+#pragma unroll
+    for (int j = 0; j < 2 * NH1; ++j) {
+      const float c = sc[e[j] >> 10];
+      const float4 x = *reinterpret_cast<const float4*>(S1a + (e[j] & 1023u));
+      v1[j % NH1][0].x = fmaf(c, x.x, v1[j % NH1][0].x);
+      v1[j % NH1][0].y = fmaf(c, x.y, v1[j % NH1][0].y);
+      v1[j % NH1][1].x = fmaf(c, x.z, v1[j % NH1][1].x);
+      v1[j % NH1][1].y = fmaf(c, x.w, v1[j % NH1][1].y);
+    }
+  }
+  for (int i = 0; i < n2; i += 2, p2 += 2 * NH2) {
+    unsigned e[2 * NH2];
+    load_codes<NH2>(p2, e);
+#pragma unroll
+    for (int j = 0; j < 2 * NH2; ++j) {
+      const float c = sc[e[j] >> 10];
+      const uint4* b = S2 + (e[j] & 1023u);
+      const float4 x = *reinterpret_cast<const float4*>(b);
+      const float4 y = *reinterpret_cast<const float4*>(b + CHUNK2_ST);
+      crfma<float>(v2[j % NH2][0], c, make_float2(x.x, x.y));
+      crfma<float>(v2[j % NH2][1], c, make_float2(x.z, x.w));
+      crfma<float>(v2[j % NH2][2], c, make_float2(y.x, y.y));
+      crfma<float>(v2[j % NH2][3], c, make_float2(y.z, y.w));
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int h1 = 0; h1 < NH1; ++h1)
+#pragma unroll
+        for (int h2 = 0; h2 < NH2; ++h2) {
+          int s;  // alpha3 + 2 alpha4
+          if (SHAPE == 0) s = h2;
+          else if (SHAPE == 3) s = h1;
+          else if (SHAPE == 1) s = h1 + 2 * h2;
+          else s = h2 + 2 * h1;
+          const int m = (a * 4 + b) * 4 + s;
+          float2 z = make_float2(acc[2 * m], acc[2 * m + 1]);
+          cfma<float>(z, v1[h1][a], v2[h2][b]);
+          acc[2 * m] = z.x;
+          acc[2 * m + 1] = z.y;
+        }
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, 1) k_contract_chunk2(
+    const float2* __restrict__ FB, int L, int nchunks, int qb, const ChunkHdr* __restrict__ chunks,
+    const int* __restrict__ group_ch, const int* __restrict__ items, const DevTerm* __restrict__ terms,
+    const int* __restrict__ tab_off, const unsigned short* __restrict__ tab, const float* __restrict__ codes, int st1,
+    int st2, int max_slot, int max_tab, float2* __restrict__ Ft) {
+  constexpr int NT = NW * 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned short* TAB = reinterpret_cast<unsigned short*>(smem_raw);
+  unsigned short* ZROW = TAB + max_tab;                                               // max_tab % 8 == 0
+  uint4* SB = reinterpret_cast<uint4*>(smem_raw + (size_t)(max_tab + CHUNK2_ZROW) * 2);
+  constexpr int slab = 4 * CHUNK2_ST;                                                 // uint4 per buffer
+  float2* OUT = reinterpret_cast<float2*>(SB + 2 * slab);
+  float* SC = reinterpret_cast<float*>(OUT + max_slot * 64);
+  if (threadIdx.x < 64) {
+    const float a = codes[threadIdx.x >> 1];
+    SC[threadIdx.x] = (threadIdx.x & 1) ? -a : a;
+  }
+  for (int i = threadIdx.x; i < CHUNK2_ZROW; i += NT) ZROW[i] = (unsigned short)(31u << 11);
+  const long long V = (long long)L * L * L;
+  const int ci = blockIdx.x % nchunks;
+  const long long q_begin = (long long)(blockIdx.x / nchunks) * qb;
+  const long long q_end = min(V, q_begin + qb);
+  const ChunkHdr& ck = chunks[ci];
+  const int base1 = ck.base1, n1c = ck.ncell1, base2 = ck.base2, n2c = ck.ncell2;
+
+  // slab layout: four planes of CHUNK2_ST 16-byte slots (side 1 spins 0-1, side 1
+  // spins 2-3, side 2 spins 0-1, side 2 spins 2-3), indexed by cell
+  auto issue_slabs = [&](long long q, uint4* S) {
+    const int qx = (int)(q % L), qy = (int)((q / L) % L), qz = (int)(q / ((long long)L * L));
+    const long long qm = (L - qx) % L + L * ((L - qy) % L + (long long)L * ((L - qz) % L));
+    for (int i = threadIdx.x; i < 2 * n1c; i += NT) {
+      const int c = i >> 1, p = i & 1;
+      cp_async16b(S + p * CHUNK2_ST + c,
+                  reinterpret_cast<const char*>(FB + ((long long)(base1 + c) * V + q) * 4) + 16 * p);
+    }
+    uint4* S2 = S + 2 * CHUNK2_ST;
+    for (int i = threadIdx.x; i < 2 * n2c; i += NT) {
+      const int c = i >> 1, p = i & 1;
+      cp_async16b(S2 + p * CHUNK2_ST + c,
+                  reinterpret_cast<const char*>(FB + ((long long)(base2 + c) * V + qm) * 4) + 16 * p);
+    }
+  };
+
+  for (int i = threadIdx.x; i < ck.tab_len / 8; i += NT)
+    cp_async16b(TAB + 8 * i, tab + ck.tab_off + 8 * i);
+  if (q_begin < q_end) issue_slabs(q_begin, SB);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (int i = threadIdx.x; i < ck.nslot * 64; i += NT) OUT[i] = make_float2(0.f, 0.f);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ag = lane & 1, kk = lane >> 1;
+  const int it0 = ck.item_off + ck.warp_off[w], it1 = ck.item_off + ck.warp_off[w + 1];
+  for (long long q = q_begin; q < q_end; ++q) {
+    uint4* S = SB + ((q - q_begin) & 1) * slab;
+    if (q + 1 < q_end) issue_slabs(q + 1, SB + ((q + 1 - q_begin) & 1) * slab);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    const uint4* S1a = S + ag * CHUNK2_ST;
+    const uint4* S2 = S + 2 * CHUNK2_ST;
+    float acc[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+    int cur = -1;
+    for (int it = it0; it < it1; ++it) {
+      const int term = items[2 * it], k0 = items[2 * it + 1];
+      const DevTerm h = terms[term];
+      const int local = h.pad - ck.ch_local0;
+      if (local != cur) {
+        if (cur >= 0) {
+          pair_reduce_stage<16>(acc, lane);
+          float2* o = OUT + (ck.out_base[w] + cur - ck.cfirst[w]) * 64 + ag * 32 + 2 * kk;
+          o[0].x += acc[0]; o[0].y += acc[1]; o[1].x += acc[2]; o[1].y += acc[3];
+#pragma unroll
+          for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+        }
+        cur = local;
+      }
+      const unsigned short* T1 = TAB + tab_off[2 * term];
+      const unsigned short* T2 = TAB + tab_off[2 * term + 1];
+      const int nh1 = 1 << ((h.shape & 1) + ((h.shape >> 1) & 1));
+      for (int kb = 0; kb < 32 && k0 + kb < h.K; kb += 16) {
+        const int k = k0 + kb + kk;
+        const bool active = k < h.K;
+        const unsigned short* p1 = active ? T1 + k * nh1 * h.n1 : ZROW;
+        const unsigned short* p2 = active ? T2 + k * (4 / nh1) * h.n2 : ZROW;
+        switch (h.shape) {
+          case 0: chunk2_item<0>(h.n1, h.n2, p1, p2, S1a, S2, SC, acc); break;
+          case 1: chunk2_item<1>(h.n1, h.n2, p1, p2, S1a, S2, SC, acc); break;
+          case 2: chunk2_item<2>(h.n1, h.n2, p1, p2, S1a, S2, SC, acc); break;
+          default: chunk2_item<3>(h.n1, h.n2, p1, p2, S1a, S2, SC, acc); break;
+        }
+      }
+    }
+    if (cur >= 0) {
+      pair_reduce_stage<16>(acc, lane);
+      float2* o = OUT + (ck.out_base[w] + cur - ck.cfirst[w]) * 64 + ag * 32 + 2 * kk;
+      o[0].x += acc[0]; o[0].y += acc[1]; o[1].x += acc[2]; o[1].y += acc[3];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ck.nch * 64; i += NT) {
+      const int c = i / 64, m = i % 64;
+      float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int ww = 0; ww < NW; ++ww) {  // fixed order
+        const int r = c - ck.cfirst[ww];
+        if (r >= 0 && r < ck.out_base[ww + 1] - ck.out_base[ww]) {
+          float2& v = OUT[(ck.out_base[ww] + r) * 64 + m];
+          sum.x += v.x;
+          sum.y += v.y;
+          v = make_float2(0.f, 0.f);
+        }
+      }
+      const int spin = (m & ~3) + 2 * (m & 1) + ((m >> 1) & 1);
+      Ft[((long long)group_ch[ck.ch_off + c] * 64 + spin) * V + q] = sum;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+  }
+}
+
 // f * 2^ex as a double, by integer operations on the bit pattern (exact): a
 // normal FP32 value keeps its sign and mantissa and gets the FP64 exponent
 // E - 127 + 1023 + ex; zeros stay zeros; FP32 subnormals, infinities, NaNs
@@ -783,6 +983,31 @@ cudaError_t launch_contract_chunk(const float2* FB, int L, int nchunks, int qb, 
   if (e != cudaSuccess) return e;
   const long long nqb = (V + qb - 1) / qb;
   if (nqb * nchunks > 2147483647LL || max_tab % 8) return cudaErrorInvalidValue;
+  kern<<<(unsigned)(nqb * nchunks), NBS_CHUNK_WARPS * 32, sm, st>>>(FB, L, nchunks, qb, (const ChunkHdr*)chunks,
+                                                                    group_ch, items, terms, tab_off, tab, codes, st1, st2,
+                                                                    max_slot, max_tab, Ft);
+  return cudaGetLastError();
+}
+
+size_t chunk2_smem_bytes(int st1, int st2, int max_slot, int max_tab) {
+  (void)st1;
+  (void)st2;
+  return (size_t)(max_tab + CHUNK2_ZROW) * 2 + (size_t)2 * 4 * CHUNK2_ST * 16 +
+         (size_t)max_slot * 64 * sizeof(float2) + 64 * sizeof(float);
+}
+
+cudaError_t launch_contract_chunk2(const float2* FB, int L, int nchunks, int qb, const void* chunks,
+                                   const int* group_ch, const int* items, const DevTerm* terms, const int* tab_off,
+                                   const unsigned short* tab, const float* codes, int st1, int st2, int max_slot,
+                                   int max_tab, int max_row, float2* Ft, cudaStream_t st) {
+  const long long V = (long long)L * L * L;
+  const size_t sm = chunk2_smem_bytes(st1, st2, max_slot, max_tab);
+  if (max_row > CHUNK2_ZROW || max_tab % 8 || st1 > CHUNK2_ST || st2 > CHUNK2_ST) return cudaErrorInvalidValue;
+  auto kern = k_contract_chunk2<NBS_CHUNK_WARPS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const long long nqb = (V + qb - 1) / qb;
+  if (nqb * nchunks > 2147483647LL) return cudaErrorInvalidValue;
   kern<<<(unsigned)(nqb * nchunks), NBS_CHUNK_WARPS * 32, sm, st>>>(FB, L, nchunks, qb, (const ChunkHdr*)chunks,
                                                                     group_ch, items, terms, tab_off, tab, codes, st1, st2,
                                                                     max_slot, max_tab, Ft);

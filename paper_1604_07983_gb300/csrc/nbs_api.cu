@@ -83,9 +83,9 @@ struct nbs_ctx {
   int plan_gen = 0;
   DevBuf d_terms, d_chtb, d_chnl, d_e1, d_e2, d_cells, d_groups, d_gch, d_items;
   int slab_st1 = 0, slab_st2 = 0, slab_nch = 0;
-  DevBuf d_chunks, d_ctab, d_citems, d_ctoff, d_codes;
-  int chunk_st1 = 0, chunk_st2 = 0, chunk_slot = 0, chunk_tab = 0;
-  int chunk_qb = 64;
+  DevBuf d_chunks, d_qchunks, d_ctab, d_citems, d_ctoff, d_codes;
+  int chunk_st1 = 0, chunk_st2 = 0, chunk_slot = 0, chunk_tab = 0, chunk_row = 0, quad_slot = 0;
+  int chunk_qb = 32;
   int tables_mode = -1;
   TypeRecipeSet recipes;
 
@@ -198,14 +198,26 @@ int upload_tables(nbs_ctx* h) {
       h->chunk_slot = std::max(h->chunk_slot, c.nslot);
       h->chunk_tab = std::max(h->chunk_tab, c.tab_len);
     }
+    h->quad_slot = 0;
+    for (const QuadChunkHdr& c : P.quad_chunks) h->quad_slot = std::max(h->quad_slot, c.nslot);
+    h->chunk_row = 0;
+    for (const TermHdr& t : P.terms) {
+      const int nh1 = 1 << ((t.shape & 1) + ((t.shape >> 1) & 1));
+      h->chunk_row = std::max(h->chunk_row, std::max(t.n1 * nh1, t.n2 * (4 / nh1)));
+    }
     float codes[32] = {};
     for (size_t i = 0; i < P.coef_codes.size() && i < 31; ++i) codes[i] = (float)P.coef_codes[i];
     if ((rc = ensure(h, h->d_chunks, std::max<size_t>(P.chunks.size(), 1) * sizeof(ChunkHdr), "chunks"))) return rc;
+    if ((rc = ensure(h, h->d_qchunks, std::max<size_t>(P.quad_chunks.size(), 1) * sizeof(QuadChunkHdr), "quad chunks")))
+      return rc;
     if ((rc = ensure(h, h->d_ctab, std::max<size_t>(P.chunk_tab.size(), 8) * 2, "chunk tables"))) return rc;
     if ((rc = ensure(h, h->d_citems, std::max<size_t>(P.chunk_items.size(), 1) * sizeof(int), "chunk items"))) return rc;
     if ((rc = ensure(h, h->d_ctoff, std::max<size_t>(P.term_tab_off.size(), 1) * sizeof(int), "table offsets"))) return rc;
     if ((rc = ensure(h, h->d_codes, sizeof(codes), "coefficient codes"))) return rc;
     CK(cudaMemcpyAsync(h->d_chunks.p, P.chunks.data(), P.chunks.size() * sizeof(ChunkHdr), cudaMemcpyHostToDevice, h->st), "upload chunks");
+    CK(cudaMemcpyAsync(h->d_qchunks.p, P.quad_chunks.data(), P.quad_chunks.size() * sizeof(QuadChunkHdr),
+                       cudaMemcpyHostToDevice, h->st),
+       "upload quad chunks");
     CK(cudaMemcpyAsync(h->d_ctab.p, P.chunk_tab.data(), P.chunk_tab.size() * 2, cudaMemcpyHostToDevice, h->st), "upload chunk tables");
     CK(cudaMemcpyAsync(h->d_citems.p, P.chunk_items.data(), P.chunk_items.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload chunk items");
     CK(cudaMemcpyAsync(h->d_ctoff.p, P.term_tab_off.data(), P.term_tab_off.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload table offsets");
@@ -342,8 +354,9 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
       if ((rc = build_blocks<T>(h, t))) return rc;
     }
     cudaEvent_t e3 = stage_begin(h);
-    // default in FP32: the chunk kernel when the tables fit; FP64: the thread-per-momentum kernel
-    const bool use_chunk = (h->contract_cfg == 2 || h->contract_cfg == 0) && sizeof(T) == 4 && h->plan.chunks_ok;
+    // default in FP32: the quad-lane chunk kernel when the tables fit; FP64: the thread-per-momentum kernel
+    const bool f32_chunks = sizeof(T) == 4 && h->plan.chunks_ok;
+    const bool use_quad = f32_chunks && (h->contract_cfg == 0 || h->contract_cfg == 5);
     if (h->mode == NBS_BF16X3) {
       if (!h->plan.chunks_ok) return fail(h, NBS_EINVAL, "BF16X3 needs channel tables that fit the chunk kernel");
       CK(launch_contract_tc((const float2*)h->FB.p, h->L, (int)h->plan.chunks.size(), h->chunk_qb, h->d_chunks.p,
@@ -351,7 +364,22 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
                             (const int*)h->d_ctoff.p, (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
                             h->chunk_st1, h->chunk_st2, h->chunk_slot, h->chunk_tab, (float2*)h->Ft.p, h->st),
          "contraction (tensor cores)");
-    } else if (use_chunk) {
+    } else if (use_quad) {
+      CK(launch_contract_quad((const float2*)h->FB.p, h->L, (int)h->plan.quad_chunks.size(), h->chunk_qb,
+                              h->d_qchunks.p, (const int*)h->d_gch.p, (const int*)h->d_citems.p,
+                              (const DevTerm*)h->d_terms.p, (const int*)h->d_ctoff.p,
+                              (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
+                              std::max(h->chunk_st1, h->chunk_st2), h->quad_slot, h->chunk_tab, h->chunk_row,
+                              (float2*)h->Ft.p, h->st),
+         "contraction");
+    } else if (f32_chunks && h->contract_cfg == 3) {
+      CK(launch_contract_chunk2((const float2*)h->FB.p, h->L, (int)h->plan.chunks.size(), h->chunk_qb,
+                                h->d_chunks.p, (const int*)h->d_gch.p, (const int*)h->d_citems.p,
+                                (const DevTerm*)h->d_terms.p, (const int*)h->d_ctoff.p,
+                                (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p, h->chunk_st1,
+                                h->chunk_st2, h->chunk_slot, h->chunk_tab, h->chunk_row, (float2*)h->Ft.p, h->st),
+         "contraction");
+    } else if (f32_chunks && h->contract_cfg == 2) {
       CK(launch_contract_chunk((const float2*)h->FB.p, h->L, (int)h->plan.chunks.size(), h->chunk_qb, h->d_chunks.p,
                                (const int*)h->d_gch.p, (const int*)h->d_citems.p, (const DevTerm*)h->d_terms.p,
                                (const int*)h->d_ctoff.p, (const unsigned short*)h->d_ctab.p,
@@ -366,7 +394,7 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
          "contraction");
     } else {
       // configs 1 and 2 name other kernels; where the chunk kernel cannot run (FP64) use the default shape
-      const int cfg = h->contract_cfg <= 2 ? 0 : h->contract_cfg;
+      const int cfg = h->contract_cfg <= 5 ? 0 : h->contract_cfg;
       CK(launch_contract<T>((const C<T>*)h->FB.p, h->L, (const DevTerm*)h->d_terms.p, (const int*)h->d_chtb.p, nch,
                             (const Ent<T>*)h->d_e1.p, (const Ent<T>*)h->d_e2.p, (C<T>*)h->Ft.p, cfg, h->st),
          "contraction");
@@ -551,8 +579,8 @@ int nbs_set_param(nbs_ctx* h, int param, int value) {
   switch (param) {
     case NBS_PARAM_CONTRACT_CFG: {
       const int a = value / 10, w = value % 10;
-      if (value != 0 && value != 1 && value != 2 && !((a == 1 || a == 2 || a == 4) && (w == 1 || w == 2 || w == 4)))
-        return fail(h, NBS_EINVAL, "contraction config must be 0, 1, 2 or A*10+W with A, W in {1, 2, 4}");
+      if (!(value >= 0 && value <= 5 && value != 4) && !((a == 1 || a == 2 || a == 4) && (w == 1 || w == 2 || w == 4)))
+        return fail(h, NBS_EINVAL, "contraction config must be 0, 1, 2, 3, 5 or A*10+W with A, W in {1, 2, 4}");
       h->contract_cfg = value;
       return NBS_OK;
     }

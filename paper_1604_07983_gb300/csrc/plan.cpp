@@ -250,6 +250,7 @@ void build_chunks(Plan& plan) {
   plan.chunks.clear();
   plan.chunk_tab.clear();
   plan.chunk_items.clear();
+  plan.quad_chunks.clear();
   plan.term_tab_off.assign(2 * plan.terms.size(), 0);
   plan.coef_codes.clear();
   plan.chunks_ok = false;
@@ -288,7 +289,7 @@ void build_chunks(Plan& plan) {
       ck.tab_off = (int)plan.chunk_tab.size();
       ck.item_off = (int)plan.chunk_items.size() / 2;
       std::vector<std::pair<int, int>> its;
-      std::vector<double> cost;
+      std::vector<double> cost, qcost;
       for (int local = c; local < c_end; ++local) {
         const int ci = plan.group_ch[g.ch_off + local];
         for (int t = plan.ch_term_begin[ci]; t < plan.ch_term_begin[ci + 1]; ++t) {
@@ -315,35 +316,52 @@ void build_chunks(Plan& plan) {
             while ((plan.chunk_tab.size() - ck.tab_off) % 8) plan.chunk_tab.push_back((unsigned short)(0x1F << 11));
           }
           for (int k0 = 0; k0 < th.K; k0 += 32) {
+            // warp instructions per step ~ a fixed part (products, loop control) plus
+            // one part per gather entry of a shared index (ratios from instruction counts)
+            const double ent = nh1 * th.n1 + nh2 * th.n2;
+            const int nkb = (std::min(32, th.K - k0) + 15) / 16;  // pair lanes: 16 indices per step
             its.push_back({t, k0});
-            cost.push_back(64.0 + 4.0 * (nh1 * th.n1 + nh2 * th.n2));
+            cost.push_back(nkb * (26.0 + ent));
+            const int nks = (std::min(32, th.K - k0) + 7) / 8;    // quad lanes: 8 indices per step
+            qcost.push_back(nks * (23.0 + ent));
           }
         }
       }
       ck.tab_len = (int)plan.chunk_tab.size() - ck.tab_off;
-      double total = 0;
-      for (double x : cost) total += x;
-      int w = 0;
-      double acc = 0;
-      ck.warp_off[0] = 0;
-      for (size_t i = 0; i < its.size(); ++i) {
-        acc += cost[i];
-        if (w < NBS_CHUNK_WARPS - 1 && acc >= total * (w + 1) / NBS_CHUNK_WARPS) ck.warp_off[++w] = (int)i + 1;
-      }
-      while (w < NBS_CHUNK_WARPS) ck.warp_off[++w] = (int)its.size();
-      ck.out_base[0] = 0;
-      for (int ww = 0; ww < NBS_CHUNK_WARPS; ++ww) {
-        int n = 0;
-        ck.cfirst[ww] = 0;
-        if (ck.warp_off[ww + 1] > ck.warp_off[ww]) {
-          const int c0 = plan.terms[its[ck.warp_off[ww]].first].pad - c;
-          const int c1 = plan.terms[its[ck.warp_off[ww + 1] - 1].first].pad - c;
-          ck.cfirst[ww] = c0;
-          n = c1 - c0 + 1;
+      // contiguous per-warp item ranges of about equal cost, and the partial-sum
+      // slots each warp needs (one per channel its range touches)
+      auto split = [&](const std::vector<double>& cst, int nw, int* warp_off, int* out_base, int* cfirst) {
+        double total = 0;
+        for (double x : cst) total += x;
+        int w = 0;
+        double acc = 0;
+        warp_off[0] = 0;
+        for (size_t i = 0; i < its.size(); ++i) {
+          acc += cst[i];
+          if (w < nw - 1 && acc >= total * (w + 1) / nw) warp_off[++w] = (int)i + 1;
         }
-        ck.out_base[ww + 1] = ck.out_base[ww] + n;
-      }
-      ck.nslot = ck.out_base[NBS_CHUNK_WARPS];
+        while (w < nw) warp_off[++w] = (int)its.size();
+        out_base[0] = 0;
+        for (int ww = 0; ww < nw; ++ww) {
+          int n = 0;
+          cfirst[ww] = 0;
+          if (warp_off[ww + 1] > warp_off[ww]) {
+            const int c0 = plan.terms[its[warp_off[ww]].first].pad - c;
+            const int c1 = plan.terms[its[warp_off[ww + 1] - 1].first].pad - c;
+            cfirst[ww] = c0;
+            n = c1 - c0 + 1;
+          }
+          out_base[ww + 1] = out_base[ww] + n;
+        }
+        return out_base[nw];
+      };
+      ck.nslot = split(cost, NBS_CHUNK_WARPS, ck.warp_off, ck.out_base, ck.cfirst);
+      QuadChunkHdr qk = {};
+      qk.base1 = ck.base1; qk.ncell1 = ck.ncell1; qk.base2 = ck.base2; qk.ncell2 = ck.ncell2;
+      qk.ch_off = ck.ch_off; qk.nch = ck.nch; qk.tab_off = ck.tab_off; qk.tab_len = ck.tab_len;
+      qk.item_off = ck.item_off; qk.ch_local0 = ck.ch_local0;
+      qk.nslot = split(qcost, NBS_QUAD_WARPS, qk.warp_off, qk.out_base, qk.cfirst);
+      plan.quad_chunks.push_back(qk);
       for (auto& it : its) {
         plan.chunk_items.push_back(it.first);
         plan.chunk_items.push_back(it.second);
@@ -621,7 +639,7 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
       g.item_off = (int)plan.items.size() / 2;
       // items in channel order, with their cost
       std::vector<std::pair<int, int>> its;
-      std::vector<double> cost;
+      std::vector<double> cost, qcost;
       for (int local = 0; local < g.nch; ++local) {
         const int ci = kv.second[local];
         plan.group_ch.push_back(ci);
@@ -630,8 +648,14 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
           th.pad = local;
           const int nh1 = 1 << ((th.shape & 1) + (th.shape >> 1 & 1)), nh2 = 4 / nh1;
           for (int k0 = 0; k0 < th.K; k0 += 32) {
+            // warp instructions per step ~ a fixed part (products, loop control) plus
+            // one part per gather entry of a shared index (ratios from instruction counts)
+            const double ent = nh1 * th.n1 + nh2 * th.n2;
+            const int nkb = (std::min(32, th.K - k0) + 15) / 16;  // pair lanes: 16 indices per step
             its.push_back({t, k0});
-            cost.push_back(64.0 + 4.0 * (nh1 * th.n1 + nh2 * th.n2));
+            cost.push_back(nkb * (26.0 + ent));
+            const int nks = (std::min(32, th.K - k0) + 7) / 8;    // quad lanes: 8 indices per step
+            qcost.push_back(nks * (23.0 + ent));
           }
         }
       }

@@ -69,6 +69,22 @@ struct ChunkHdr {
   int pad[3];
 };
 
+// The same chunks split over NBS_QUAD_WARPS warps for the quad-lane contraction
+// (four lanes per shared index, eight indices per warp step): same tables and
+// items, its own per-warp item ranges and partial-sum slots.
+#define NBS_QUAD_WARPS 16
+struct QuadChunkHdr {
+  int base1, ncell1, base2, ncell2;
+  int ch_off, nch;
+  int tab_off, tab_len;
+  int item_off, nslot;
+  int warp_off[NBS_QUAD_WARPS + 1];
+  int out_base[NBS_QUAD_WARPS + 1];
+  int cfirst[NBS_QUAD_WARPS];
+  int ch_local0;
+  int pad[3];
+};
+
 struct Plan {
   std::vector<int> channels;                  // built-in ids, in request order
   std::vector<BlockType> types;
@@ -87,6 +103,7 @@ struct Plan {
   std::vector<int> chunk_items;               // pairs (term, k0)
   std::vector<int> term_tab_off;              // per term: side-1, side-2 offsets inside its chunk's table
   std::vector<double> coef_codes;             // |coefficient| of each code
+  std::vector<QuadChunkHdr> quad_chunks;      // one per chunk (valid when chunks_ok)
   // flops of the contraction per q (complex multiply-adds), for rooflines
   double cmac_per_q = 0, gathers_per_q = 0;
 };

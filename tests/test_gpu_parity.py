@@ -115,7 +115,7 @@ def test_fp32_all_channels_L4(nbs):
         assert rel(F32[c, 0], ref) < FP32_TOL, names[c]
 
 
-@pytest.mark.parametrize("cfg", [1, 2, 22, 11])
+@pytest.mark.parametrize("cfg", [1, 2, 3, 5, 22, 11])
 def test_contraction_variants_all_channels(nbs, cfg):
     """Every contraction kernel and launch shape against the oracle, FP64 and FP32, all 52 channels."""
     L = 3
@@ -128,6 +128,29 @@ def test_contraction_variants_all_channels(nbs, cfg):
         ref = oracle(names[c], *props[0], L)
         assert rel(F64[c, 0], ref) < FP64_TOL, (cfg, names[c])
         assert rel(F32[c, 0], ref) < FP32_TOL, (cfg, names[c])
+
+
+def test_chunk_kernel_forms_agree_bitwise(nbs):
+    """The two forms of the chunk contraction (configs 2, 3) do the same FP32 operations in the same
+    order: identical results, here with a momentum block (24) that leaves a ragged last block at 4^3.
+    The quad-lane form (config 5, the default) sums in another order: equal to FP32 rounding."""
+    L = 4
+    props = seeded(1723, L, 1, decay=0.5)
+    ids = list(range(nbs.channel_count()))
+    out = []
+    for cfg in (2, 3, 5):
+        with nbs.Context(L, 1, precision=nbs.NBS_FP32) as ctx:
+            ctx.set_param(ctx.PARAM_CONTRACT_CFG, cfg)
+            ctx.set_param(ctx.PARAM_CHUNK_QBLOCK, 24)
+            ctx.load_props(torch.from_numpy(props[0][0]).cuda(), torch.from_numpy(props[0][1]).cuda(), 0)
+            o = torch.empty((len(ids), 1, 4, 4, 2, 2, L ** 3), dtype=torch.complex128, device="cuda")
+            ctx.correlate(ids, 0, 1, o)
+            torch.cuda.synchronize()
+            out.append(o.cpu().numpy())
+    assert np.isfinite(out[0]).all()
+    assert np.array_equal(out[0], out[1])
+    for c in ids:
+        assert rel(out[2][c], out[0][c]) < 1e-6, c
 
 
 def test_bf16x3_tensor_core_path_all_channels(nbs):
