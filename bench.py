@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--c64", action="store_true", help="store the propagators as complex64 (the 48^3 x 64 config)")
     ap.add_argument("--decay", type=float, default=DECAY)
     ap.add_argument("--autotune", action="store_true", help="pick the contraction shape with the autotuner first")
+    ap.add_argument("--no-graphs", action="store_true", help="batched workload without CUDA graphs")
     ap.add_argument("--workload", choices=["single", "batched"], default="single",
                     help="batched: six configurations 2x16^3x32, 2x24^3x48, 2x32^3x32, every timeslice")
     return ap.parse_args()
@@ -323,24 +324,28 @@ def run_ours(args, rank, world, local_rank):
     value = job_rate(nch * args.steps, world, ms / 1e3)
 
     # ---- end to end through the public API with host buffers ----
-    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    # every step's propagators are copied in from pinned host memory (nbs_load_props), then one
+    # nbs_correlate call over those timeslices writes every result to pinned host memory; inside
+    # the call the copy-out of timeslice t overlaps the compute of t + 1
+    e2e_steps = max(1, min(args.e2e_steps, args.steps, T))
     pin_u = [torch.from_numpy(Sl).pin_memory() for Sl, _ in host_props[:e2e_steps]]
     pin_s = [torch.from_numpy(Ss).pin_memory() for _, Ss in host_props[:e2e_steps]]
-    out_h = torch.empty((nch, 1, 4, 4, 2, 2, V), dtype=torch.complex128).pin_memory()
+    out_h = torch.empty((nch, e2e_steps, 4, 4, 2, 2, V), dtype=torch.complex128).pin_memory()
+    out_w = torch.empty((nch, 1, 4, 4, 2, 2, V), dtype=torch.complex128).pin_memory()
     ctx.set_profiling(False)
     ctx.load_props(pin_u[0], pin_s[0], 0)
-    ctx.correlate(ids, 0, 1, out_h)
+    ctx.correlate(ids, 0, 1, out_w)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         ctx.load_props(pin_u[k], pin_s[k], k)
-        ctx.correlate(ids, k, k + 1, out_h)
+    ctx.correlate(ids, 0, e2e_steps, out_h)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e_value = job_rate(nch * e2e_steps, world, e2e_s)
-    h2d = 2 * V * 144 * 16
+    h2d = 2 * V * 144 * (8 if args.c64 else 16)
     d2h = nch * 64 * V * 16
     ctx.close()
 
@@ -416,7 +421,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof,
         "stages_ms_per_step": {k: round(v, 4) for k, v in per_launch_ms.items()},
         "gpu_launches": int(launches),
-        "contraction_shape": {"cfg": tuned["cfg"], "qb": tuned["qb"], "timings": tuned["timings"]} if tuned else
+        "contraction_shape": {"cfg": tuned["cfg"], "qb": tuned["qb"], "timings": tuned["timings"],
+                              "fft_block": tuned["fft_block"], "fft_timings": tuned["fft_timings"]} if tuned else
                              {"cfg": args.contract_cfg, "qb": args.qblock},
         "clocks": clocks.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -434,7 +440,9 @@ BATCH = [(16, 32), (16, 32), (24, 48), (24, 48), (32, 32), (32, 32)]
 
 def run_batched(args, rank, world, P, prec, ids, dist=None):
     """Six configurations of uneven size (seeds 1608..1613), every timeslice of each, one
-    context per configuration; a step is one timeslice of one configuration."""
+    context per configuration; a step is one timeslice of one configuration.  Each
+    (configuration, timeslice) is captured once as a CUDA graph (nbs_graph_capture) and the
+    timed region replays the 224 graphs back to back (--no-graphs: plain nbs_correlate calls)."""
     import torch
     nch = len(ids)
     ctxs, outs, jobs = [], [], []
@@ -446,8 +454,13 @@ def run_batched(args, rank, world, P, prec, ids, dist=None):
         ctxs.append(ctx)
         outs.append(torch.empty((nch, 1, 4, 4, 2, 2, L ** 3), dtype=torch.complex128, device="cuda"))
         jobs += [(ci, t) for t in range(T)]
-    for ci in range(len(BATCH)):  # warm-up: one timeslice per configuration
+    for ci in range(len(BATCH)):  # warm-up (allocates every buffer): one timeslice per configuration
         ctxs[ci].correlate(ids, 0, 1, outs[ci])
+    graphs = None
+    if not args.no_graphs:
+        graphs = [ctxs[ci].capture(ids, t, t + 1, outs[ci]) for ci, t in jobs]
+        for ci in range(len(BATCH)):
+            graphs[jobs.index((ci, 0))].launch()
     torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clocks:
@@ -455,8 +468,12 @@ def run_batched(args, rank, world, P, prec, ids, dist=None):
             dist.barrier()
         torch.cuda.synchronize()
         start.record()
-        for ci, t in jobs:
-            ctxs[ci].correlate(ids, t, t + 1, outs[ci])
+        if graphs:
+            for g in graphs:
+                g.launch(wait=False)
+        else:
+            for ci, t in jobs:
+                ctxs[ci].correlate(ids, t, t + 1, outs[ci])
         stop.record()
         torch.cuda.synchronize()
         if dist:
@@ -471,7 +488,10 @@ def run_batched(args, rank, world, P, prec, ids, dist=None):
             "n_gpus": world, "steps": len(jobs), "warmup": len(BATCH), "ms_per_step": ms / len(jobs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec != P.NBS_FP64 else "f64", "data": "synthetic, seeds 1608-1613",
-            "config": {"workload": "6 configurations, %d timeslices, all %d channels" % (len(jobs), nch)},
+            "config": {"workload": "6 configurations, %d timeslices, all %d channels" % (len(jobs), nch),
+                       "launch": "one captured CUDA graph per (configuration, timeslice)" if graphs else
+                                 "nbs_correlate per (configuration, timeslice)"},
+            "gpu_launches": sum(12 if BATCH[ci][0] > 1 else 6 for ci, _ in jobs),
             "clocks": clocks.summary()}), flush=True)
 
 

@@ -56,6 +56,7 @@ extern "C" {
 
 typedef struct nbs_ctx nbs_ctx;
 typedef struct nbs_plan nbs_plan;
+typedef struct nbs_graph nbs_graph;
 
 /* Device allocator hook: alloc(bytes, user) returns a device pointer or NULL;
  * free(ptr, user).  Installed per process before nbs_create; NULL restores
@@ -93,12 +94,41 @@ int nbs_blocks(nbs_ctx* h, int t);
  * nbs_channel_info) for timeslices t_begin <= t < t_end.  For each t the
  * blocks are (re)built when needed, the effective blocks are formed and
  * multiplied in momentum space (Eqs. (4.2)-(4.3)), and the inverse FFT
- * gives F(r).  out: caller-allocated complex128
+ * gives F(r).  Source spins: id c (0 <= c < nbs_channel_count()) projects
+ * them onto the upper components, alpha3, alpha4 in {0, 1}; id c + k *
+ * nbs_channel_count() with k = 1, 2, 3 onto alpha3 in {2 (k & 1),
+ * 2 (k & 1) + 1} and alpha4 in {2 (k >> 1), 2 (k >> 1) + 1}, so the four
+ * ids c + k n cover the full 4 x 4 source spin of Eq. (2.4).
+ * out: caller-allocated complex128
  *   [n_channels][t_end - t_begin][a1][a2][a3][a4][z][y][x]
+ * (a3, a4 in {0, 1} relative to the id's source spin pair)
  * on the device (out_on_device = 1) or on the host (0; pinned memory is
  * copied asynchronously per timeslice).  Returns when `out` is complete. */
 int nbs_correlate(nbs_ctx* h, const int* channel_ids, int n_channels,
                   int t_begin, int t_end, void* out, int out_on_device);
+
+/* CUDA-graph form of nbs_correlate for repeated work lists (the paper
+ * launches the same kernels for every timeslice and configuration).
+ * nbs_graph_capture records, without running it, the device work that
+ * nbs_correlate(h, channel_ids, n_channels, t_begin, t_end, out, 1) would
+ * do -- rescale, blocks, forward FFT, contraction, inverse FFT, restore for
+ * every timeslice of the range -- into a CUDA graph that the context's stream
+ * replays with nbs_graph_launch.  A replay reads the propagators loaded in
+ * the context at that time (load new ones with nbs_load_props between
+ * replays, same storage type) and writes the same device buffer `out`
+ * (complex128, layout of nbs_correlate).  The caller owns the graph
+ * (nbs_graph_destroy) and must destroy it before the context.
+ * Preconditions: profiling off; propagators loaded for every t of the
+ * range.  Every buffer the path needs is allocated before the capture.
+ * nbs_graph_launch returns NBS_ESTATE if the context's buffers were
+ * reallocated (a later call with more channels or another precision) or a
+ * timeslice's storage type changed since the capture, NBS_ENAN after a
+ * waited replay whose propagators held a non-finite value.  wait = 0 returns
+ * after the launch; synchronise the context's stream before reading `out`. */
+int nbs_graph_capture(nbs_ctx* h, const int* channel_ids, int n_channels, int t_begin, int t_end,
+                      void* out, nbs_graph** graph);
+int nbs_graph_launch(nbs_graph* graph, int wait);
+int nbs_graph_destroy(nbs_graph* graph);
 
 /* Zero-momentum projection of the last nbs_correlate's final timeslice,
  * sum_r F(r) = F~(q = 0), complex128 [n_channels][64] on the host. */
@@ -125,6 +155,9 @@ int nbs_zero_momentum(nbs_ctx* h, double* out);
 #define NBS_PARAM_CONTRACT_CFG 0
 /* NBS_PARAM_CHUNK_QBLOCK: momenta per block of the chunk contractions (default 32). */
 #define NBS_PARAM_CHUNK_QBLOCK 1
+/* NBS_PARAM_FFT_BLOCK: threads per block of the strided (y, z) passes of the
+ * 3-D FFTs: 64, 128 (default) or 256. */
+#define NBS_PARAM_FFT_BLOCK 2
 int nbs_set_param(nbs_ctx* h, int param, int value);
 
 /* Profiling (stage timing with CUDA events on the context's stream).

@@ -60,6 +60,13 @@ for _a, _b, _c in itertools.permutations(range(3)):
 PROJ = np.zeros((4, 2))
 PROJ[0, 0] = PROJ[1, 1] = 1.0
 
+
+def projector(offset: int) -> np.ndarray:
+    """delta(alpha', alpha) for the source spin pair alpha in {2 offset, 2 offset + 1} (offset 0: PROJ)."""
+    P = np.zeros((4, 2))
+    P[2 * offset, 0] = P[2 * offset + 1, 1] = 1.0
+    return P
+
 # --- interpolating fields, Eqs. (2.2) and (2.3) ------------------------------
 
 _R6 = 1.0 / math.sqrt(6.0)
@@ -140,17 +147,19 @@ def _letter_size(ch: str) -> int:
     return 4 if ch in _SPIN else 3
 
 
-def source_factors():
+def source_factors(block=(0, 0)):
     """The source tensor of Eq. (2.4) as (baryon, letters, tensor) factors.
 
     eps_{c1 c2 c3} eps_{c4 c5 c6} (Cg5)_{a1 a2} (Cg5)_{a4 a5} delta_{a3 alpha3} delta_{a6 alpha4}
+    with alpha3 in {2 block[0], 2 block[0] + 1} and alpha4 in {2 block[1], 2 block[1] + 1}
+    (block (0, 0): the upper Dirac components).
     """
     fs = []
     for b in range(2):
         k = 3 * b
         fs.append((b, "eps", _COL[k] + _COL[k + 1] + _COL[k + 2], EPS))
         fs.append((b, "cg5", _SPIN[k] + _SPIN[k + 1], CG5))
-        fs.append((b, "proj", _SPIN[k + 2] + _OUT[b], PROJ))
+        fs.append((b, "proj", _SPIN[k + 2] + _OUT[b], projector(block[b])))
     return fs
 
 
@@ -164,7 +173,7 @@ def _factor_slots(letters: str):
     return out
 
 
-def topologies(B1: str, B2: str, B3: str, B4: str) -> list[Term]:
+def topologies(B1: str, B2: str, B3: str, B4: str, block=(0, 0)) -> list[Term]:
     """Group the Wick permutations of Eq. (2.4) into the effective-block terms of Eq. (2.7).
 
     For every pair of source monomials and every set S of three source slots,
@@ -199,15 +208,15 @@ def topologies(B1: str, B2: str, B3: str, B4: str) -> list[Term]:
                 if e2 not in t.side2:
                     t.side2.append(e2)
         for S, t in sorted(groups.items()):
-            _assign_factors(t)
+            _assign_factors(t, block)
             terms.append(t)
     return terms
 
 
-def _assign_factors(t: Term) -> None:
+def _assign_factors(t: Term, block=(0, 0)) -> None:
     in1 = set(t.S)
     xi = set()
-    for b, kind, letters, tensor in source_factors():
+    for b, kind, letters, tensor in source_factors(block):
         slots = _factor_slots(letters)
         if kind == "proj":
             side1 = slots[0] in in1
@@ -315,32 +324,33 @@ def all_r(L: int):
     return [(x, y, z) for z in range(L) for y in range(L) for x in range(L)]
 
 
-def correlator(channel, props: dict, L: int, r_list=None) -> np.ndarray:
+def correlator(channel, props: dict, L: int, r_list=None, block=(0, 0)) -> np.ndarray:
     """F^{<B1 B2 B3bar B4bar>}_{a1 a2, a3 a4}(r) for one timeslice, by direct sum over X.
 
     channel: (B1, B2, B3, B4) field names (keys of FIELDS).
     props:   {'u': S_u, 'd': S_d, 's': S_s}, complex128 [V, 12, 12] each.
     r_list:  None for every r (site order), else a list of (rx, ry, rz).
-    Returns complex128 [4, 4, 2, 2, n_r]  (alpha1, alpha2, alpha3, alpha4, r).
+    block:   source spin pair (o3, o4): alpha3 = 2 o3 + j3, alpha4 = 2 o4 + j4 for j in {0, 1}.
+    Returns complex128 [4, 4, 2, 2, n_r]  (alpha1, alpha2, j3, j4, r).
     """
     B1, B2, B3, B4 = channel
     if r_list is None:
         r_list = all_r(L)
     blocks = _Blocks(props)
     F = np.zeros((len(r_list), 4, 4, 2, 2), dtype=np.complex128)
-    for t in topologies(B1, B2, B3, B4):
+    for t in topologies(B1, B2, B3, B4, block):
         E1 = effective_block(t, 1, blocks)
         E2 = effective_block(t, 2, blocks)
         F += t.sign0 * t.c34 * _place(direct_sum(E1, E2, L, r_list), t)
     return np.moveaxis(F, 0, -1)
 
 
-def zero_momentum(channel, props: dict, L: int) -> np.ndarray:
+def zero_momentum(channel, props: dict, L: int, block=(0, 0)) -> np.ndarray:
     """sum_r F(r) = sum_terms sign (sum_x E1)(sum_y E2): complex128 [4, 4, 2, 2]."""
     B1, B2, B3, B4 = channel
     blocks = _Blocks(props)
     F = np.zeros((4, 4, 2, 2), dtype=np.complex128)
-    for t in topologies(B1, B2, B3, B4):
+    for t in topologies(B1, B2, B3, B4, block):
         s1 = effective_block(t, 1, blocks).sum(axis=0)
         s2 = effective_block(t, 2, blocks).sum(axis=0)
         F += t.sign0 * t.c34 * _place((s1 @ s2.T)[None], t)[0]

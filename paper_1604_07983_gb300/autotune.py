@@ -1,11 +1,12 @@
-"""Launch-shape autotuner for the contraction (the dominant kernel of the path).
+"""Launch-shape autotuner for the contraction and the 3-D FFTs.
 
 For a context with propagators loaded, it times each candidate kernel / launch
 shape of the effective-block contraction on one timeslice with the library's
-own CUDA-event stage timing (nbs_set_profiling / nbs_profile), keeps the
-fastest, and caches the choice in a JSON file keyed by (GPU name, L,
-precision, channel set).  Results do not depend on the choice beyond
-rounding; every candidate is covered by the parity tests.
+own CUDA-event stage timing (nbs_set_profiling / nbs_profile) and keeps the
+fastest, then does the same for the block size of the FFTs' strided passes
+(forward and inverse stage times), and caches the choice in a JSON file keyed
+by (GPU name, L, precision, channel set).  Results do not depend on the choice
+beyond rounding; every candidate is covered by the parity tests.
 """
 
 from __future__ import annotations
@@ -41,23 +42,29 @@ def _load():
         return {}
 
 
-def _apply(ctx: Context, cfg: int, qb: int):
+FFT_BLOCKS = (64, 128, 256)
+
+
+def _apply(ctx: Context, cfg: int, qb: int, fft_block: int = 0):
     ctx.set_param(Context.PARAM_CONTRACT_CFG, cfg)
     if qb:
         ctx.set_param(Context.PARAM_CHUNK_QBLOCK, qb)
+    if fft_block:
+        ctx.set_param(Context.PARAM_FFT_BLOCK, fft_block)
 
 
 def tune(ctx: Context, ids, precision: int, t: int = 0, reps: int = 2, use_cache: bool = True) -> dict:
-    """Pick the fastest contraction shape for (ctx.L, precision, ids) and apply it to ctx.
+    """Pick the fastest contraction shape and FFT block for (ctx.L, precision, ids) and apply them to ctx.
 
-    Propagators for timeslice t must be loaded.  Returns {"cfg", "qb", "ms", "timings"}.
+    Propagators for timeslice t must be loaded.  Returns {"cfg", "qb", "ms", "timings", "fft_block",
+    "fft_ms", "fft_timings"}.
     """
     import torch
     key = _key(ctx, ids, precision)
     cache = _load() if use_cache else {}
-    if key in cache:
+    if key in cache and "fft_block" in cache[key]:
         best = cache[key]
-        _apply(ctx, best["cfg"], best["qb"])
+        _apply(ctx, best["cfg"], best["qb"], best["fft_block"])
         return best
     out = torch.empty((len(ids), 1, 4, 4, 2, 2, ctx.V), dtype=torch.complex128, device="cuda")
     timings = []
@@ -73,6 +80,20 @@ def tune(ctx: Context, ids, precision: int, t: int = 0, reps: int = 2, use_cache
     best = dict(min(timings, key=lambda r: r["ms"]))
     best["timings"] = timings
     _apply(ctx, best["cfg"], best["qb"])
+    fft_timings = []
+    for fb in FFT_BLOCKS:
+        ctx.set_param(Context.PARAM_FFT_BLOCK, fb)
+        ctx.blocks(t)  # warm-up
+        ctx.set_profiling(True)
+        for _ in range(reps):
+            ctx.blocks(t)                     # rescale, blocks, forward FFT (always rebuilt)
+            ctx.correlate(ids, t, t + 1, out)  # contraction and inverse FFT on those blocks
+        stages, _ = ctx.profile()
+        ctx.set_profiling(False)
+        fft_timings.append({"fft_block": fb, "ms": (stages["fft_fwd"] + stages["fft_inv"]) / reps})
+    fbest = min(fft_timings, key=lambda r: r["ms"])
+    best["fft_block"], best["fft_ms"], best["fft_timings"] = fbest["fft_block"], fbest["ms"], fft_timings
+    _apply(ctx, best["cfg"], best["qb"], best["fft_block"])
     if use_cache:
         cache[key] = best
         os.makedirs(os.path.dirname(CACHE), exist_ok=True)

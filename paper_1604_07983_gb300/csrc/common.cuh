@@ -67,10 +67,10 @@ cudaError_t fft_init();
 bool fft_supported(int L);
 // forward FFT of the stored blocks, layout [cell][z][y][x][alpha]
 template <typename T>
-cudaError_t fft3d_blocks(C<T>* data, long long ncells, int L, cudaStream_t st);
+cudaError_t fft3d_blocks(C<T>* data, long long ncells, int L, cudaStream_t st, int sb = 128);
 // inverse FFT of nbatch contiguous cubes [batch][z][y][x]
 template <typename T>
-cudaError_t fft3d_inverse(C<T>* data, long long nbatch, int L, cudaStream_t st);
+cudaError_t fft3d_inverse(C<T>* data, long long nbatch, int L, cudaStream_t st, int sb = 128);
 // kernels_contract.cu
 template <typename T>
 cudaError_t launch_contract(const C<T>* FB, int L, const DevTerm* terms, const int* ch_tb, int nch,

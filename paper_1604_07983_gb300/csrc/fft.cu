@@ -140,7 +140,7 @@ struct Stage {
 
 // lines along y or z: line l -> base = (l / inner) * group + (l % inner), step = stride
 template <typename T, int L, int DIR>
-__global__ void __launch_bounds__(128) k_fft_strided(C<T>* __restrict__ data, long long nlines, int inner,
+__global__ void __launch_bounds__(256) k_fft_strided(C<T>* __restrict__ data, long long nlines, int inner,
                                                      long long group, int stride) {
   long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= nlines) return;
@@ -180,8 +180,9 @@ __global__ void __launch_bounds__(NT) k_fft_contig(C<T>* __restrict__ data, long
 }
 
 // batch cubes of L^3 elements, each element a vector of IL interleaved values
+// sb: threads per block of the two strided passes (64, 128 or 256; a tuning parameter)
 template <typename T, int L, int DIR, int IL>
-cudaError_t run3d(C<T>* data, long long nbatch, cudaStream_t st) {
+cudaError_t run3d(C<T>* data, long long nbatch, int sb, cudaStream_t st) {
   const long long nlines = nbatch * IL * L * L;
   if (nlines == 0 || L == 1) return cudaSuccess;
   {
@@ -195,34 +196,35 @@ cudaError_t run3d(C<T>* data, long long nbatch, cudaStream_t st) {
     long long blocks = (nlines + NT - 1) / NT;
     kern<<<(unsigned)blocks, NT, sm, st>>>(data, nlines);
   }
+  if (sb != 64 && sb != 128 && sb != 256) return cudaErrorInvalidValue;
   // y: lines (batch, z, x, i): inner = IL*L, group = IL*L^2, stride IL*L
   {
-    long long blocks = (nlines + 127) / 128;
-    k_fft_strided<T, L, DIR><<<(unsigned)blocks, 128, 0, st>>>(data, nlines, IL * L, (long long)IL * L * L, IL * L);
+    long long blocks = (nlines + sb - 1) / sb;
+    k_fft_strided<T, L, DIR><<<(unsigned)blocks, sb, 0, st>>>(data, nlines, IL * L, (long long)IL * L * L, IL * L);
   }
   // z: lines (batch, y, x, i): inner = IL*L^2, group = IL*L^3, stride IL*L^2
   {
-    long long blocks = (nlines + 127) / 128;
-    k_fft_strided<T, L, DIR><<<(unsigned)blocks, 128, 0, st>>>(data, nlines, IL * L * L, (long long)IL * L * L * L,
-                                                               IL * L * L);
+    long long blocks = (nlines + sb - 1) / sb;
+    k_fft_strided<T, L, DIR><<<(unsigned)blocks, sb, 0, st>>>(data, nlines, IL * L * L, (long long)IL * L * L * L,
+                                                              IL * L * L);
   }
   return cudaGetLastError();
 }
 
 template <typename T, int DIR, int IL>
-cudaError_t dispatch(C<T>* data, long long nbatch, int L, cudaStream_t st) {
+cudaError_t dispatch(C<T>* data, long long nbatch, int L, int sb, cudaStream_t st) {
   switch (L) {
     case 1: return cudaSuccess;
-    case 2: return run3d<T, 2, DIR, IL>(data, nbatch, st);
-    case 3: return run3d<T, 3, DIR, IL>(data, nbatch, st);
-    case 4: return run3d<T, 4, DIR, IL>(data, nbatch, st);
-    case 6: return run3d<T, 6, DIR, IL>(data, nbatch, st);
-    case 8: return run3d<T, 8, DIR, IL>(data, nbatch, st);
-    case 12: return run3d<T, 12, DIR, IL>(data, nbatch, st);
-    case 16: return run3d<T, 16, DIR, IL>(data, nbatch, st);
-    case 24: return run3d<T, 24, DIR, IL>(data, nbatch, st);
-    case 32: return run3d<T, 32, DIR, IL>(data, nbatch, st);
-    case 48: return run3d<T, 48, DIR, IL>(data, nbatch, st);
+    case 2: return run3d<T, 2, DIR, IL>(data, nbatch, sb, st);
+    case 3: return run3d<T, 3, DIR, IL>(data, nbatch, sb, st);
+    case 4: return run3d<T, 4, DIR, IL>(data, nbatch, sb, st);
+    case 6: return run3d<T, 6, DIR, IL>(data, nbatch, sb, st);
+    case 8: return run3d<T, 8, DIR, IL>(data, nbatch, sb, st);
+    case 12: return run3d<T, 12, DIR, IL>(data, nbatch, sb, st);
+    case 16: return run3d<T, 16, DIR, IL>(data, nbatch, sb, st);
+    case 24: return run3d<T, 24, DIR, IL>(data, nbatch, sb, st);
+    case 32: return run3d<T, 32, DIR, IL>(data, nbatch, sb, st);
+    case 48: return run3d<T, 48, DIR, IL>(data, nbatch, sb, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -250,19 +252,19 @@ cudaError_t fft_init() {
 
 // forward transform of the stored blocks [cell][site][alpha] (4 interleaved cubes per cell)
 template <typename T>
-cudaError_t fft3d_blocks(C<T>* data, long long ncells, int L, cudaStream_t st) {
-  return dispatch<T, -1, 4>(data, ncells, L, st);
+cudaError_t fft3d_blocks(C<T>* data, long long ncells, int L, cudaStream_t st, int sb) {
+  return dispatch<T, -1, 4>(data, ncells, L, sb, st);
 }
 
 // inverse transform of nbatch contiguous cubes
 template <typename T>
-cudaError_t fft3d_inverse(C<T>* data, long long nbatch, int L, cudaStream_t st) {
-  return dispatch<T, +1, 1>(data, nbatch, L, st);
+cudaError_t fft3d_inverse(C<T>* data, long long nbatch, int L, cudaStream_t st, int sb) {
+  return dispatch<T, +1, 1>(data, nbatch, L, sb, st);
 }
 
-template cudaError_t fft3d_blocks<float>(float2*, long long, int, cudaStream_t);
-template cudaError_t fft3d_blocks<double>(double2*, long long, int, cudaStream_t);
-template cudaError_t fft3d_inverse<float>(float2*, long long, int, cudaStream_t);
-template cudaError_t fft3d_inverse<double>(double2*, long long, int, cudaStream_t);
+template cudaError_t fft3d_blocks<float>(float2*, long long, int, cudaStream_t, int);
+template cudaError_t fft3d_blocks<double>(double2*, long long, int, cudaStream_t, int);
+template cudaError_t fft3d_inverse<float>(float2*, long long, int, cudaStream_t, int);
+template cudaError_t fft3d_inverse<double>(double2*, long long, int, cudaStream_t, int);
 
 }  // namespace nbs

@@ -58,6 +58,9 @@ struct nbs_plan {
 
 struct nbs_ctx {
   int L = 0, T = 0, V = 0, device = 0;
+  unsigned buf_gen = 0;          // bumped by every device (re)allocation
+  bool capturing = false;        // enqueueing into a CUDA graph: no allocation, no host synchronisation
+  cudaStream_t gst = nullptr;    // capture stream
   int mode = NBS_FP64;
   cudaStream_t st = 0;
   cudaStream_t cst = nullptr;
@@ -86,6 +89,7 @@ struct nbs_ctx {
   DevBuf d_chunks, d_qchunks, d_ctab, d_citems, d_ctoff, d_codes;
   int chunk_st1 = 0, chunk_st2 = 0, chunk_slot = 0, chunk_tab = 0, chunk_row = 0, quad_slot = 0;
   int chunk_qb = 32;
+  int fft_block = 128;  // NBS_PARAM_FFT_BLOCK
   int tables_mode = -1;
   TypeRecipeSet recipes;
 
@@ -158,6 +162,9 @@ void prof_resolve(nbs_ctx* h) {
 
 int ensure(nbs_ctx* h, DevBuf& b, size_t bytes, const char* what) {
   if (b.bytes >= bytes && b.p) return NBS_OK;
+  if (h->capturing)
+    return fail(h, NBS_ESTATE, std::string("buffer for ") + what + " would be allocated while capturing");
+  ++h->buf_gen;
   if (b.p) {
     cudaStreamSynchronize(h->st);
     dev_free(b.p, h->free_fn, h->free_user);
@@ -315,7 +322,7 @@ int build_blocks(nbs_ctx* h, int t) {
   const void* s = base + (size_t)V * 144 * sizeof(double2);
   const int c64 = h->have[t] == NBS_C64;
   cudaEvent_t e0 = stage_begin(h);
-  CK(cudaMemsetAsync(h->small.p, 0, 64, h->st), "clear scale scratch");
+  CK(cudaMemsetAsync(h->small.p, 0, 16, h->st), "clear max|S|");  // the NaN flag accumulates over a call
   CK(launch_props_maxabs(u, s, c64, V, h->maxbits, h->flags, h->st), "max|S|");
   CK(launch_props_scale<T>(u, s, c64, V, h->maxbits, h->exps, (C<T>*)h->propsT.p, h->st), "rescale");
   stage_end(h, 0, e0);
@@ -326,14 +333,25 @@ int build_blocks(nbs_ctx* h, int t) {
      "field blocks");
   stage_end(h, 1, e1);
   cudaEvent_t e2 = stage_begin(h);
-  CK(fft3d_blocks<T>((C<T>*)h->FB.p, P.ncells, h->L, h->st), "forward FFT");
+  CK(fft3d_blocks<T>((C<T>*)h->FB.p, P.ncells, h->L, h->st, h->fft_block), "forward FFT");
   stage_end(h, 2, e2);
   h->launches += 4 + (h->L > 1 ? 3 : 0);
-  CK(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->st), "flags");
   h->blocks_t = t;
   h->blocks_mode = h->mode;
   h->blocks_gen = h->plan_gen;
   return NBS_OK;
+}
+
+// every device buffer nbs_correlate(nch channels) needs, allocated now
+template <typename T>
+int prepare(nbs_ctx* h, int nch) {
+  const int V = h->V;
+  int rc;
+  if ((rc = ensure(h, h->propsT, 2ull * 144 * V * sizeof(C<T>), "scaled propagators"))) return rc;
+  if ((rc = ensure(h, h->Q, 6ull * 144 * V * sizeof(C<T>), "diquarks"))) return rc;
+  if ((rc = ensure(h, h->FB, 4ull * h->plan.ncells * V * sizeof(C<T>), "baryon blocks"))) return rc;
+  if ((rc = ensure(h, h->Ft, (size_t)nch * 64 * V * sizeof(C<T>), "momentum-space correlators"))) return rc;
+  return ensure(h, h->zm, (size_t)nch * 64 * sizeof(C<T>), "zero momentum");
 }
 
 template <typename T>
@@ -344,13 +362,14 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
   if ((rc = ensure(h, h->Ft, (size_t)nch * 64 * V * sizeof(C<T>), "momentum-space correlators"))) return rc;
   if ((rc = ensure(h, h->zm, (size_t)nch * 64 * sizeof(C<T>), "zero momentum"))) return rc;
   const size_t per_t = (size_t)nch * 64 * V * sizeof(double2);
+  CK(cudaMemsetAsync(h->flags, 0, sizeof(int), h->st), "clear NaN flag");
   if (!on_dev) {
     for (int b = 0; b < 2; ++b)
       if ((rc = ensure(h, h->stage[b], per_t, "output staging"))) return rc;
   }
   for (int t = t0; t < t1; ++t) {
     if (h->have[t] < 0) return fail(h, NBS_ESTATE, "no propagators loaded for timeslice " + std::to_string(t));
-    if (!(h->blocks_t == t && h->blocks_mode == h->mode && h->blocks_gen == h->plan_gen)) {
+    if (h->capturing || !(h->blocks_t == t && h->blocks_mode == h->mode && h->blocks_gen == h->plan_gen)) {
       if ((rc = build_blocks<T>(h, t))) return rc;
     }
     cudaEvent_t e3 = stage_begin(h);
@@ -408,7 +427,7 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
          "zero momentum");
     }
     cudaEvent_t e4 = stage_begin(h);
-    CK(fft3d_inverse<T>((C<T>*)h->Ft.p, (long long)nch * 64, h->L, h->st), "inverse FFT");
+    CK(fft3d_inverse<T>((C<T>*)h->Ft.p, (long long)nch * 64, h->L, h->st, h->fft_block), "inverse FFT");
     stage_end(h, 4, e4);
     cudaEvent_t e5 = stage_begin(h);
     const long long tt = t - t0;
@@ -432,10 +451,19 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
     }
     stage_end(h, 5, e5);
   }
+  CK(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->st), "NaN flag");
+  if (h->capturing) {  // a replay leaves other blocks behind than the ones last built here
+    h->blocks_t = -1;
+    h->last_nch = nch;
+    return NBS_OK;
+  }
   if (!on_dev) CK(cudaStreamSynchronize(h->cst), "copy sync");
   CK(cudaStreamSynchronize(h->st), "sync");
   prof_resolve(h);
-  if (*h->host_flags) return fail(h, NBS_ENAN, "non-finite value in the propagators");
+  if (*h->host_flags) {
+    h->blocks_t = -1;
+    return fail(h, NBS_ENAN, "non-finite value in the propagators");
+  }
   h->last_nch = nch;
   return NBS_OK;
 }
@@ -505,7 +533,8 @@ int nbs_destroy(nbs_ctx* h) {
   if (h->cst) cudaStreamSynchronize(h->cst);
   DevBuf* bufs[] = {&h->props, &h->propsT, &h->Q, &h->FB, &h->Ft, &h->zm, &h->small, &h->stage[0], &h->stage[1],
                     &h->d_terms, &h->d_chtb, &h->d_chnl, &h->d_e1, &h->d_e2, &h->d_cells, &h->d_groups,
-                    &h->d_gch, &h->d_items, &h->d_chunks, &h->d_ctab, &h->d_citems, &h->d_ctoff, &h->d_codes};
+                    &h->d_gch, &h->d_items, &h->d_chunks, &h->d_qchunks, &h->d_ctab, &h->d_citems, &h->d_ctoff,
+                    &h->d_codes};
   for (DevBuf* b : bufs) dev_free(b->p, h->free_fn, h->free_user);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   for (int b = 0; b < 2; ++b) {
@@ -513,6 +542,7 @@ int nbs_destroy(nbs_ctx* h) {
     if (h->ev_ready[b]) cudaEventDestroy(h->ev_ready[b]);
   }
   if (h->cst) cudaStreamDestroy(h->cst);
+  if (h->gst) cudaStreamDestroy(h->gst);
   if (h->host_flags) cudaFreeHost(h->host_flags);
   delete h;
   return NBS_OK;
@@ -553,11 +583,16 @@ int nbs_blocks(nbs_ctx* h, int t) {
   int rc;
   if (!h->plan_ok && (rc = ensure_plan(h, all_channels()))) return rc;
   if (h->tables_mode != h->mode && (rc = upload_tables(h))) return rc;
+  CK(cudaMemsetAsync(h->flags, 0, sizeof(int), h->st), "clear NaN flag");
   rc = is_f32(h->mode) ? build_blocks<float>(h, t) : build_blocks<double>(h, t);
   if (rc) return rc;
+  CK(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->st), "NaN flag");
   CK(cudaStreamSynchronize(h->st), "sync");
   prof_resolve(h);
-  if (*h->host_flags) return fail(h, NBS_ENAN, "non-finite value in the propagators");
+  if (*h->host_flags) {
+    h->blocks_t = -1;
+    return fail(h, NBS_ENAN, "non-finite value in the propagators");
+  }
   return NBS_OK;
 }
 
@@ -574,6 +609,92 @@ int nbs_correlate(nbs_ctx* h, const int* channel_ids, int n_channels, int t_begi
                          : correlate<double>(h, n_channels, t_begin, t_end, out, out_on_device);
 }
 
+struct nbs_graph {
+  nbs_ctx* h = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned buf_gen = 0;
+  int mode = 0, t0 = 0, t1 = 0;
+  std::vector<signed char> have;  // propagator storage types of [t0, t1) at capture
+};
+
+int nbs_graph_capture(nbs_ctx* h, const int* channel_ids, int n_channels, int t_begin, int t_end, void* out,
+                      nbs_graph** graph) {
+  if (!h) return fail(nullptr, NBS_EINVAL, "null context");
+  if (!graph) return fail(h, NBS_EINVAL, "null graph pointer");
+  *graph = nullptr;
+  if (!channel_ids || n_channels < 1 || n_channels > 65535) return fail(h, NBS_EINVAL, "bad channel list");
+  if (t_begin < 0 || t_end > h->T || t_begin >= t_end) return fail(h, NBS_EINVAL, "bad timeslice range");
+  if (!out) return fail(h, NBS_EINVAL, "null output");
+  if (h->prof) return fail(h, NBS_EINVAL, "profiling must be off while capturing");
+  for (int t = t_begin; t < t_end; ++t)
+    if (h->have[t] < 0) return fail(h, NBS_ESTATE, "no propagators loaded for timeslice " + std::to_string(t));
+  std::vector<int> ids(channel_ids, channel_ids + n_channels);
+  int rc = ensure_plan(h, ids);
+  if (!rc) rc = is_f32(h->mode) ? prepare<float>(h, n_channels) : prepare<double>(h, n_channels);
+  if (rc) return rc;
+  cudaError_t e;
+  if (!h->gst && (e = cudaStreamCreateWithFlags(&h->gst, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(h, e, "capture stream");
+  CK(cudaStreamSynchronize(h->st), "sync before capture");
+  cudaStream_t user = h->st;
+  h->st = h->gst;
+  if ((e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed)) != cudaSuccess) {
+    h->st = user;
+    return cuda_fail(h, e, "begin capture");
+  }
+  h->capturing = true;
+  rc = is_f32(h->mode) ? correlate<float>(h, n_channels, t_begin, t_end, out, 1)
+                       : correlate<double>(h, n_channels, t_begin, t_end, out, 1);
+  h->capturing = false;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(h->st, &g);
+  h->st = user;
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(h, e, "instantiate graph");
+  nbs_graph* G = new nbs_graph();
+  G->h = h;
+  G->exec = exec;
+  G->buf_gen = h->buf_gen;
+  G->mode = h->mode;
+  G->t0 = t_begin;
+  G->t1 = t_end;
+  G->have.assign(h->have.begin() + t_begin, h->have.begin() + t_end);
+  *graph = G;
+  return NBS_OK;
+}
+
+int nbs_graph_launch(nbs_graph* graph, int wait) {
+  if (!graph || !graph->h) return fail(nullptr, NBS_EINVAL, "null graph");
+  nbs_ctx* h = graph->h;
+  if (graph->buf_gen != h->buf_gen || graph->mode != h->mode)
+    return fail(h, NBS_ESTATE, "the context's buffers or precision changed since the capture; capture again");
+  for (int t = graph->t0; t < graph->t1; ++t)
+    if (h->have[t] != graph->have[t - graph->t0])
+      return fail(h, NBS_ESTATE, "propagator storage of timeslice " + std::to_string(t) + " changed since the capture");
+  *h->host_flags = 0;
+  CK(cudaGraphLaunch(graph->exec, h->st), "graph launch");
+  h->blocks_t = -1;
+  if (!wait) return NBS_OK;
+  CK(cudaStreamSynchronize(h->st), "sync");
+  if (*h->host_flags) return fail(h, NBS_ENAN, "non-finite value in the propagators");
+  return NBS_OK;
+}
+
+int nbs_graph_destroy(nbs_graph* graph) {
+  if (!graph) return NBS_OK;
+  if (graph->exec) cudaGraphExecDestroy(graph->exec);
+  delete graph;
+  return NBS_OK;
+}
+
 int nbs_set_param(nbs_ctx* h, int param, int value) {
   if (!h) return fail(nullptr, NBS_EINVAL, "null context");
   switch (param) {
@@ -587,6 +708,10 @@ int nbs_set_param(nbs_ctx* h, int param, int value) {
     case NBS_PARAM_CHUNK_QBLOCK:
       if (value < 1 || value > (1 << 20)) return fail(h, NBS_EINVAL, "momentum block must be in [1, 2^20]");
       h->chunk_qb = value;
+      return NBS_OK;
+    case NBS_PARAM_FFT_BLOCK:
+      if (value != 64 && value != 128 && value != 256) return fail(h, NBS_EINVAL, "FFT block must be 64, 128 or 256");
+      h->fft_block = value;
       return NBS_OK;
     default: return fail(h, NBS_EINVAL, "unknown parameter");
   }

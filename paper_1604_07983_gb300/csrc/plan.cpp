@@ -380,10 +380,13 @@ void build_chunks(Plan& plan) {
 std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
   plan = Plan();
   const auto& table = channel_table();
+  // id = channel + n * block: block o3 + 2 o4 selects the source spins
+  // alpha3 in {2 o3, 2 o3 + 1}, alpha4 in {2 o4, 2 o4 + 1} (block 0: the upper components)
+  const int nbase = (int)table.size();
   for (int id : ids) {
-    if (id < 0 || id >= (int)table.size()) {
+    if (id < 0 || id >= NBS_SPIN_BLOCKS * nbase) {
       std::ostringstream os;
-      os << "channel id " << id << " outside [0, " << table.size() << ")";
+      os << "channel id " << id << " outside [0, " << NBS_SPIN_BLOCKS * nbase << ")";
       return os.str();
     }
   }
@@ -391,7 +394,7 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
 
   // ---- stored block types over the sink fields in use -----------------------
   bool used[NFIELDS] = {};
-  for (int id : ids) { used[table[id].b[0]] = used[table[id].b[1]] = true; }
+  for (int id : ids) { used[table[id % nbase].b[0]] = used[table[id % nbase].b[1]] = true; }
   std::vector<TypeBuild> types;
   FieldMap fmap[NFIELDS];
   for (int f = 0; f < NFIELDS; ++f) {
@@ -440,7 +443,9 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
   // ---- contraction terms -----------------------------------------------------
   plan.ch_term_begin.push_back(0);
   for (int ci = 0; ci < (int)ids.size(); ++ci) {
-    const ChannelDef& ch = table[ids[ci]];
+    const ChannelDef& ch = table[ids[ci] % nbase];
+    const int sblock = ids[ci] / nbase;
+    const int soff[2] = {sblock & 1, sblock >> 1};  // source spin pair offsets of alpha3, alpha4
     const int B1 = ch.b[0], B2 = ch.b[1];
     int cf1[3], cf2[3];
     canonical_flavours(B1, cf1);
@@ -527,7 +532,7 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
                 int bit = 0;
                 for (int b = 0; b < 2; ++b) {
                   if (pside[b] != side) continue;
-                  sp[3 * b + 2] = (h >> bit) & 1;  // projector: spin of the third slot = alpha_{3/4}
+                  sp[3 * b + 2] = 2 * soff[b] + ((h >> bit) & 1);  // projector: third slot's spin = alpha_{3/4}
                   ++bit;
                 }
                 // free indices of this side's slots
@@ -625,7 +630,7 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
   {
     std::map<std::pair<int, int>, std::vector<int>> by_types;  // (type B1, type B2) -> channels
     for (int ci = 0; ci < (int)ids.size(); ++ci) {
-      const ChannelDef& ch = table[ids[ci]];
+      const ChannelDef& ch = table[ids[ci] % nbase];
       by_types[{fmap[ch.b[0]].type, fmap[ch.b[1]].type}].push_back(ci);
     }
     for (auto& kv : by_types) {

@@ -108,6 +108,11 @@ struct Plan {
   double cmac_per_q = 0, gathers_per_q = 0;
 };
 
+// Source spin blocks: channel id c + n * k (n = built-in channels, k < 4)
+// projects the source spins onto alpha3 in {2 (k & 1), 2 (k & 1) + 1} and
+// alpha4 in {2 (k >> 1), 2 (k >> 1) + 1}; k = 0 is the upper components.
+#define NBS_SPIN_BLOCKS 4
+
 // Compile the tables for the given channel ids.  Returns "" or an error text.
 std::string compile_plan(const std::vector<int>& channel_ids, Plan& out);
 

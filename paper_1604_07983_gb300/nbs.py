@@ -26,7 +26,7 @@ EXPORTS = ["nbs_set_allocator", "nbs_create", "nbs_destroy", "nbs_set_precision"
            "nbs_load_props", "nbs_blocks", "nbs_correlate", "nbs_zero_momentum", "nbs_set_param", "nbs_set_profiling",
            "nbs_profile", "nbs_channel_count",
            "nbs_channel_info", "nbs_last_error", "nbs_plan_create", "nbs_plan_destroy", "nbs_plan_sizes",
-           "nbs_plan_export", "nbs_correlate_static"]
+           "nbs_plan_export", "nbs_correlate_static", "nbs_graph_capture", "nbs_graph_launch", "nbs_graph_destroy"]
 
 
 class NBSError(RuntimeError):
@@ -70,6 +70,9 @@ def lib():
         "nbs_plan_sizes": (i, [vp, ctypes.POINTER(ll)]),
         "nbs_plan_export": (i, [vp, i, vp]),
         "nbs_correlate_static": (i, [vp, vp, i, i, i, vp, vp]),
+        "nbs_graph_capture": (i, [vp, ctypes.POINTER(i), i, i, i, vp, ctypes.POINTER(vp)]),
+        "nbs_graph_launch": (i, [vp, i]),
+        "nbs_graph_destroy": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -184,6 +187,28 @@ def correlate_static(u, s, L: int, channel_id: int, out, stream=None):
     return out
 
 
+def full_spin_ids(channel_ids):
+    """The ids that cover the full 4 x 4 source spin of the given channels: for each channel c the
+    four source spin pairs c + k * channel_count(), k = o3 + 2 o4 (alpha3 in {2 o3, 2 o3 + 1},
+    alpha4 in {2 o4, 2 o4 + 1}), in the order [k][channel]."""
+    n = channel_count()
+    return [c + k * n for k in range(4) for c in channel_ids]
+
+
+def assemble_full_spin(out):
+    """[4 * n, nt, 4, 4, 2, 2, V] (ids from full_spin_ids) -> [n, nt, 4, 4, 4, 4, V]
+    (alpha1, alpha2, alpha3, alpha4)."""
+    k4 = out.shape[0]
+    n = k4 // 4
+    parts = out.reshape((4, n) + tuple(out.shape[1:]))  # [k][c][t][a1][a2][j3][j4][V]
+    shape = (n, out.shape[1], 4, 4, 4, 4, out.shape[-1])
+    full = out.new_empty(shape) if hasattr(out, "new_empty") else __import__("numpy").empty(shape, out.dtype)
+    for k in range(4):
+        o3, o4 = k & 1, k >> 1
+        full[:, :, :, :, 2 * o3:2 * o3 + 2, 2 * o4:2 * o4 + 2] = parts[k]
+    return full
+
+
 # ---- context -----------------------------------------------------------------
 
 def _ptr(x):
@@ -207,6 +232,9 @@ class Context:
             self.set_stream(stream)
 
     def close(self):
+        for g in getattr(self, "_graphs", []):
+            g.close()
+        self._graphs = []
         if getattr(self, "h", None):
             self._lib.nbs_destroy(self.h)
             self.h = None
@@ -254,8 +282,23 @@ class Context:
                self.h)
         return out
 
+    def capture(self, channel_ids, t_begin: int, t_end: int, out) -> "Graph":
+        """CUDA graph of correlate(channel_ids, t_begin, t_end, out) for a device tensor out (nbs_graph_capture)."""
+        if not getattr(out, "is_cuda", False):
+            raise ValueError("graph capture needs a device output tensor")
+        ids = (ctypes.c_int * len(channel_ids))(*channel_ids)
+        g = ctypes.c_void_p()
+        _check(self._lib.nbs_graph_capture(self.h, ids, len(channel_ids), t_begin, t_end, _ptr(out), ctypes.byref(g)),
+               self.h)
+        graph = Graph(self, g)
+        if not hasattr(self, "_graphs"):
+            self._graphs = []
+        self._graphs.append(graph)
+        return graph
+
     PARAM_CONTRACT_CFG = 0
     PARAM_CHUNK_QBLOCK = 1
+    PARAM_FFT_BLOCK = 2
 
     def set_param(self, param: int, value: int):
         _check(self._lib.nbs_set_param(self.h, param, value), self.h)
@@ -277,3 +320,26 @@ class Context:
         out = np.zeros((n_channels, 4, 4, 2, 2), dtype=np.complex128)
         _check(self._lib.nbs_zero_momentum(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), self.h)
         return out
+
+
+class Graph:
+    """A captured correlator work list (nbs_graph_*); keeps its context alive."""
+
+    def __init__(self, ctx: "Context", g):
+        self.ctx, self.g = ctx, g
+
+    def launch(self, wait: bool = True):
+        if not self.g or not self.ctx.h:
+            raise NBSError(-4, "graph or context closed")
+        _check(self.ctx._lib.nbs_graph_launch(self.g, int(wait)), self.ctx.h)
+
+    def close(self):
+        if self.g:
+            self.ctx._lib.nbs_graph_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

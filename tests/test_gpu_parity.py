@@ -259,5 +259,71 @@ def test_state_and_nan_errors(nbs):
             ctx.correlate([0], 0, 1, out)
         assert e.value.code == -6
         with pytest.raises(nbs.NBSError) as e:
-            ctx.correlate([52], 0, 1, out)
+            ctx.correlate([4 * 52], 0, 1, out)  # ids run over 52 channels x 4 source spin pairs
         assert e.value.code == -1
+
+
+def test_graph_replay_matches_correlate(nbs):
+    """A captured CUDA graph of nbs_correlate replays the same kernels: identical output; a replay after
+    new propagators are loaded gives the new correlators; buffer reallocation and NaN inputs are errors."""
+    L, T = 4, 3
+    props = seeded(1731, L, T, decay=0.5)
+    ids = [0, 9, 24, 51]
+    shape = (len(ids), T, 4, 4, 2, 2, L ** 3)
+    with nbs.Context(L, T, precision=nbs.NBS_FP32) as ctx:
+        for t, (Sl, Ss) in enumerate(props):
+            ctx.load_props(torch.from_numpy(Sl).cuda(), torch.from_numpy(Ss).cuda(), t)
+        ref = torch.empty(shape, dtype=torch.complex128, device="cuda")
+        ctx.correlate(ids, 0, T, ref)
+        out = torch.full(shape, float("nan"), dtype=torch.complex128, device="cuda")
+        g = ctx.capture(ids, 0, T, out)
+        torch.cuda.synchronize()
+        assert torch.isnan(out).all()          # capturing runs nothing
+        g.launch()
+        assert torch.equal(out, ref)
+        # new propagators in slot 1, replay
+        Sl, Ss = I.propagator(1732, "l", L, 1, 0.5), I.propagator(1732, "s", L, 1, 0.5)
+        ctx.load_props(torch.from_numpy(Sl).cuda(), torch.from_numpy(Ss).cuda(), 1)
+        g.launch()
+        one = torch.empty((len(ids), 1, 4, 4, 2, 2, L ** 3), dtype=torch.complex128, device="cuda")
+        ctx.correlate(ids, 1, 2, one)
+        assert torch.equal(out[:, 1:2], one) and torch.equal(out[:, 0], ref[:, 0])
+        names = nbs.channel_names()
+        got = out.cpu().numpy()
+        for k, c in enumerate(ids):
+            assert rel(got[k, 1], oracle(names[c], Sl, Ss, L)) < FP32_TOL, names[c]
+        # NaN propagators are reported by a waited replay
+        bad = torch.from_numpy(Sl).cuda()
+        bad[3, 2, 1] = float("nan")
+        ctx.load_props(bad, torch.from_numpy(Ss).cuda(), 2)
+        with pytest.raises(nbs.NBSError) as ei:
+            g.launch()
+        assert ei.value.code == -6
+        # more channels reallocate the context's buffers: the graph refuses to run
+        ctx.load_props(torch.from_numpy(props[2][0]).cuda(), torch.from_numpy(props[2][1]).cuda(), 2)
+        big = torch.empty((52, 1, 4, 4, 2, 2, L ** 3), dtype=torch.complex128, device="cuda")
+        ctx.correlate(list(range(52)), 0, 1, big)
+        with pytest.raises(nbs.NBSError) as ei:
+            g.launch()
+        assert ei.value.code == -4
+
+
+def test_full_source_spin(nbs):
+    """All 4 x 4 source spins (ids c + k * 52) through the GPU path, FP64 and FP32, against the
+    oracle's correlator for each source spin pair."""
+    L = 4
+    props = seeded(1741, L, 1, decay=0.5)
+    names = nbs.channel_names()
+    chans = [0, 24, 51]
+    ids = nbs.full_spin_ids(chans)
+    F64 = nbs.assemble_full_spin(gpu_correlate(nbs, ids, L, props, nbs.NBS_FP64))
+    F32 = nbs.assemble_full_spin(gpu_correlate(nbs, ids, L, props, nbs.NBS_FP32))
+    assert F64.shape == (len(chans), 1, 4, 4, 4, 4, L ** 3)
+    for j, c in enumerate(chans):
+        for k in range(4):
+            o3, o4 = k & 1, k >> 1
+            ref = oracle(names[c], *props[0], L) if k == 0 else \
+                O.correlator(names[c], {"u": props[0][0], "d": props[0][0], "s": props[0][1]}, L, block=(o3, o4))
+            sl = (j, 0, slice(None), slice(None), slice(2 * o3, 2 * o3 + 2), slice(2 * o4, 2 * o4 + 2))
+            assert rel(F64[sl], ref) < FP64_TOL, (names[c], k)
+            assert rel(F32[sl], ref) < FP32_TOL, (names[c], k)

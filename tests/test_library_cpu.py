@@ -56,9 +56,13 @@ def test_argument_errors_without_gpu(lib):
     assert b"flavours" in lib.nbs_last_error(None)
     assert lib.nbs_create(ctypes.byref(h), 5, 8, 2) == nbs.NBS_EINVAL
     assert lib.nbs_create(ctypes.byref(h), 8, 0, 2) == nbs.NBS_EINVAL
-    ids = (ctypes.c_int * 1)(99)
     p = ctypes.c_void_p()
-    assert lib.nbs_plan_create(ctypes.byref(p), ids, 1) == nbs.NBS_EINVAL
+    for bad in (4 * 52, -1):  # ids run over 52 channels x 4 source spin pairs
+        ids = (ctypes.c_int * 1)(bad)
+        assert lib.nbs_plan_create(ctypes.byref(p), ids, 1) == nbs.NBS_EINVAL
+    ids = (ctypes.c_int * 1)(99)  # channel 47, source spins alpha3 in {2, 3}, alpha4 in {0, 1}
+    assert lib.nbs_plan_create(ctypes.byref(p), ids, 1) == nbs.NBS_OK
+    lib.nbs_plan_destroy(p)
     assert lib.nbs_channel_info(52, None, 0) == nbs.NBS_EINVAL
     assert lib.nbs_set_precision(None, 0) == nbs.NBS_EINVAL
 
@@ -184,3 +188,26 @@ def test_compiled_tables_reproduce_oracle(lib, L, ids):
     for k, c in enumerate(ids):
         Fo = O.correlator(names[c], props, L)
         assert np.linalg.norm(F[k] - Fo) <= 1e-12 * np.linalg.norm(Fo), names[c]
+
+
+def test_source_spin_blocks_reproduce_oracle(lib):
+    """Ids c + k * 52 (k = 1, 2, 3) project the source spins onto the other three pairs
+    (alpha3 in {2 (k & 1), +1}, alpha4 in {2 (k >> 1), +1}); the compiled tables, run by the
+    emulator, equal the oracle's correlator for that pair (itself pinned to the determinant
+    definition at those spins)."""
+    from plan_emulator import emulate
+    names = nbs.channel_names()
+    n = len(names)
+    L = 2
+    Sl, Ss = I.propagator(62, "l", L, 0), I.propagator(62, "s", L, 0)
+    props = {"u": Sl, "d": Sl, "s": Ss}
+    base = [0, 9, 24, 33, 51]
+    ids = [c + k * n for k in (1, 2, 3) for c in base]
+    F = emulate(ids, Sl, Ss, L)
+    for j, vid in enumerate(ids):
+        c, k = vid % n, vid // n
+        Fo = O.correlator(names[c], props, L, block=(k & 1, k >> 1))
+        assert np.linalg.norm(Fo) > 0
+        assert np.linalg.norm(F[j] - Fo) <= 1e-12 * np.linalg.norm(Fo), (names[c], k)
+    with pytest.raises(nbs.NBSError):
+        nbs.plan_tables([4 * n])

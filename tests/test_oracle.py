@@ -118,6 +118,18 @@ def test_oracle_equals_determinant_wick_L1(channel):
         assert abs(F[spins][0] - b) <= 1e-12 * abs(b)
 
 
+@pytest.mark.parametrize("block", [(1, 0), (0, 1), (1, 1)])
+def test_oracle_other_source_spins_equal_determinant_wick_L1(block):
+    """Source spins outside the upper components (alpha3, alpha4 in {2 o3, 2 o3 + 1} x {2 o4, 2 o4 + 1})
+    against the determinant definition, which takes any source spins."""
+    props = props3(13, 1)
+    for channel in CHANNELS_L1[:3]:
+        F = O.correlator(channel, props, 1, block=block)
+        for a1, a2, j3, j4 in [(0, 1, 0, 1), (2, 3, 1, 0), (3, 0, 1, 1)]:
+            b = correlator_brute(channel, props, 1, (0, 0, 0), (a1, a2, 2 * block[0] + j3, 2 * block[1] + j4))
+            assert abs(F[a1, a2, j3, j4][0] - b) <= 1e-12 * abs(b), (channel, block)
+
+
 def test_oracle_equals_determinant_wick_L2_shift():
     props = props3(12, 2)
     r = (1, 0, 1)
