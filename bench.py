@@ -365,7 +365,8 @@ def run_ours(args, rank, world, local_rank):
     if dominant == "contract" and prec == P.NBS_BF16X3:
         peak = peaks.get("bf16_tflops", 1900.0)
         ach = 3 * flops_per_launch / (per_launch_ms["contract"] / 1e3) / 1e12
-        roof = {"kernel": "k_contract_tc", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+        tc_cfg = tuned["cfg"] if tuned else args.contract_cfg
+        roof = {"kernel": "k_contract_tc" if tc_cfg == 2 else "k_contract_tcq", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None,
                 "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)" if "bf16_tflops" in peaks else "fallback",
                 "work_per_launch": "3 bf16 products x 8 flop x 64 x sum|xi~| (=%d) x V complex MACs of Eq. (4.3)"

@@ -151,6 +151,9 @@ int nbs_zero_momentum(nbs_ctx* h, double* out);
  *       sink spin each, 16 warps per block), else the default;
  *   A*10 + W = the thread-per-momentum kernel with A sink spins alpha1 per
  *       thread (1, 2 or 4) and W warps per block (1, 2 or 4).
+ * In NBS_BF16X3 mode the tensor-core kernels run: the quad-lane form
+ * (fragments by movmatrix, no shared-memory staging) by default, the
+ * two-lane form with shared-memory staging for config 2.
  * NBS_EINVAL for any other value. */
 #define NBS_PARAM_CONTRACT_CFG 0
 /* NBS_PARAM_CHUNK_QBLOCK: momenta per block of the chunk contractions (default 32). */

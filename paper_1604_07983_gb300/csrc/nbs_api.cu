@@ -376,7 +376,15 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
     // default in FP32: the quad-lane chunk kernel when the tables fit; FP64: the thread-per-momentum kernel
     const bool f32_chunks = sizeof(T) == 4 && h->plan.chunks_ok;
     const bool use_quad = f32_chunks && (h->contract_cfg == 0 || h->contract_cfg == 5);
-    if (h->mode == NBS_BF16X3) {
+    if (h->mode == NBS_BF16X3 && h->plan.chunks_ok && h->contract_cfg != 2) {
+      CK(launch_contract_tcq((const float2*)h->FB.p, h->L, (int)h->plan.quad_chunks.size(), h->chunk_qb,
+                             h->d_qchunks.p, (const int*)h->d_gch.p, (const int*)h->d_citems.p,
+                             (const DevTerm*)h->d_terms.p, (const int*)h->d_ctoff.p,
+                             (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
+                             std::max(h->chunk_st1, h->chunk_st2), h->quad_slot, h->chunk_tab, h->chunk_row,
+                             (float2*)h->Ft.p, h->st),
+         "contraction (tensor cores)");
+    } else if (h->mode == NBS_BF16X3) {
       if (!h->plan.chunks_ok) return fail(h, NBS_EINVAL, "BF16X3 needs channel tables that fit the chunk kernel");
       CK(launch_contract_tc((const float2*)h->FB.p, h->L, (int)h->plan.chunks.size(), h->chunk_qb, h->d_chunks.p,
                             (const int*)h->d_gch.p, (const int*)h->d_citems.p, (const DevTerm*)h->d_terms.p,

@@ -153,13 +153,15 @@ def test_chunk_kernel_forms_agree_bitwise(nbs):
         assert rel(out[2][c], out[0][c]) < 1e-6, c
 
 
-def test_bf16x3_tensor_core_path_all_channels(nbs):
-    """Split-BF16 x 3 contraction on the tensor cores: every channel against the oracle at 2e-5."""
+@pytest.mark.parametrize("cfg", [0, 2])
+def test_bf16x3_tensor_core_path_all_channels(nbs, cfg):
+    """Split-BF16 x 3 contraction on the tensor cores (config 0: quad-lane fragments by movmatrix,
+    config 2: shared-memory staging): every channel against the oracle at 2e-5."""
     L = 4
     props = seeded(1722, L, 2, decay=0.5)
     names = nbs.channel_names()
     ids = list(range(len(names)))
-    F = gpu_correlate(nbs, ids, L, props, nbs.NBS_BF16X3)
+    F = gpu_correlate(nbs, ids, L, props, nbs.NBS_BF16X3, cfg=cfg)
     for c in ids:
         for t in range(2):
             assert rel(F[c, t], oracle(names[c], *props[t], L)) < FP32_TOL, (names[c], t)
