@@ -642,9 +642,9 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
       g.ch_off = (int)plan.group_ch.size();
       g.nch = (int)kv.second.size();
       g.item_off = (int)plan.items.size() / 2;
-      // items in channel order, with their cost
+      // items in channel order, with their cost (products plus gathers of 32 shared indices)
       std::vector<std::pair<int, int>> its;
-      std::vector<double> cost, qcost;
+      std::vector<double> cost;
       for (int local = 0; local < g.nch; ++local) {
         const int ci = kv.second[local];
         plan.group_ch.push_back(ci);
@@ -653,14 +653,8 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
           th.pad = local;
           const int nh1 = 1 << ((th.shape & 1) + (th.shape >> 1 & 1)), nh2 = 4 / nh1;
           for (int k0 = 0; k0 < th.K; k0 += 32) {
-            // warp instructions per step ~ a fixed part (products, loop control) plus
-            // one part per gather entry of a shared index (ratios from instruction counts)
-            const double ent = nh1 * th.n1 + nh2 * th.n2;
-            const int nkb = (std::min(32, th.K - k0) + 15) / 16;  // pair lanes: 16 indices per step
             its.push_back({t, k0});
-            cost.push_back(nkb * (26.0 + ent));
-            const int nks = (std::min(32, th.K - k0) + 7) / 8;    // quad lanes: 8 indices per step
-            qcost.push_back(nks * (23.0 + ent));
+            cost.push_back(64.0 + 4.0 * (nh1 * th.n1 + nh2 * th.n2));
           }
         }
       }
