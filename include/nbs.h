@@ -66,9 +66,12 @@ typedef void (*nbs_free_fn)(void* ptr, void* user);
 int nbs_set_allocator(nbs_alloc_fn alloc, nbs_free_fn free_fn, void* user);
 
 /* Create a context for an L^3 x T lattice on the current CUDA device.
- * flavours: 2 = {light (u = d), strange} (isospin limit, Sec. 4 (i));
- * any other value is rejected with NBS_EINVAL.  1 <= L <= 64, 1 <= T <= 4096.
- * Allocates the propagator store (2 flavours x T timeslices). */
+ * flavours: 2 = {light (u = d), strange} (isospin limit, Sec. 4 (i): the
+ * blocks of n, Sigma-, Xi- are shared with p, Sigma+, Xi0); 3 = {u, d, s}
+ * with u != d (every sink field gets its own stored blocks, propagators
+ * loaded with nbs_load_props3); any other value is rejected with NBS_EINVAL.
+ * 1 <= L <= 64, 1 <= T <= 4096.  Allocates the propagator store
+ * (flavours x T timeslices). */
 int nbs_create(nbs_ctx** out, int L, int T, int flavours);
 int nbs_destroy(nbs_ctx* h);
 
@@ -83,6 +86,10 @@ int nbs_set_stream(nbs_ctx* h, void* stream);
  * V*144 complex numbers of `dtype`; on_device selects device or host
  * pointers.  The library copies; the caller keeps ownership.  0 <= t < T. */
 int nbs_load_props(nbs_ctx* h, const void* u, const void* s, int t, int dtype, int on_device);
+/* The same for a context with flavours = 3: the u, d and s propagators
+ * (same layout and dtype).  NBS_EINVAL on a flavours = 2 context (and
+ * nbs_load_props on a flavours = 3 one). */
+int nbs_load_props3(nbs_ctx* h, const void* u, const void* d, const void* s, int t, int dtype, int on_device);
 
 /* Build the momentum-space baryon blocks of timeslice t: per-timeslice
  * power-of-two rescale of the propagators, blocks of Eq. (4.1) for every
@@ -214,8 +221,10 @@ int nbs_correlate_static(const void* u, const void* s, int L, int dtype, int cha
  * nbs_plan_create runs the host "channel compiler" (Sec. 4 (ii)-(iii): the
  * diagrammatic classification done on the CPU and packed as structures of
  * arrays) for a channel list without touching a GPU.  Tests use it to check
- * the tables on the CPU. */
+ * the tables on the CPU.  nbs_plan_create_flavours compiles for 2 or 3
+ * propagator flavours (nbs_create's meaning); nbs_plan_create uses 2. */
 int nbs_plan_create(nbs_plan** out, const int* channel_ids, int n_channels);
+int nbs_plan_create_flavours(nbs_plan** out, const int* channel_ids, int n_channels, int flavours);
 int nbs_plan_destroy(nbs_plan* p);
 /* sizes[0..NBS_PLAN_NSIZES-1]: see NBS_PS_* below */
 #define NBS_PS_NTYPES     0   /* stored block types                          */

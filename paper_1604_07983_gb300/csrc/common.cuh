@@ -51,17 +51,20 @@ struct TypeRecipe {
 
 // ---- launchers (defined in the .cu files) ----------------------------------
 // kernels_blocks.cu
-cudaError_t launch_props_maxabs(const void* u, const void* s, int in_c64, int V,
+// the propagators of one timeslice, one pointer per flavour (nflav = 2: l, s; 3: u, d, s)
+struct PropPtrs { const void* p[3]; };
+cudaError_t launch_props_maxabs(const PropPtrs& props, int nflav, int in_c64, int V,
                                 unsigned long long* maxbits, int* flags, cudaStream_t st);
 template <typename T>
-cudaError_t launch_props_scale(const void* u, const void* s, int in_c64, int V,
+cudaError_t launch_props_scale(const PropPtrs& props, int nflav, int in_c64, int V,
                                const unsigned long long* maxbits, int* exps, C<T>* out, cudaStream_t st);
+// Q[(d*3 + c)*144 + j1*12 + j2][site] for the n_diquarks(nflav) diquarks of plan.h
 template <typename T>
-cudaError_t launch_diquarks(const C<T>* props, int V, C<T>* Q, cudaStream_t st);
+cudaError_t launch_diquarks(const C<T>* props, int V, int nflav, C<T>* Q, cudaStream_t st);
 struct TypeRecipeSet { TypeRecipe t[NBS_MAX_TYPES]; };
 template <typename T>
 cudaError_t launch_field_blocks(const C<T>* props, const C<T>* Q, const int* cells, int ncells,
-                                const TypeRecipeSet& recipes, int V, C<T>* FB, cudaStream_t st);
+                                const TypeRecipeSet& recipes, int V, int nflav, C<T>* FB, cudaStream_t st);
 // fft.cu
 cudaError_t fft_init();
 bool fft_supported(int L);
@@ -115,8 +118,9 @@ cudaError_t launch_contract_tc(const float2* FB, int L, int nchunks, int qb, con
                                const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
                                const float* codes, int st1, int st2, int max_slot, int max_tab, float2* Ft,
                                cudaStream_t st);
+// ch_fl: per channel the quarks of each propagator (3 ints); exps: per propagator
 template <typename T>
-cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_nl, const int* exps,
+cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_fl, const int* exps, int nflav,
                            double2* out, long long ch_stride, cudaStream_t st);
 
 }  // namespace nbs

@@ -7,7 +7,9 @@
 //
 // Stage a1: the diquarks
 //   Q^{d}_c(x; j1, j2) = sum_{ab} eps_abc sum_{beta gamma} (Cg5)_{beta gamma}
-//                        S_l[x](beta a; j1) S_{l or s}[x](gamma b; j2)      (d = ll, ls)
+//                        S_f0[x](beta a; j1) S_f1[x](gamma b; j2)
+// for the diquark flavour pairs d = (f0, f1) of plan.h (ll, ls with u = d;
+// uu, ud, dd, us, ds with three propagators)
 // then the stored field blocks
 //   FB_T(alpha; y0, y1, y2) = sum_terms coef * sum_c Q^{d}_c(y_a0, y_a1) S_f3[x](alpha c; y_a2),
 // i.e. the normal block of Eq. (4.1) N^{f1 f2 f3}_alpha(j1, j2, j3)
@@ -16,6 +18,7 @@
 // that the paper does per field, Sec. 4 (i)-(ii)).
 // Output layout: FB[cell][site][alpha]: per cell four interleaved L^3 cubes.
 #include "common.cuh"
+#include "plan.h"
 
 namespace nbs {
 
@@ -29,10 +32,9 @@ __device__ __forceinline__ double cabs2(double2 z) { return z.x * z.x + z.y * z.
 __device__ __forceinline__ double cabs2(float2 z) { return (double)z.x * z.x + (double)z.y * z.y; }
 
 template <typename Tin>
-__global__ void __launch_bounds__(256) k_maxabs(const typename InC<Tin>::type* __restrict__ u,
-                                                const typename InC<Tin>::type* __restrict__ s, long long n,
+__global__ void __launch_bounds__(256) k_maxabs(const PropPtrs props, long long n,
                                                 unsigned long long* __restrict__ maxbits, int* __restrict__ flags) {
-  const auto* src = blockIdx.y == 0 ? u : s;
+  const auto* src = reinterpret_cast<const typename InC<Tin>::type*>(props.p[blockIdx.y]);
   double m = 0.0;
   bool bad = false;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -64,14 +66,13 @@ __device__ __forceinline__ int scale_exponent(unsigned long long bits) {
 
 // 16 sites per block; out[f][e][site] = in[site][e] * 2^-exp_f
 template <typename Tin, typename T>
-__global__ void __launch_bounds__(256) k_scale_transpose(const typename InC<Tin>::type* __restrict__ u,
-                                                         const typename InC<Tin>::type* __restrict__ s, int V,
+__global__ void __launch_bounds__(256) k_scale_transpose(const PropPtrs props, int V,
                                                          const unsigned long long* __restrict__ maxbits,
                                                          int* __restrict__ exps, C<T>* __restrict__ out) {
   constexpr int NS = 16;
   __shared__ C<T> tile[144][NS + 1];
   const int f = blockIdx.y;
-  const auto* src = f == 0 ? u : s;
+  const auto* src = reinterpret_cast<const typename InC<Tin>::type*>(props.p[f]);
   const int e = scale_exponent(maxbits[f]);
   if (blockIdx.x == 0 && threadIdx.x == 0) exps[f] = e;
   const int site0 = blockIdx.x * NS;
@@ -88,14 +89,17 @@ __global__ void __launch_bounds__(256) k_scale_transpose(const typename InC<Tin>
   }
 }
 
-// Q[(d*3 + c)*144 + j1*12 + j2][site], d = 0 (S_l S_l), 1 (S_l S_s)
+// Q[(d*3 + c)*144 + j1*12 + j2][site] for diquark d = (f0, f1)
+struct DiquarkPairs { int f0[NBS_MAX_DIQUARKS], f1[NBS_MAX_DIQUARKS]; };
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_diquarks(const C<T>* __restrict__ P, int V, C<T>* __restrict__ Q) {
+__global__ void __launch_bounds__(128) k_diquarks(const C<T>* __restrict__ P, int V, const DiquarkPairs dp,
+                                                  C<T>* __restrict__ Q) {
   const int site = blockIdx.x * blockDim.x + threadIdx.x;
   if (site >= V) return;
   const int d = blockIdx.y / 12, j1 = blockIdx.y % 12;
-  const C<T>* S1 = P;                       // light
-  const C<T>* S2 = P + (long long)d * 144 * V;
+  const C<T>* S1 = P + (long long)dp.f0[d] * 144 * V;
+  const C<T>* S2 = P + (long long)dp.f1[d] * 144 * V;
   C<T> a[12];  // S1[(beta, a); j1], index 3*beta + a
 #pragma unroll
   for (int i = 0; i < 12; ++i) a[i] = S1[(long long)(i * 12 + j1) * V + site];
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(128) k_diquarks(const C<T>* __restrict__ P, in
 }
 
 // one cell per blockIdx.y, sites along x; cells[g] = y0 + 12 y1 + 144 y2 + (type << 11)
-template <typename T>
+template <typename T, int NF>
 __global__ void __launch_bounds__(128) k_field_blocks(const C<T>* __restrict__ P, const C<T>* __restrict__ Q,
                                                       const int* __restrict__ cells, const TypeRecipeSet rs, int V,
                                                       C<T>* __restrict__ FB) {
@@ -147,8 +151,8 @@ __global__ void __launch_bounds__(128) k_field_blocks(const C<T>* __restrict__ P
     const int pat = R.pat[t], arg = R.arg[t];
     const T coef = (T)R.coef[t];
     const int j1 = y[arg & 3], j2 = y[(arg >> 2) & 3], j3 = y[(arg >> 4) & 3];
-    const int d = (pat == 0 || pat == 1) ? 0 : 1;   // LLL, LLS -> ll diquark
-    const int f3 = (pat == 1 || pat == 3) ? 1 : 0;  // LLS, LSS -> strange third quark
+    const int d = pat / NF;   // pattern = diquark * NF + flavour of the third quark
+    const int f3 = pat % NF;
     const C<T>* S3 = P + (long long)f3 * 144 * V;
     C<T> q[3];
 #pragma unroll
@@ -169,54 +173,62 @@ __global__ void __launch_bounds__(128) k_field_blocks(const C<T>* __restrict__ P
 
 }  // namespace
 
-cudaError_t launch_props_maxabs(const void* u, const void* s, int in_c64, int V, unsigned long long* maxbits,
+cudaError_t launch_props_maxabs(const PropPtrs& props, int nflav, int in_c64, int V, unsigned long long* maxbits,
                                 int* flags, cudaStream_t st) {
   long long n = (long long)V * 144;
   int blocks = (int)min((n + 255) / 256, 1216LL);
-  dim3 grid(blocks, 2);
+  dim3 grid(blocks, nflav);
   if (in_c64)
-    k_maxabs<float><<<grid, 256, 0, st>>>((const float2*)u, (const float2*)s, n, maxbits, flags);
+    k_maxabs<float><<<grid, 256, 0, st>>>(props, n, maxbits, flags);
   else
-    k_maxabs<double><<<grid, 256, 0, st>>>((const double2*)u, (const double2*)s, n, maxbits, flags);
+    k_maxabs<double><<<grid, 256, 0, st>>>(props, n, maxbits, flags);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_props_scale(const void* u, const void* s, int in_c64, int V, const unsigned long long* maxbits,
+cudaError_t launch_props_scale(const PropPtrs& props, int nflav, int in_c64, int V, const unsigned long long* maxbits,
                                int* exps, C<T>* out, cudaStream_t st) {
-  dim3 grid((V + 15) / 16, 2);
+  dim3 grid((V + 15) / 16, nflav);
   if (in_c64)
-    k_scale_transpose<float, T><<<grid, 256, 0, st>>>((const float2*)u, (const float2*)s, V, maxbits, exps, out);
+    k_scale_transpose<float, T><<<grid, 256, 0, st>>>(props, V, maxbits, exps, out);
   else
-    k_scale_transpose<double, T><<<grid, 256, 0, st>>>((const double2*)u, (const double2*)s, V, maxbits, exps, out);
+    k_scale_transpose<double, T><<<grid, 256, 0, st>>>(props, V, maxbits, exps, out);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_diquarks(const C<T>* props, int V, C<T>* Q, cudaStream_t st) {
-  dim3 grid((V + 127) / 128, 24);
-  k_diquarks<T><<<grid, 128, 0, st>>>(props, V, Q);
+cudaError_t launch_diquarks(const C<T>* props, int V, int nflav, C<T>* Q, cudaStream_t st) {
+  DiquarkPairs dp = {};
+  const int nd = n_diquarks(nflav);
+  for (int d = 0; d < nd; ++d) diquark_flavours(nflav, d, dp.f0[d], dp.f1[d]);
+  dim3 grid((V + 127) / 128, nd * 12);
+  k_diquarks<T><<<grid, 128, 0, st>>>(props, V, dp, Q);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_field_blocks(const C<T>* props, const C<T>* Q, const int* cells, int ncells,
-                                const TypeRecipeSet& recipes, int V, C<T>* FB, cudaStream_t st) {
+                                const TypeRecipeSet& recipes, int V, int nflav, C<T>* FB, cudaStream_t st) {
   if (ncells > 65535) return cudaErrorInvalidValue;
   dim3 grid((V + 127) / 128, ncells);
-  k_field_blocks<T><<<grid, 128, 0, st>>>(props, Q, cells, recipes, V, FB);
+  if (nflav == 2)
+    k_field_blocks<T, 2><<<grid, 128, 0, st>>>(props, Q, cells, recipes, V, FB);
+  else if (nflav == 3)
+    k_field_blocks<T, 3><<<grid, 128, 0, st>>>(props, Q, cells, recipes, V, FB);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
-template cudaError_t launch_props_scale<float>(const void*, const void*, int, int, const unsigned long long*, int*,
+template cudaError_t launch_props_scale<float>(const PropPtrs&, int, int, int, const unsigned long long*, int*,
                                                float2*, cudaStream_t);
-template cudaError_t launch_props_scale<double>(const void*, const void*, int, int, const unsigned long long*, int*,
+template cudaError_t launch_props_scale<double>(const PropPtrs&, int, int, int, const unsigned long long*, int*,
                                                 double2*, cudaStream_t);
-template cudaError_t launch_diquarks<float>(const float2*, int, float2*, cudaStream_t);
-template cudaError_t launch_diquarks<double>(const double2*, int, double2*, cudaStream_t);
+template cudaError_t launch_diquarks<float>(const float2*, int, int, float2*, cudaStream_t);
+template cudaError_t launch_diquarks<double>(const double2*, int, int, double2*, cudaStream_t);
 template cudaError_t launch_field_blocks<float>(const float2*, const float2*, const int*, int,
-                                                const TypeRecipeSet&, int, float2*, cudaStream_t);
+                                                const TypeRecipeSet&, int, int, float2*, cudaStream_t);
 template cudaError_t launch_field_blocks<double>(const double2*, const double2*, const int*, int,
-                                                 const TypeRecipeSet&, int, double2*, cudaStream_t);
+                                                 const TypeRecipeSet&, int, int, double2*, cudaStream_t);
 
 }  // namespace nbs

@@ -873,18 +873,18 @@ __device__ __forceinline__ double scaled_double(float f, int ex) {
   return ldexp((double)f, ex);
 }
 
-// out[ch * ch_stride + c*V + r] = Ft[ch][c][r] * 2^(e_l n_l + e_s n_s) / V
+// out[ch * ch_stride + c*V + r] = Ft[ch][c][r] * 2^(sum_f e_f n_f) / V
 // FP32 input: 1/V applied in FP32, the power of two added to the exponent
 // (no FP64 arithmetic, which is scarce on GB300); two complex values per
 // 16-byte load and RS independent loads in flight per thread.  FP64 input:
 // FP64 multiply.
 template <typename T>
-__global__ void __launch_bounds__(256) k_restore(const C<T>* __restrict__ Ft, long long V, const int* __restrict__ ch_nl,
-                                                 const int* __restrict__ exps, double2* __restrict__ out,
+__global__ void __launch_bounds__(256) k_restore(const C<T>* __restrict__ Ft, long long V, const int* __restrict__ ch_fl,
+                                                 const int* __restrict__ exps, int nflav, double2* __restrict__ out,
                                                  long long ch_stride) {
   const int ch = blockIdx.y;
-  const int nl = ch_nl[ch];
-  const int ex = exps[0] * nl + exps[1] * (6 - nl);
+  int ex = 0;  // sum over the propagators of (their exponent) x (their quarks in the sink pair)
+  for (int f = 0; f < nflav; ++f) ex += exps[f] * ch_fl[3 * ch + f];
   const long long n = 64 * V;
   const C<T>* src = Ft + ch * n;
   double2* dst = out + ch * ch_stride;
@@ -1015,13 +1015,13 @@ cudaError_t launch_contract_chunk2(const float2* FB, int L, int nchunks, int qb,
 }
 
 template <typename T>
-cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_nl, const int* exps, double2* out,
+cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_fl, const int* exps, int nflav, double2* out,
                            long long ch_stride, cudaStream_t st) {
   long long n = 64LL * V;
   if (sizeof(T) == 4) n /= 8;  // 16-byte loads, four per thread per pass
   int bx = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096));
   dim3 grid(bx, nch);
-  k_restore<T><<<grid, 256, 0, st>>>(Ft, (long long)V, ch_nl, exps, out, ch_stride);
+  k_restore<T><<<grid, 256, 0, st>>>(Ft, (long long)V, ch_fl, exps, nflav, out, ch_stride);
   return cudaGetLastError();
 }
 
@@ -1037,9 +1037,9 @@ template cudaError_t launch_contract_slab<double>(const double2*, int, int, cons
                                                   double2*, cudaStream_t);
 template size_t slab_smem_bytes<float>(int, int, int);
 template size_t slab_smem_bytes<double>(int, int, int);
-template cudaError_t launch_restore<float>(const float2*, int, int, const int*, const int*, double2*, long long,
+template cudaError_t launch_restore<float>(const float2*, int, int, const int*, const int*, int, double2*, long long,
                                            cudaStream_t);
-template cudaError_t launch_restore<double>(const double2*, int, int, const int*, const int*, double2*, long long,
+template cudaError_t launch_restore<double>(const double2*, int, int, const int*, const int*, int, double2*, long long,
                                             cudaStream_t);
 
 }  // namespace nbs

@@ -58,6 +58,7 @@ struct nbs_plan {
 
 struct nbs_ctx {
   int L = 0, T = 0, V = 0, device = 0;
+  int nflav = 2;                 // propagators per timeslice: 2 (l = u = d, s) or 3 (u, d, s)
   unsigned buf_gen = 0;          // bumped by every device (re)allocation
   bool capturing = false;        // enqueueing into a CUDA graph: no allocation, no host synchronisation
   cudaStream_t gst = nullptr;    // capture stream
@@ -236,7 +237,7 @@ int upload_tables(nbs_ctx* h) {
   CK(cudaMemcpyAsync(h->d_items.p, P.items.data(), P.items.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload items");
   if ((rc = ensure(h, h->d_terms, std::max<size_t>(terms.size(), 1) * sizeof(DevTerm), "terms"))) return rc;
   if ((rc = ensure(h, h->d_chtb, P.ch_term_begin.size() * sizeof(int), "term ranges"))) return rc;
-  if ((rc = ensure(h, h->d_chnl, std::max<size_t>(P.ch_nl.size(), 1) * sizeof(int), "flavour content"))) return rc;
+  if ((rc = ensure(h, h->d_chnl, std::max<size_t>(P.ch_fl.size(), 3) * sizeof(int), "flavour content"))) return rc;
   std::vector<int> cells(P.ncells);
   for (size_t ti = 0; ti < P.types.size(); ++ti) {
     const BlockType& bt = P.types[ti];
@@ -245,7 +246,8 @@ int upload_tables(nbs_ctx* h) {
   if ((rc = ensure(h, h->d_cells, std::max<size_t>(cells.size(), 1) * sizeof(int), "cells"))) return rc;
   CK(cudaMemcpyAsync(h->d_terms.p, terms.data(), terms.size() * sizeof(DevTerm), cudaMemcpyHostToDevice, h->st), "upload terms");
   CK(cudaMemcpyAsync(h->d_chtb.p, P.ch_term_begin.data(), P.ch_term_begin.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload ranges");
-  CK(cudaMemcpyAsync(h->d_chnl.p, P.ch_nl.data(), P.ch_nl.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload nl");
+  CK(cudaMemcpyAsync(h->d_chnl.p, P.ch_fl.data(), P.ch_fl.size() * sizeof(int), cudaMemcpyHostToDevice, h->st),
+     "upload flavour content");
   CK(cudaMemcpyAsync(h->d_cells.p, cells.data(), cells.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload cells");
   std::memset(&h->recipes, 0, sizeof(h->recipes));
   if (P.types.size() > NBS_MAX_TYPES) return fail(h, NBS_EINVAL, "too many block types");
@@ -292,7 +294,7 @@ int ensure_plan(nbs_ctx* h, const std::vector<int>& ids) {
     if (h->tables_mode != h->mode) return upload_tables(h);
     return NBS_OK;
   }
-  std::string e = compile_plan(ids, h->plan);
+  std::string e = compile_plan(ids, h->plan, h->nflav);
   if (!e.empty()) {
     h->plan_ok = false;
     return fail(h, NBS_EINVAL, e);
@@ -314,22 +316,23 @@ int build_blocks(nbs_ctx* h, int t) {
   const int V = h->V;
   const Plan& P = h->plan;
   int rc;
-  if ((rc = ensure(h, h->propsT, 2ull * 144 * V * sizeof(C<T>), "scaled propagators"))) return rc;
-  if ((rc = ensure(h, h->Q, 6ull * 144 * V * sizeof(C<T>), "diquarks"))) return rc;
+  const int nf = h->nflav;
+  if ((rc = ensure(h, h->propsT, (size_t)nf * 144 * V * sizeof(C<T>), "scaled propagators"))) return rc;
+  if ((rc = ensure(h, h->Q, (size_t)n_diquarks(nf) * 3 * 144 * V * sizeof(C<T>), "diquarks"))) return rc;
   if ((rc = ensure(h, h->FB, 4ull * P.ncells * V * sizeof(C<T>), "baryon blocks"))) return rc;
-  const char* base = (const char*)h->props.p + (size_t)t * 2 * V * 144 * sizeof(double2);
-  const void* u = base;
-  const void* s = base + (size_t)V * 144 * sizeof(double2);
+  const char* base = (const char*)h->props.p + (size_t)t * nf * V * 144 * sizeof(double2);
+  PropPtrs pp = {};
+  for (int f = 0; f < nf; ++f) pp.p[f] = base + (size_t)f * V * 144 * sizeof(double2);
   const int c64 = h->have[t] == NBS_C64;
   cudaEvent_t e0 = stage_begin(h);
-  CK(cudaMemsetAsync(h->small.p, 0, 16, h->st), "clear max|S|");  // the NaN flag accumulates over a call
-  CK(launch_props_maxabs(u, s, c64, V, h->maxbits, h->flags, h->st), "max|S|");
-  CK(launch_props_scale<T>(u, s, c64, V, h->maxbits, h->exps, (C<T>*)h->propsT.p, h->st), "rescale");
+  CK(cudaMemsetAsync(h->small.p, 0, 32, h->st), "clear max|S|");  // the NaN flag accumulates over a call
+  CK(launch_props_maxabs(pp, nf, c64, V, h->maxbits, h->flags, h->st), "max|S|");
+  CK(launch_props_scale<T>(pp, nf, c64, V, h->maxbits, h->exps, (C<T>*)h->propsT.p, h->st), "rescale");
   stage_end(h, 0, e0);
   cudaEvent_t e1 = stage_begin(h);
-  CK(launch_diquarks<T>((const C<T>*)h->propsT.p, V, (C<T>*)h->Q.p, h->st), "diquarks");
+  CK(launch_diquarks<T>((const C<T>*)h->propsT.p, V, nf, (C<T>*)h->Q.p, h->st), "diquarks");
   CK(launch_field_blocks<T>((const C<T>*)h->propsT.p, (const C<T>*)h->Q.p, (const int*)h->d_cells.p, P.ncells,
-                            h->recipes, V, (C<T>*)h->FB.p, h->st),
+                            h->recipes, V, nf, (C<T>*)h->FB.p, h->st),
      "field blocks");
   stage_end(h, 1, e1);
   cudaEvent_t e2 = stage_begin(h);
@@ -347,8 +350,8 @@ template <typename T>
 int prepare(nbs_ctx* h, int nch) {
   const int V = h->V;
   int rc;
-  if ((rc = ensure(h, h->propsT, 2ull * 144 * V * sizeof(C<T>), "scaled propagators"))) return rc;
-  if ((rc = ensure(h, h->Q, 6ull * 144 * V * sizeof(C<T>), "diquarks"))) return rc;
+  if ((rc = ensure(h, h->propsT, (size_t)h->nflav * 144 * V * sizeof(C<T>), "scaled propagators"))) return rc;
+  if ((rc = ensure(h, h->Q, (size_t)n_diquarks(h->nflav) * 3 * 144 * V * sizeof(C<T>), "diquarks"))) return rc;
   if ((rc = ensure(h, h->FB, 4ull * h->plan.ncells * V * sizeof(C<T>), "baryon blocks"))) return rc;
   if ((rc = ensure(h, h->Ft, (size_t)nch * 64 * V * sizeof(C<T>), "momentum-space correlators"))) return rc;
   return ensure(h, h->zm, (size_t)nch * 64 * sizeof(C<T>), "zero momentum");
@@ -441,12 +444,14 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
     const long long tt = t - t0;
     if (on_dev) {
       double2* o = (double2*)out + tt * 64 * V;
-      CK(launch_restore<T>((const C<T>*)h->Ft.p, V, nch, (const int*)h->d_chnl.p, h->exps, o, nt * 64 * V, h->st),
+      CK(launch_restore<T>((const C<T>*)h->Ft.p, V, nch, (const int*)h->d_chnl.p, h->exps, h->nflav, o, nt * 64 * V,
+                           h->st),
          "restore");
     } else {
       const int b = (int)(tt & 1);
       if (tt >= 2) CK(cudaStreamWaitEvent(h->st, h->ev_done[b], 0), "wait staging");
-      CK(launch_restore<T>((const C<T>*)h->Ft.p, V, nch, (const int*)h->d_chnl.p, h->exps, (double2*)h->stage[b].p,
+      CK(launch_restore<T>((const C<T>*)h->Ft.p, V, nch, (const int*)h->d_chnl.p, h->exps, h->nflav,
+                           (double2*)h->stage[b].p,
                            64LL * V, h->st),
          "restore");
       CK(cudaEventRecord(h->ev_ready[b], h->st), "event");
@@ -493,7 +498,8 @@ int nbs_set_allocator(nbs_alloc_fn alloc, nbs_free_fn free_fn, void* user) {
 int nbs_create(nbs_ctx** out, int L, int T, int flavours) {
   if (!out) return fail(nullptr, NBS_EINVAL, "null output pointer");
   *out = nullptr;
-  if (flavours != 2) return fail(nullptr, NBS_EINVAL, "only flavours = 2 (light u = d, strange) is supported");
+  if (flavours != 2 && flavours != 3)
+    return fail(nullptr, NBS_EINVAL, "flavours must be 2 (light u = d, strange) or 3 (u, d, s)");
   if (L < 1 || L > 64 || !fft_supported(L))
     return fail(nullptr, NBS_EINVAL, "L must be one of 1 2 3 4 6 8 12 16 24 32 48");
   if (T < 1 || T > 4096) return fail(nullptr, NBS_EINVAL, "T must be in [1, 4096]");
@@ -501,6 +507,7 @@ int nbs_create(nbs_ctx** out, int L, int T, int flavours) {
   h->L = L;
   h->T = T;
   h->V = L * L * L;
+  h->nflav = flavours;
   h->free_fn = g_free;
   h->free_user = g_alloc_user;
   h->have.assign(T, -1);
@@ -521,16 +528,16 @@ int nbs_create(nbs_ctx** out, int L, int T, int flavours) {
     return fail(nullptr, NBS_ENOMEM, "pinned flag");
   }
   *h->host_flags = 0;
-  int rc = ensure(h, h->props, (size_t)T * 2 * h->V * 144 * sizeof(double2), "propagator store");
+  int rc = ensure(h, h->props, (size_t)T * flavours * h->V * 144 * sizeof(double2), "propagator store");
   if (!rc) rc = ensure(h, h->small, 256, "scale scratch");
   if (rc) {
     std::string m = h->err;
     nbs_destroy(h);
     return fail(nullptr, rc, m);
   }
-  h->maxbits = (unsigned long long*)h->small.p;
-  h->flags = (int*)((char*)h->small.p + 16);
-  h->exps = (int*)((char*)h->small.p + 64);
+  h->maxbits = (unsigned long long*)h->small.p;  // one per flavour (<= 3)
+  h->flags = (int*)((char*)h->small.p + 32);
+  h->exps = (int*)((char*)h->small.p + 64);      // one per flavour
   *out = h;
   return NBS_OK;
 }
@@ -569,19 +576,35 @@ int nbs_set_stream(nbs_ctx* h, void* stream) {
   return NBS_OK;
 }
 
-int nbs_load_props(nbs_ctx* h, const void* u, const void* s, int t, int dtype, int on_device) {
-  if (!h) return fail(nullptr, NBS_EINVAL, "null context");
-  if (!u || !s) return fail(h, NBS_EINVAL, "null propagator pointer");
+namespace {
+int load_props(nbs_ctx* h, const void* const* src, int n, int t, int dtype, int on_device) {
+  for (int f = 0; f < n; ++f)
+    if (!src[f]) return fail(h, NBS_EINVAL, "null propagator pointer");
   if (t < 0 || t >= h->T) return fail(h, NBS_EINVAL, "timeslice out of range");
   if (dtype != NBS_C128 && dtype != NBS_C64) return fail(h, NBS_EINVAL, "dtype must be NBS_C128 or NBS_C64");
   const size_t bytes = (size_t)h->V * 144 * (dtype == NBS_C128 ? sizeof(double2) : sizeof(float2));
-  char* base = (char*)h->props.p + (size_t)t * 2 * h->V * 144 * sizeof(double2);
+  char* base = (char*)h->props.p + (size_t)t * h->nflav * h->V * 144 * sizeof(double2);
   cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  CK(cudaMemcpyAsync(base, u, bytes, k, h->st), "copy u");
-  CK(cudaMemcpyAsync(base + (size_t)h->V * 144 * sizeof(double2), s, bytes, k, h->st), "copy s");
+  for (int f = 0; f < n; ++f)
+    CK(cudaMemcpyAsync(base + (size_t)f * h->V * 144 * sizeof(double2), src[f], bytes, k, h->st), "copy propagator");
   h->have[t] = (signed char)dtype;
   if (h->blocks_t == t) h->blocks_t = -1;
   return NBS_OK;
+}
+}  // namespace
+
+int nbs_load_props(nbs_ctx* h, const void* u, const void* s, int t, int dtype, int on_device) {
+  if (!h) return fail(nullptr, NBS_EINVAL, "null context");
+  if (h->nflav != 2) return fail(h, NBS_EINVAL, "a context with flavours = 3 takes nbs_load_props3");
+  const void* src[2] = {u, s};
+  return load_props(h, src, 2, t, dtype, on_device);
+}
+
+int nbs_load_props3(nbs_ctx* h, const void* u, const void* d, const void* s, int t, int dtype, int on_device) {
+  if (!h) return fail(nullptr, NBS_EINVAL, "null context");
+  if (h->nflav != 3) return fail(h, NBS_EINVAL, "nbs_load_props3 needs a context created with flavours = 3");
+  const void* src[3] = {u, d, s};
+  return load_props(h, src, 3, t, dtype, on_device);
 }
 
 int nbs_blocks(nbs_ctx* h, int t) {
@@ -753,11 +776,11 @@ int nbs_zero_momentum(nbs_ctx* h, double* out) {
   } else {
     CK(cudaMemcpy(tmp.data(), h->zm.p, n * sizeof(double2), cudaMemcpyDeviceToHost), "zero momentum");
   }
-  int e[2];
-  CK(cudaMemcpy(e, h->exps, sizeof(e), cudaMemcpyDeviceToHost), "exponents");
+  int e[3] = {0, 0, 0};
+  CK(cudaMemcpy(e, h->exps, h->nflav * sizeof(int), cudaMemcpyDeviceToHost), "exponents");
   for (int c = 0; c < h->last_nch; ++c) {
-    const int nl = h->plan.ch_nl[c];
-    const double sc = std::ldexp(1.0, e[0] * nl + e[1] * (6 - nl));
+    const int* fl = &h->plan.ch_fl[3 * c];
+    const double sc = std::ldexp(1.0, e[0] * fl[0] + e[1] * fl[1] + e[2] * fl[2]);
     for (int k = 0; k < 128; ++k) out[c * 128 + k] = tmp[c * 128 + k] * sc;
   }
   return NBS_OK;
@@ -785,9 +808,13 @@ int nbs_channel_info(int id, char* buf, int len) {
 const char* nbs_last_error(const nbs_ctx* h) { return h ? h->err.c_str() : g_err.c_str(); }
 
 int nbs_plan_create(nbs_plan** out, const int* channel_ids, int n_channels) {
+  return nbs_plan_create_flavours(out, channel_ids, n_channels, 2);
+}
+
+int nbs_plan_create_flavours(nbs_plan** out, const int* channel_ids, int n_channels, int flavours) {
   if (!out || !channel_ids || n_channels < 1) return fail(nullptr, NBS_EINVAL, "bad arguments");
   nbs_plan* p = new nbs_plan();
-  std::string e = compile_plan(std::vector<int>(channel_ids, channel_ids + n_channels), p->plan);
+  std::string e = compile_plan(std::vector<int>(channel_ids, channel_ids + n_channels), p->plan, flavours);
   if (!e.empty()) {
     delete p;
     *out = nullptr;

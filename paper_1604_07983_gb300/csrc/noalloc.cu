@@ -42,7 +42,7 @@ constexpr size_t kFB = kQ + 6 * 144 * kMaxV * 16;                      // [cells
 constexpr size_t kFt = kFB + (size_t)kMaxCells * kMaxV * 4 * 16;       // [64][V]
 constexpr size_t kTerms = kFt + 64 * kMaxV * 16;                       // DevTerm[kMaxTerms]
 constexpr size_t kChtb = kTerms + kMaxTerms * sizeof(DevTerm);         // int[2]
-constexpr size_t kChnl = kChtb + 16;                                   // int[1]
+constexpr size_t kChnl = kChtb + 16;                                   // int[3]
 constexpr size_t kCells = kChnl + 16;                                  // int[kMaxCells]
 constexpr size_t kE1 = (kCells + kMaxCells * 4 + 255) / 256 * 256;     // Ent<double>[kMaxEntries]
 constexpr size_t kE2 = kE1 + (size_t)kMaxEntries * sizeof(Ent<double>);
@@ -143,7 +143,7 @@ extern "C" int nbs_correlate_static(const void* u, const void* s, int L, int dty
   for (size_t i = 0; i < e2.size(); ++i) { e2[i].cell = P.ent2_cell[i]; e2[i].pad = 0; e2[i].coef = P.ent2_coef[i]; }
   SCK(cudaMemcpyAsync(base + kTerms, terms.data(), terms.size() * sizeof(DevTerm), cudaMemcpyHostToDevice, st), "terms");
   SCK(cudaMemcpyAsync(base + kChtb, P.ch_term_begin.data(), 2 * sizeof(int), cudaMemcpyHostToDevice, st), "ranges");
-  SCK(cudaMemcpyAsync(base + kChnl, P.ch_nl.data(), sizeof(int), cudaMemcpyHostToDevice, st), "flavours");
+  SCK(cudaMemcpyAsync(base + kChnl, P.ch_fl.data(), 3 * sizeof(int), cudaMemcpyHostToDevice, st), "flavours");
   SCK(cudaMemcpyAsync(base + kCells, cells.data(), cells.size() * sizeof(int), cudaMemcpyHostToDevice, st), "cells");
   SCK(cudaMemcpyAsync(base + kE1, e1.data(), e1.size() * sizeof(Ent<double>), cudaMemcpyHostToDevice, st), "e1");
   SCK(cudaMemcpyAsync(base + kE2, e2.data(), e2.size() * sizeof(Ent<double>), cudaMemcpyHostToDevice, st), "e2");
@@ -158,16 +158,17 @@ extern "C" int nbs_correlate_static(const void* u, const void* s, int L, int dty
   double2* Ft = (double2*)(base + kFt);
   const int c64 = dtype == NBS_C64;
   SCK(cudaMemsetAsync(base + kSmall, 0, 64, st), "clear reduction words");
-  SCK(launch_props_maxabs(u, s, c64, V, maxbits, flags, st), "max|S|");
-  SCK(launch_props_scale<double>(u, s, c64, V, maxbits, exps, props, st), "rescale");
-  SCK(launch_diquarks<double>(props, V, Q, st), "diquarks");
-  SCK(launch_field_blocks<double>(props, Q, (const int*)(base + kCells), P.ncells, rs, V, FB, st), "field blocks");
+  const PropPtrs pp = {{u, s, nullptr}};
+  SCK(launch_props_maxabs(pp, 2, c64, V, maxbits, flags, st), "max|S|");
+  SCK(launch_props_scale<double>(pp, 2, c64, V, maxbits, exps, props, st), "rescale");
+  SCK(launch_diquarks<double>(props, V, 2, Q, st), "diquarks");
+  SCK(launch_field_blocks<double>(props, Q, (const int*)(base + kCells), P.ncells, rs, V, 2, FB, st), "field blocks");
   SCK(fft3d_blocks<double>(FB, P.ncells, L, st), "forward FFT");
   SCK(launch_contract<double>(FB, L, (const DevTerm*)(base + kTerms), (const int*)(base + kChtb), 1,
                               (const Ent<double>*)(base + kE1), (const Ent<double>*)(base + kE2), Ft, 0, st),
       "contraction");
   SCK(fft3d_inverse<double>(Ft, 64, L, st), "inverse FFT");
-  SCK(launch_restore<double>(Ft, V, 1, (const int*)(base + kChnl), exps, (double2*)out, 64LL * V, st), "restore");
+  SCK(launch_restore<double>(Ft, V, 1, (const int*)(base + kChnl), exps, 2, (double2*)out, 64LL * V, st), "restore");
   int flag = 0;
   SCK(cudaMemcpyAsync(&flag, flags, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
   SCK(cudaStreamSynchronize(st), "sync");

@@ -66,16 +66,32 @@ const int kPerm3[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1},
 using RKey = std::array<int, 4>;  // pattern, a0, a1, a2
 using Recipe = std::map<RKey, double>;
 
-int lflav(int q) { return q == FS ? 1 : 0; }
+// propagator index of a quark flavour: l = u = d and s for nflav = 2, u, d, s for 3
+int lflav(int q, int nflav) { return nflav == 2 ? (q == FS ? 1 : 0) : q; }
 
-bool add_term(Recipe& R, int f0, int f1, int f2, int a0, int a1, int a2, double c) {
+int diquark_index(int nflav, int f0, int f1) {
+  for (int d = 0; d < n_diquarks(nflav); ++d) {
+    int g0, g1;
+    diquark_flavours(nflav, d, g0, g1);
+    if (g0 == f0 && g1 == f1) return d;
+  }
+  return -1;
+}
+
+// the pattern's diquark has two quarks of one flavour (symmetric in its two arguments)
+bool same_flavour_diquark(int pat, int nflav) {
+  int f0, f1;
+  diquark_flavours(nflav, pat / nflav, f0, f1);
+  return f0 == f1;
+}
+
+bool add_term(Recipe& R, int nflav, int f0, int f1, int f2, int a0, int a1, int a2, double c) {
   // N^{f0 f1 f2}(j_a0, j_a1, j_a2) = N^{f1 f0 f2}(j_a1, j_a0, j_a2)  (eps and Cg5 both antisymmetric)
   if (f0 > f1) { std::swap(f0, f1); std::swap(a0, a1); }
-  int pat;
-  if (f0 == 0 && f1 == 0) pat = f2 ? LLS : LLL;
-  else if (f0 == 0 && f1 == 1) pat = f2 ? LSS : LSL;
-  else return false;  // two strange quarks in the diquark: not an octet field
-  if ((pat == LLL || pat == LLS) && a0 > a1) std::swap(a0, a1);
+  const int d = diquark_index(nflav, f0, f1);
+  if (d < 0) return false;  // two strange quarks in the diquark: not an octet field
+  const int pat = d * nflav + f2;
+  if (f0 == f1 && a0 > a1) std::swap(a0, a1);
   R[{pat, a0, a1, a2}] += c;
   return true;
 }
@@ -87,12 +103,12 @@ void prune(Recipe& R) {
 }
 
 // R o pi : j -> FB(j_pi(0), j_pi(1), j_pi(2))
-Recipe compose(const Recipe& R, const int* pi) {
+Recipe compose(const Recipe& R, const int* pi, int nflav) {
   Recipe out;
   for (auto& kv : R) {
     int pat = kv.first[0];
     int a0 = pi[kv.first[1]], a1 = pi[kv.first[2]], a2 = pi[kv.first[3]];
-    if ((pat == LLL || pat == LLS) && a0 > a1) std::swap(a0, a1);
+    if (same_flavour_diquark(pat, nflav) && a0 > a1) std::swap(a0, a1);
     out[{pat, a0, a1, a2}] += kv.second;
   }
   prune(out);
@@ -115,14 +131,15 @@ void canonical_flavours(int field, int cf[3]) {
   cf[0] = q[0]; cf[1] = q[1]; cf[2] = q[2];
 }
 
-bool field_recipe(int field, Recipe& R) {
+bool field_recipe(int field, Recipe& R, int nflav) {
   int cf[3];
   canonical_flavours(field, cf);
   for (const Mono& m : field_monomials(field)) {
     for (auto& tau : kPerm3) {
       if (m.q[0] != cf[tau[0]] || m.q[1] != cf[tau[1]] || m.q[2] != cf[tau[2]]) continue;
       double c = m.c * perm_sign(tau, 3);
-      if (!add_term(R, lflav(m.q[0]), lflav(m.q[1]), lflav(m.q[2]), tau[0], tau[1], tau[2], c))
+      if (!add_term(R, nflav, lflav(m.q[0], nflav), lflav(m.q[1], nflav), lflav(m.q[2], nflav), tau[0], tau[1], tau[2],
+                    c))
         return false;
     }
   }
@@ -377,8 +394,10 @@ void build_chunks(Plan& plan) {
 
 }  // namespace
 
-std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
+std::string compile_plan(const std::vector<int>& ids, Plan& plan, int nflav) {
   plan = Plan();
+  if (nflav != 2 && nflav != 3) return "flavours must be 2 (u = d, s) or 3 (u, d, s)";
+  plan.nflav = nflav;
   const auto& table = channel_table();
   // id = channel + n * block: block o3 + 2 o4 selects the source spins
   // alpha3 in {2 o3, 2 o3 + 1}, alpha4 in {2 o4, 2 o4 + 1} (block 0: the upper components)
@@ -400,11 +419,11 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
   for (int f = 0; f < NFIELDS; ++f) {
     if (!used[f]) continue;
     Recipe R;
-    if (!field_recipe(f, R)) return std::string("field ") + field_name(f) + " has no block pattern";
+    if (!field_recipe(f, R, nflav)) return std::string("field ") + field_name(f) + " has no block pattern";
     bool found = false;
     for (int t = 0; t < (int)types.size() && !found; ++t) {
       for (auto& pi : kPerm3) {
-        Recipe C = compose(types[t].R, pi);
+        Recipe C = compose(types[t].R, pi, nflav);
         for (double s : {1.0, -1.0}) {
           if (equal_scaled(R, C, s)) {
             fmap[f].type = t;
@@ -424,7 +443,7 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
     for (auto& pr : pairs) {
       int sw[3] = {0, 1, 2};
       std::swap(sw[pr[0]], sw[pr[1]]);
-      Recipe C = compose(R, sw);
+      Recipe C = compose(R, sw, nflav);
       int sym = equal_scaled(C, R, 1.0) ? 1 : (equal_scaled(C, R, -1.0) ? -1 : 0);
       if (sym) {
         T.bt.pack_p = pr[0]; T.bt.pack_q = pr[1]; T.bt.pack_r = pr[2]; T.bt.pack_sym = sym;
@@ -451,9 +470,14 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan) {
     canonical_flavours(B1, cf1);
     canonical_flavours(B2, cf2);
     {
-      int nl = 0;
-      for (int k = 0; k < 3; ++k) nl += (cf1[k] != FS) + (cf2[k] != FS);
+      int nl = 0, fl[3] = {0, 0, 0};
+      for (int k = 0; k < 3; ++k) {
+        nl += (cf1[k] != FS) + (cf2[k] != FS);
+        ++fl[lflav(cf1[k], nflav)];
+        ++fl[lflav(cf2[k], nflav)];
+      }
       plan.ch_nl.push_back(nl);
+      plan.ch_fl.insert(plan.ch_fl.end(), fl, fl + 3);
     }
     for (const Mono& m3 : field_monomials(ch.b[2])) {
       for (const Mono& m4 : field_monomials(ch.b[3])) {

@@ -12,7 +12,21 @@ namespace nbs {
 enum Flavour { FU = 0, FD = 1, FS = 2 };
 enum Field { P = 0, N, SIGP, SIG0, SIGM, XI0, XIM, LAM, XU, XD, XS, NFIELDS };
 // normal-block flavour patterns (u = d = l): q1 q2 q3
+// Normal-block patterns: pattern = diquark * nflav + flavour of the third
+// quark, the diquark being an ordered flavour pair of the propagators in use.
+// nflav = 2 (u = d = l, s): diquarks ll, ls -> patterns lll, lls, lsl, lss;
+// nflav = 3 (u, d, s):      diquarks uu, ud, dd, us, ds -> 15 patterns.
 enum Pattern { LLL = 0, LLS = 1, LSL = 2, LSS = 3 };
+#define NBS_MAX_DIQUARKS 5
+inline int n_diquarks(int nflav) { return nflav == 2 ? 2 : 5; }
+// flavours (f0 <= f1) of diquark d; -1 if d is out of range
+inline void diquark_flavours(int nflav, int d, int& f0, int& f1) {
+  static const int p2[2][2] = {{0, 0}, {0, 1}};
+  static const int p3[5][2] = {{0, 0}, {0, 1}, {1, 1}, {0, 2}, {1, 2}};
+  if (nflav == 2 && d >= 0 && d < 2) { f0 = p2[d][0]; f1 = p2[d][1]; return; }
+  if (nflav == 3 && d >= 0 && d < 5) { f0 = p3[d][0]; f1 = p3[d][1]; return; }
+  f0 = f1 = -1;
+}
 
 struct Mono { double c; int q[3]; };
 const std::vector<Mono>& field_monomials(int field);
@@ -93,7 +107,9 @@ struct Plan {
   std::vector<int> ent1_cell, ent2_cell;
   std::vector<double> ent1_coef, ent2_coef;
   std::vector<int> ch_term_begin;             // size nch + 1
+  int nflav = 2;                              // propagators: 2 (l = u = d, s) or 3 (u, d, s)
   std::vector<int> ch_nl;                     // light quarks of the sink pair
+  std::vector<int> ch_fl;                     // per channel: quarks of each propagator (3 ints)
   std::vector<GroupHdr> groups;
   std::vector<int> group_ch;
   std::vector<int> items;                     // pairs (term, k0)
@@ -114,7 +130,7 @@ struct Plan {
 #define NBS_SPIN_BLOCKS 4
 
 // Compile the tables for the given channel ids.  Returns "" or an error text.
-std::string compile_plan(const std::vector<int>& channel_ids, Plan& out);
+std::string compile_plan(const std::vector<int>& channel_ids, Plan& out, int nflav = 2);
 
 // Set the text that nbs_last_error(NULL) returns on this thread.
 void set_global_error(const std::string& msg);

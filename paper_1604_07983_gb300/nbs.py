@@ -26,7 +26,8 @@ EXPORTS = ["nbs_set_allocator", "nbs_create", "nbs_destroy", "nbs_set_precision"
            "nbs_load_props", "nbs_blocks", "nbs_correlate", "nbs_zero_momentum", "nbs_set_param", "nbs_set_profiling",
            "nbs_profile", "nbs_channel_count",
            "nbs_channel_info", "nbs_last_error", "nbs_plan_create", "nbs_plan_destroy", "nbs_plan_sizes",
-           "nbs_plan_export", "nbs_correlate_static", "nbs_graph_capture", "nbs_graph_launch", "nbs_graph_destroy"]
+           "nbs_plan_export", "nbs_correlate_static", "nbs_graph_capture", "nbs_graph_launch", "nbs_graph_destroy",
+           "nbs_load_props3", "nbs_plan_create_flavours"]
 
 
 class NBSError(RuntimeError):
@@ -73,6 +74,8 @@ def lib():
         "nbs_graph_capture": (i, [vp, ctypes.POINTER(i), i, i, i, vp, ctypes.POINTER(vp)]),
         "nbs_graph_launch": (i, [vp, i]),
         "nbs_graph_destroy": (i, [vp]),
+        "nbs_load_props3": (i, [vp, vp, vp, vp, i, i, i]),
+        "nbs_plan_create_flavours": (i, [ctypes.POINTER(vp), ctypes.POINTER(i), i, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -115,13 +118,13 @@ PX = dict(TYPES=0, TYPETERMS=1, TYPECOEF=2, CELLS=3, TERMS=4, ENT1_CELL=5, ENT1_
           TERMTABOFF=16, CODES=17)
 
 
-def plan_tables(channel_ids):
-    """Compile the channel tables on the host and return them as numpy arrays."""
+def plan_tables(channel_ids, flavours: int = 2):
+    """Compile the channel tables on the host (2 or 3 propagator flavours) and return them as numpy arrays."""
     import numpy as np
     L = lib()
     ids = (ctypes.c_int * len(channel_ids))(*channel_ids)
     p = ctypes.c_void_p()
-    _check(L.nbs_plan_create(ctypes.byref(p), ids, len(channel_ids)))
+    _check(L.nbs_plan_create_flavours(ctypes.byref(p), ids, len(channel_ids), flavours))
     try:
         s = (ctypes.c_longlong * 12)()
         _check(L.nbs_plan_sizes(p, s))
@@ -270,6 +273,17 @@ class Context:
         _check(self._lib.nbs_load_props(self.h, _ptr(u), _ptr(s), t, NBS_C64 if c64 else NBS_C128, int(on_dev)),
                self.h)
         self._keep = (u, s)
+
+    def load_props3(self, u, d, s, t: int):
+        """u, d, s propagators (u != d) for a context created with flavours=3; arrays as in load_props."""
+        import numpy as np
+        c64 = "complex64" in str(getattr(u, "dtype", ""))
+        on_dev = bool(getattr(u, "is_cuda", False))
+        if not hasattr(u, "data_ptr"):
+            u, d, s = (np.ascontiguousarray(x) for x in (u, d, s))
+        _check(self._lib.nbs_load_props3(self.h, _ptr(u), _ptr(d), _ptr(s), t, NBS_C64 if c64 else NBS_C128,
+                                         int(on_dev)), self.h)
+        self._keep = (u, d, s)
 
     def blocks(self, t: int):
         _check(self._lib.nbs_blocks(self.h, t), self.h)

@@ -23,11 +23,21 @@ def _normal(S1, S2, S3):
     return np.einsum("abc,BG,xBaI,xGbJ,xAcK->xAIJK", _E, _G, r(S1), r(S2), r(S3), optimize=True)
 
 
-def emulate(channel_ids, Sl, Ss, L):
-    """F[ch, alpha1, alpha2, alpha3, alpha4, r] for one timeslice."""
+#: diquark flavour pairs of the normal-block patterns (pattern = diquark * nflav + third flavour)
+_DIQUARKS = {2: [(0, 0), (0, 1)], 3: [(0, 0), (0, 1), (1, 1), (0, 2), (1, 2)]}
+
+
+def emulate(channel_ids, Sl, Ss, L, Sd=None):
+    """F[ch, alpha1, alpha2, alpha3, alpha4, r] for one timeslice.  Sd given: the three-flavour tables
+    (propagators u = Sl, d = Sd, s = Ss); else the two-flavour tables (l = Sl, s = Ss)."""
     V = L ** 3
-    tb = plan_tables(channel_ids)
-    N = {0: _normal(Sl, Sl, Sl), 1: _normal(Sl, Sl, Ss), 2: _normal(Sl, Ss, Sl), 3: _normal(Sl, Ss, Ss)}
+    nf = 2 if Sd is None else 3
+    tb = plan_tables(channel_ids, flavours=nf)
+    S = [Sl, Ss] if nf == 2 else [Sl, Sd, Ss]
+    N = {}
+    for d, (f0, f1) in enumerate(_DIQUARKS[nf]):
+        for f2 in range(nf):
+            N[d * nf + f2] = _normal(S[f0], S[f1], S[f2])
     ncell = len(tb["cells"])
     FB = np.zeros((ncell, 4, V), dtype=complex)
     for ti, (off, nc, toff, nt) in enumerate(tb["types"]):

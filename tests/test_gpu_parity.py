@@ -329,3 +329,34 @@ def test_full_source_spin(nbs):
             sl = (j, 0, slice(None), slice(None), slice(2 * o3, 2 * o3 + 2), slice(2 * o4, 2 * o4 + 2))
             assert rel(F64[sl], ref) < FP64_TOL, (names[c], k)
             assert rel(F32[sl], ref) < FP32_TOL, (names[c], k)
+
+
+def test_three_flavours_u_ne_d(nbs):
+    """flavours = 3 (u != d): FP64 and FP32 against the oracle with distinct u, d, s propagators, and with
+    u = d equal to the two-flavour path."""
+    L = 4
+    names = nbs.channel_names()
+    ids = [0, 4, 9, 24, 39, 51]
+    Su, Sd, Ss = (I.propagator(1751, f, L, 0, 0.5) for f in ("u", "d", "s"))
+    shape = (len(ids), 1, 4, 4, 2, 2, L ** 3)
+    res = {}
+    for prec in (nbs.NBS_FP64, nbs.NBS_FP32):
+        with nbs.Context(L, 1, flavours=3, precision=prec) as ctx:
+            ctx.load_props3(torch.from_numpy(Su).cuda(), torch.from_numpy(Sd).cuda(), torch.from_numpy(Ss).cuda(), 0)
+            out = torch.empty(shape, dtype=torch.complex128, device="cuda")
+            ctx.correlate(ids, 0, 1, out)
+            res[prec] = out.cpu().numpy()
+            with pytest.raises(nbs.NBSError):
+                ctx.load_props(torch.from_numpy(Su).cuda(), torch.from_numpy(Ss).cuda(), 0)
+    props = {"u": Su, "d": Sd, "s": Ss}
+    for k, c in enumerate(ids):
+        ref = O.correlator(names[c], props, L)
+        assert rel(res[nbs.NBS_FP64][k, 0], ref) < FP64_TOL, names[c]
+        assert rel(res[nbs.NBS_FP32][k, 0], ref) < FP32_TOL, names[c]
+    with nbs.Context(L, 1, flavours=3, precision=nbs.NBS_FP64) as ctx:
+        u = torch.from_numpy(Su).cuda()
+        ctx.load_props3(u, u, torch.from_numpy(Ss).cuda(), 0)
+        out3 = torch.empty(shape, dtype=torch.complex128, device="cuda")
+        ctx.correlate(ids, 0, 1, out3)
+    two = gpu_correlate(nbs, ids, L, [(Su, Ss)], nbs.NBS_FP64)
+    assert rel(out3.cpu().numpy(), two) < FP64_TOL

@@ -52,7 +52,7 @@ def test_channel_table(lib):
 
 def test_argument_errors_without_gpu(lib):
     h = ctypes.c_void_p()
-    assert lib.nbs_create(ctypes.byref(h), 8, 8, 3) == nbs.NBS_EINVAL
+    assert lib.nbs_create(ctypes.byref(h), 8, 8, 4) == nbs.NBS_EINVAL
     assert b"flavours" in lib.nbs_last_error(None)
     assert lib.nbs_create(ctypes.byref(h), 5, 8, 2) == nbs.NBS_EINVAL
     assert lib.nbs_create(ctypes.byref(h), 8, 0, 2) == nbs.NBS_EINVAL
@@ -211,3 +211,25 @@ def test_source_spin_blocks_reproduce_oracle(lib):
         assert np.linalg.norm(F[j] - Fo) <= 1e-12 * np.linalg.norm(Fo), (names[c], k)
     with pytest.raises(nbs.NBSError):
         nbs.plan_tables([4 * n])
+
+
+def test_three_flavours_reproduce_oracle(lib):
+    """u != d (flavours = 3): separate stored blocks per sink field, the 15 normal-block patterns over the
+    diquarks uu, ud, dd, us, ds; the compiled tables, run by the emulator on distinct u, d, s
+    propagators, equal the oracle (which never identifies u with d)."""
+    from plan_emulator import emulate
+    names = nbs.channel_names()
+    L = 2
+    Su, Sd, Ss = (I.propagator(63, f, L, 0) for f in ("u", "d", "s"))
+    props = {"u": Su, "d": Sd, "s": Ss}
+    ids = [0, 1, 4, 9, 12, 24, 33, 39, 51]
+    tb = nbs.plan_tables(ids, flavours=3)
+    assert len(tb["types"]) > len(nbs.plan_tables(ids)["types"])   # no isospin sharing
+    F = emulate(ids, Su, Ss, L, Sd=Sd)
+    for j, c in enumerate(ids):
+        Fo = O.correlator(names[c], props, L)
+        assert np.linalg.norm(F[j] - Fo) <= 1e-12 * np.linalg.norm(Fo), names[c]
+    # with u = d the three-flavour tables give the two-flavour result
+    Fl = emulate(ids, Su, Ss, L, Sd=Su)
+    F2 = emulate(ids, Su, Ss, L)
+    assert np.linalg.norm(Fl - F2) <= 1e-12 * np.linalg.norm(F2)
