@@ -56,8 +56,9 @@ def parse():
     ap.add_argument("--decay", type=float, default=DECAY)
     ap.add_argument("--autotune", action="store_true", help="pick the contraction shape with the autotuner first")
     ap.add_argument("--no-graphs", action="store_true", help="batched workload without CUDA graphs")
-    ap.add_argument("--workload", choices=["single", "batched"], default="single",
-                    help="batched: six configurations 2x16^3x32, 2x24^3x48, 2x32^3x32, every timeslice")
+    ap.add_argument("--workload", choices=["single", "batched", "potential"], default="single",
+                    help="batched: six configurations 2x16^3x32, 2x24^3x48, 2x32^3x32, every timeslice; "
+                         "potential: the stencil from correlators to a local potential (nbs_potential)")
     return ap.parse_args()
 
 
@@ -286,6 +287,11 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.destroy_process_group()
         return
+    if args.workload == "potential":
+        run_potential(args, rank, world, P, dist)
+        if dist:
+            dist.destroy_process_group()
+        return
     host_props = make_props_host(L, T, seed, args.decay, args.c64)
 
     ctx = P.Context(L, T, precision=prec)
@@ -494,6 +500,49 @@ def run_batched(args, rank, world, P, prec, ids, dist=None):
                                  "nbs_correlate per (configuration, timeslice)"},
             "gpu_launches": sum(12 if BATCH[ci][0] > 1 else 6 for ci, _ in jobs),
             "clocks": clocks.summary()}), flush=True)
+
+
+def run_potential(args, rank, world, P, dist=None):
+    """nbs_potential on the 52 x 64 correlator components of one timeslice at L^3 (FP64, three timeslices
+    resident): 3 reads and 2 writes of 16 bytes per point, about 45 FP64 operations per point."""
+    import torch
+    L = args.L
+    V = L ** 3
+    n = 52 * 64
+    g = torch.Generator(device="cuda").manual_seed(1763 + rank)
+    R = [torch.randn((n, V), dtype=torch.complex128, device="cuda", generator=g) for _ in range(3)]
+    for _ in range(args.warmup):
+        P.potential(*R, L, 0.125, -1.0, 0.25)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clocks:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        start.record()
+        for _ in range(args.steps):
+            P.potential(*R, L, 0.125, -1.0, 0.25)
+        stop.record()
+        torch.cuda.synchronize()
+    ms = max_over_ranks(start.elapsed_time(stop), dist, "cuda") / args.steps
+    nbytes = 5 * 16.0 * n * V
+    gbs = nbytes / (ms / 1e3) / 1e9
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    # FP64 operations per point: Laplacian 14, time differences 6, combination 8, ratio K/R 17
+    tflops = 45.0 * n * V / (ms / 1e3) / 1e12
+    if rank == 0:
+        print(json.dumps({
+            "metric": "NBS potential stencil (K = a d_t^2 R + b d_t R + c lap R and K/R), points/s at %d^3" % L,
+            "value": job_rate(n * V, world, ms / 1e3), "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic complex Gaussian cubes",
+            "config": {"workload": "52 channels x 64 spin components, %d^3, one timeslice per step" % L},
+            "roofline": {"kernel": "k_potential", "bound": "alu", "achieved": tflops, "peak": 1.25, "unit": "TFLOP/s",
+                         "frac": tflops / 1.25, "traffic": None, "peak_source": "nominal GB300 FP64 1.25 TFLOP/s",
+                         "work_per_launch": "45 FP64 operations x %d points" % (n * V),
+                         "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
+                                 "bytes_per_launch": "3 reads + 2 writes x 16 B per point"}},
+            "gpu_launches": args.steps, "clocks": clocks.summary()}), flush=True)
 
 
 def main():

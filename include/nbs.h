@@ -137,6 +137,21 @@ int nbs_graph_capture(nbs_ctx* h, const int* channel_ids, int n_channels, int t_
 int nbs_graph_launch(nbs_graph* graph, int wait);
 int nbs_graph_destroy(nbs_graph* graph);
 
+/* The stencil from NBS correlators to a local potential (the step that
+ * Sec. 1 motivates: the potential follows from the NBS wave function).  For
+ * n_components cubes R(r, t) (complex128, [component][z][y][x], periodic),
+ * given at t - 1, t, t + 1, writes
+ *   K = a (R(t+1) - 2 R(t) + R(t-1)) + b (R(t+1) - R(t-1)) / 2
+ *     + c sum_{i=x,y,z} (R(r + e_i) + R(r - e_i) - 2 R(r))
+ * and, if ratio_out is not NULL, K / R(t) (IEEE division: infinite or NaN
+ * where R(t) = 0).  All pointers are device pointers; the caller normalises
+ * R (e.g. by the single-baryon correlators) and picks a, b, c (for the
+ * time-dependent method of the paper's Refs. [Ishii:2006ec, Aoki:2009ji]
+ * they carry the reduced mass).  Runs on `stream` (a cudaStream_t, 0 for the
+ * legacy default) and returns when K is written.  No context is needed. */
+int nbs_potential(const void* r_prev, const void* r_cur, const void* r_next, int L, long long n_components,
+                  double a, double b, double c, void* k_out, void* ratio_out, void* stream);
+
 /* Zero-momentum projection of the last nbs_correlate's final timeslice,
  * sum_r F(r) = F~(q = 0), complex128 [n_channels][64] on the host. */
 int nbs_zero_momentum(nbs_ctx* h, double* out);

@@ -361,3 +361,23 @@ def flavour_content(channel) -> tuple[int, int]:
     """(number of light quarks, number of strange quarks) of the sink pair."""
     m = FIELDS[channel[0]][0][1] + FIELDS[channel[1]][0][1]
     return 6 - m.count("s"), m.count("s")
+
+
+# --- from correlators to a local potential (the step Sec. 1 motivates) --------
+
+def potential_stencil(R_prev: np.ndarray, R_cur: np.ndarray, R_next: np.ndarray, L: int, a: float, b: float,
+                      c: float):
+    """K = a d_t^2 R + b d_t R + c lap R and K / R(t) for cubes R[..., V] (site = x + L (y + L z)), periodic.
+
+    Central differences in t (second difference and half the difference of the neighbours); the lattice
+    Laplacian sums the six nearest neighbours minus 6 R.  The caller normalises R and picks a, b, c.
+    """
+    shape = R_cur.shape
+    cube = lambda R: R.reshape(shape[:-1] + (L, L, L))  # axes (z, y, x)
+    Rc = cube(R_cur)
+    lap = -6.0 * Rc
+    for ax in (-1, -2, -3):
+        lap = lap + np.roll(Rc, 1, axis=ax) + np.roll(Rc, -1, axis=ax)
+    K = a * (R_next - 2.0 * R_cur + R_prev) + b * 0.5 * (R_next - R_prev) + c * lap.reshape(shape)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return K, K / R_cur

@@ -123,4 +123,8 @@ template <typename T>
 cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_fl, const int* exps, int nflav,
                            double2* out, long long ch_stride, cudaStream_t st);
 
+// kernels_potential.cu: K = a d_t^2 R + b d_t R + c lap R, P = K / R (P may be null)
+cudaError_t launch_potential(const double2* Rm, const double2* R0, const double2* Rp, int L, long long ncomp, double a,
+                             double b, double c, double2* K, double2* P, cudaStream_t st);
+
 }  // namespace nbs

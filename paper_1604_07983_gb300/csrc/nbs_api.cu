@@ -726,6 +726,20 @@ int nbs_graph_destroy(nbs_graph* graph) {
   return NBS_OK;
 }
 
+int nbs_potential(const void* r_prev, const void* r_cur, const void* r_next, int L, long long n_components, double a,
+                  double b, double c, void* k_out, void* ratio_out, void* stream) {
+  if (!r_prev || !r_cur || !r_next || !k_out) return fail(nullptr, NBS_EINVAL, "null array");
+  if (L < 1 || L > 64) return fail(nullptr, NBS_EINVAL, "L must be in [1, 64]");
+  if (n_components < 0 || n_components > (1LL << 40) / ((long long)L * L * L))
+    return fail(nullptr, NBS_EINVAL, "bad number of components");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_potential((const double2*)r_prev, (const double2*)r_cur, (const double2*)r_next, L,
+                                   n_components, a, b, c, (double2*)k_out, (double2*)ratio_out, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "potential stencil");
+  return NBS_OK;
+}
+
 int nbs_set_param(nbs_ctx* h, int param, int value) {
   if (!h) return fail(nullptr, NBS_EINVAL, "null context");
   switch (param) {

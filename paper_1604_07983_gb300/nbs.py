@@ -27,7 +27,7 @@ EXPORTS = ["nbs_set_allocator", "nbs_create", "nbs_destroy", "nbs_set_precision"
            "nbs_profile", "nbs_channel_count",
            "nbs_channel_info", "nbs_last_error", "nbs_plan_create", "nbs_plan_destroy", "nbs_plan_sizes",
            "nbs_plan_export", "nbs_correlate_static", "nbs_graph_capture", "nbs_graph_launch", "nbs_graph_destroy",
-           "nbs_load_props3", "nbs_plan_create_flavours"]
+           "nbs_load_props3", "nbs_plan_create_flavours", "nbs_potential"]
 
 
 class NBSError(RuntimeError):
@@ -76,6 +76,7 @@ def lib():
         "nbs_graph_destroy": (i, [vp]),
         "nbs_load_props3": (i, [vp, vp, vp, vp, i, i, i]),
         "nbs_plan_create_flavours": (i, [ctypes.POINTER(vp), ctypes.POINTER(i), i, i]),
+        "nbs_potential": (i, [vp, vp, vp, i, ll, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -210,6 +211,18 @@ def assemble_full_spin(out):
         o3, o4 = k & 1, k >> 1
         full[:, :, :, :, 2 * o3:2 * o3 + 2, 2 * o4:2 * o4 + 2] = parts[k]
     return full
+
+
+def potential(r_prev, r_cur, r_next, L: int, a: float, b: float, c: float, ratio: bool = True, stream=None):
+    """nbs_potential on device complex128 tensors [..., L^3] (same shape): returns K (and K / R(t))."""
+    import torch
+    n = r_cur.numel() // (L ** 3)
+    K = torch.empty_like(r_cur)
+    P = torch.empty_like(r_cur) if ratio else None
+    h = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().nbs_potential(_ptr(r_prev), _ptr(r_cur), _ptr(r_next), L, n, a, b, c, _ptr(K),
+                               _ptr(P) if P is not None else None, ctypes.c_void_p(h)))
+    return (K, P) if ratio else K
 
 
 # ---- context -----------------------------------------------------------------

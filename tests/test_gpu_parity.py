@@ -384,3 +384,23 @@ def test_48cube_complex64_storage(nbs):
     G32 = gpu_correlate(nbs, sub, L, rot, nbs.NBS_FP32, c64=True)
     for k, c in enumerate(sub):
         assert rel(G32[k, 0], F64[c, 0]) < FP32_TOL, names[c]
+
+
+def test_potential_stencil(nbs):
+    """nbs_potential against the oracle's stencil: random cubes at 5^3 and 8^3, and the correlators of one
+    channel on three consecutive timeslices (FP64 path) at 4^3."""
+    rng = np.random.default_rng(1761)
+    for L, n in ((5, 3), (8, 2)):
+        R = [rng.standard_normal((n, L ** 3)) + 1j * rng.standard_normal((n, L ** 3)) for _ in range(3)]
+        a, b, c = 0.125, -1.0, 0.25
+        K, P = nbs.potential(*(torch.from_numpy(x).cuda() for x in R), L, a, b, c)
+        Ko, Po = O.potential_stencil(R[0], R[1], R[2], L, a, b, c)
+        assert rel(K.cpu().numpy(), Ko) < 1e-14 and rel(P.cpu().numpy(), Po) < 1e-13
+    L = 4
+    props = seeded(1762, L, 3, decay=0.5)
+    F = gpu_correlate(nbs, [0], L, props, nbs.NBS_FP64)[0]          # [t, 4, 4, 2, 2, V]
+    R = [F[t].reshape(64, L ** 3) for t in range(3)]
+    K = nbs.potential(*(torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in R), L, 0.1, -1.0, 0.2,
+                      ratio=False)
+    Ko, _ = O.potential_stencil(R[0], R[1], R[2], L, 0.1, -1.0, 0.2)
+    assert rel(K.cpu().numpy(), Ko) < 1e-13

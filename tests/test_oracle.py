@@ -316,3 +316,27 @@ def test_direct_sum_paths_agree():
     assert rel(a, want) < 1e-13
     b = O.direct_sum(E1, E2, L, rs, table_bytes=0)   # the per-r branch
     assert rel(b, want) < 1e-13
+
+
+# --- the potential stencil against closed forms ------------------------------------
+
+def test_potential_stencil_closed_forms():
+    """R = exp(i k.r - E t): the lattice Laplacian multiplies by -sum_i 2 (1 - cos k_i), the central first
+    difference by -sinh(E), the second difference by 2 (cosh(E) - 1); each coefficient separately."""
+    L = 6
+    k = 2 * np.pi * np.array([1, 2, 5]) / L
+    E = 0.37
+    x = np.arange(L ** 3) % L
+    y = (np.arange(L ** 3) // L) % L
+    z = np.arange(L ** 3) // (L * L)
+    phase = np.exp(1j * (k[0] * x + k[1] * y + k[2] * z))
+    R = [phase * np.exp(-E * t) for t in (2, 3, 4)]
+    lam = -2.0 * np.sum(1.0 - np.cos(k))
+    for (a, b, c), want in [((0, 0, 1), lam), ((0, 1, 0), -np.sinh(E)), ((1, 0, 0), 2 * (np.cosh(E) - 1))]:
+        K, P = O.potential_stencil(R[0], R[1], R[2], L, a, b, c)
+        assert np.allclose(K, want * R[1], rtol=0, atol=1e-12)
+        assert np.allclose(P, want, rtol=0, atol=1e-12)
+    # a constant field has no Laplacian; linear combination of the three
+    Rc = np.full(L ** 3, 2.0 + 1.0j)
+    K, _ = O.potential_stencil(0.5 * Rc, Rc, 2.0 * Rc, L, 0.3, -1.0, 0.7)
+    assert np.allclose(K, (0.3 * (2.0 - 2.0 + 0.5) - 1.0 * 0.5 * 1.5) * Rc)
