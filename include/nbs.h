@@ -278,6 +278,11 @@ int nbs_plan_sizes(const nbs_plan* p, long long* sizes);
 #define NBS_PX_CHUNKITEMS 15  /* int32 [nchunkitems][2]: term, first shared index            */
 #define NBS_PX_TERMTABOFF 16  /* int32 [nterms][2]: side-1, side-2 offset in the chunk table */
 #define NBS_PX_CODES     17   /* double [32]: |coefficient| of each code (code 31 = 0)       */
+#define NBS_PX_QUADCHUNKS 18  /* int32 [nchunks][128]: the chunks split over the 16 warps of the
+                                 quad-lane kernels: base1, ncell1, base2, ncell2, ch_off, nch,
+                                 tab_off, tab_len, item_off, nslot, wi0[16], kb0[16], wi1[16],
+                                 kb1[16] (warp w: 8-index steps kb0..kb1 of chunk items wi0..wi1),
+                                 out_base[17], cfirst[16], ch_local0, padding              */
 int nbs_plan_export(const nbs_plan* p, int what, void* dst);
 
 #ifdef __cplusplus

@@ -203,17 +203,8 @@ __device__ __forceinline__ void slab_load_a1<float, 2>(const uint4* S, int strid
   x[1] = make_float2(a.z, a.w);
 }
 template <>
-__device__ __forceinline__ void slab_load_a1<float, 4>(const uint4* S, int stride, int cell, int ag, float2 (&x)[4]) {
-  slab_load<float>(S, stride, cell, x);
-}
-template <>
 __device__ __forceinline__ void slab_load_a1<double, 1>(const uint4* S, int stride, int cell, int ag, double2 (&x)[1]) {
   x[0] = *reinterpret_cast<const double2*>(S + ag * stride + cell);
-}
-template <>
-__device__ __forceinline__ void slab_load_a1<double, 2>(const uint4* S, int stride, int cell, int ag, double2 (&x)[2]) {
-  x[0] = *reinterpret_cast<const double2*>(S + (2 * ag) * stride + cell);
-  x[1] = *reinterpret_cast<const double2*>(S + (2 * ag + 1) * stride + cell);
 }
 
 // N gather entries (N even) from a 16-byte aligned run: cell - base and coefficient

@@ -221,7 +221,10 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
 
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a = lane & 3, kq = lane >> 2;
-  const int it0 = ck.item_off + ck.warp_off[w], it1 = ck.item_off + ck.warp_off[w + 1];
+  // this warp's steps: from step kb0 of item wi0 to step kb1 (exclusive) of item wi1
+  const int it0 = ck.item_off + ck.wi0[w], it1 = ck.item_off + ck.wi1[w];
+  const int sb0 = ck.kb0[w], sb1 = ck.kb1[w];
+  const bool has_work = it0 < it1 || (it0 == it1 && sb0 < sb1);
   for (long long q = q_begin; q < q_end; ++q) {
     uint4* S = SB + ((q - q_begin) & 1) * slab;
     if (q + 1 < q_end) issue_slabs(q + 1, SB + ((q + 1 - q_begin) & 1) * slab);
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
         for (int z = 0; z < 4; ++z) D[x][y][z] = 0.f;
     unsigned used = 0;  // shapes accumulated since the last flush (warp-uniform)
     int cur = -1;
-    for (int it = it0; it < it1; ++it) {
+    for (int it = it0; has_work && it <= it1; ++it) {
       const int term = items[2 * it], k0 = items[2 * it + 1];
       const DevTerm h = terms[term];
       const int local = h.pad - ck.ch_local0;
@@ -250,7 +253,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
       const unsigned short* T1 = TAB + tab_off[2 * term];
       const unsigned short* T2 = TAB + tab_off[2 * term + 1];
       const int nh1 = 1 << ((h.shape & 1) + ((h.shape >> 1) & 1));
-      for (int kb = 0; kb < 32 && k0 + kb < h.K; kb += 8) {
+      const int kb_end = 8 * (it == it1 ? sb1 : 4);
+      for (int kb = it == it0 ? 8 * sb0 : 0; kb < kb_end && k0 + kb < h.K; kb += 8) {
         const int k = k0 + kb + kq;
         const bool active = k < h.K;  // the four lanes of a quad agree
         const unsigned short* p1 = active ? T1 + k * nh1 * h.n1 : ZROW;

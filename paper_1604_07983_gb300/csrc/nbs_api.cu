@@ -919,6 +919,10 @@ int nbs_plan_export(const nbs_plan* p, int what, void* dst) {
     case NBS_PX_CODES:
       for (int i = 0; i < 32; ++i) D[i] = i < (int)P.coef_codes.size() && i < 31 ? P.coef_codes[i] : 0.0;
       return NBS_OK;
+    case NBS_PX_QUADCHUNKS:
+      static_assert(sizeof(QuadChunkHdr) == 128 * sizeof(int), "quad chunk header layout");
+      if (P.chunks_ok) std::memcpy(I, P.quad_chunks.data(), P.quad_chunks.size() * sizeof(QuadChunkHdr));
+      return NBS_OK;
     default: return fail(nullptr, NBS_EINVAL, "unknown export");
   }
 }

@@ -377,7 +377,52 @@ void build_chunks(Plan& plan) {
       qk.base1 = ck.base1; qk.ncell1 = ck.ncell1; qk.base2 = ck.base2; qk.ncell2 = ck.ncell2;
       qk.ch_off = ck.ch_off; qk.nch = ck.nch; qk.tab_off = ck.tab_off; qk.tab_len = ck.tab_len;
       qk.item_off = ck.item_off; qk.ch_local0 = ck.ch_local0;
-      qk.nslot = split(qcost, NBS_QUAD_WARPS, qk.warp_off, qk.out_base, qk.cfirst);
+      {
+        // split the chunk's 8-index steps (qcost[i] / nsteps[i] each) into NBS_QUAD_WARPS
+        // contiguous ranges of about equal cost
+        std::vector<int> first(its.size() + 1, 0);  // first global step of each item
+        std::vector<double> step_cost;
+        for (size_t i = 0; i < its.size(); ++i) {
+          const TermHdr& th = plan.terms[its[i].first];
+          const int nks = (std::min(32, th.K - its[i].second) + 7) / 8;
+          first[i + 1] = first[i] + nks;
+          for (int j = 0; j < nks; ++j) step_cost.push_back(qcost[i] / nks);
+        }
+        const int nsteps = first.back();
+        double total = 0;
+        for (double x : step_cost) total += x;
+        std::vector<int> cut(NBS_QUAD_WARPS + 1, nsteps);
+        cut[0] = 0;
+        int w = 0;
+        double acc = 0;
+        for (int g = 0; g < nsteps; ++g) {
+          acc += step_cost[g];
+          if (w < NBS_QUAD_WARPS - 1 && acc >= total * (w + 1) / NBS_QUAD_WARPS) cut[++w] = g + 1;
+        }
+        auto locate = [&](int g, int& item, int& kb) {  // global step -> (item, step inside it)
+          item = (int)(std::upper_bound(first.begin(), first.end(), g) - first.begin()) - 1;
+          kb = g - first[item];
+        };
+        qk.out_base[0] = 0;
+        for (int ww = 0; ww < NBS_QUAD_WARPS; ++ww) {
+          int n = 0;
+          qk.cfirst[ww] = 0;
+          if (cut[ww + 1] > cut[ww]) {
+            locate(cut[ww], qk.wi0[ww], qk.kb0[ww]);
+            locate(cut[ww + 1] - 1, qk.wi1[ww], qk.kb1[ww]);
+            ++qk.kb1[ww];  // exclusive
+            const int c0 = plan.terms[its[qk.wi0[ww]].first].pad - c;
+            const int c1 = plan.terms[its[qk.wi1[ww]].first].pad - c;
+            qk.cfirst[ww] = c0;
+            n = c1 - c0 + 1;
+          } else {
+            qk.wi0[ww] = qk.wi1[ww] = 0;
+            qk.kb0[ww] = qk.kb1[ww] = 0;  // no steps
+          }
+          qk.out_base[ww + 1] = qk.out_base[ww] + n;
+        }
+        qk.nslot = qk.out_base[NBS_QUAD_WARPS];
+      }
       plan.quad_chunks.push_back(qk);
       for (auto& it : its) {
         plan.chunk_items.push_back(it.first);

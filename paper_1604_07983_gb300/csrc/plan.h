@@ -87,16 +87,19 @@ struct ChunkHdr {
 // (four lanes per shared index, eight indices per warp step): same tables and
 // items, its own per-warp item ranges and partial-sum slots.
 #define NBS_QUAD_WARPS 16
+// Warp w takes the 8-index steps from step kb0[w] of item wi0[w] up to (not
+// including) step kb1[w] of item wi1[w] (items relative to item_off): ranges are
+// cut at steps, not items, so the warps get nearly equal work.
 struct QuadChunkHdr {
   int base1, ncell1, base2, ncell2;
   int ch_off, nch;
   int tab_off, tab_len;
   int item_off, nslot;
-  int warp_off[NBS_QUAD_WARPS + 1];
+  int wi0[NBS_QUAD_WARPS], kb0[NBS_QUAD_WARPS], wi1[NBS_QUAD_WARPS], kb1[NBS_QUAD_WARPS];
   int out_base[NBS_QUAD_WARPS + 1];
   int cfirst[NBS_QUAD_WARPS];
   int ch_local0;
-  int pad[3];
+  int pad[20];  // 128 ints
 };
 
 struct Plan {

@@ -233,3 +233,27 @@ def test_three_flavours_reproduce_oracle(lib):
     Fl = emulate(ids, Su, Ss, L, Sd=Su)
     F2 = emulate(ids, Su, Ss, L)
     assert np.linalg.norm(Fl - F2) <= 1e-12 * np.linalg.norm(F2)
+
+
+def test_quad_warp_ranges_cover_every_step_once(lib):
+    """The quad-lane kernels cut each chunk's 8-index steps into 16 contiguous warp ranges: every step of
+    every item is taken by exactly one warp and each warp's channels fit its partial-sum slots."""
+    tb = nbs.plan_tables(list(range(52)))
+    T, items = tb["terms"], tb["chunk_items"]
+    for ck, qk in zip(tb["chunks"], tb["quad_chunks"]):
+        item_off, nit = ck[8], ck[10 + 8]
+        nks = [(min(32, T[t][1] - k0) + 7) // 8 for t, k0 in items[item_off:item_off + nit]]
+        wi0, kb0, wi1, kb1 = qk[10:26], qk[26:42], qk[42:58], qk[58:74]
+        out_base, cfirst, ch_local0 = qk[74:91], qk[91:107], qk[107]
+        seen = [[0] * n for n in nks]
+        for w in range(16):
+            if not (wi0[w] < wi1[w] or (wi0[w] == wi1[w] and kb0[w] < kb1[w])):
+                continue
+            for it in range(wi0[w], wi1[w] + 1):
+                local = T[items[item_off + it][0]][7] - ch_local0
+                assert 0 <= local - cfirst[w] < out_base[w + 1] - out_base[w]
+                for st in range(kb0[w] if it == wi0[w] else 0, kb1[w] if it == wi1[w] else 4):
+                    if st < nks[it]:
+                        seen[it][st] += 1
+        assert all(x == 1 for row in seen for x in row)
+        assert qk[9] == out_base[16]
