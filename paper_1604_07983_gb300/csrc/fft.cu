@@ -179,6 +179,60 @@ __global__ void __launch_bounds__(NT) k_fft_contig(C<T>* __restrict__ data, long
   for (int e = threadIdx.x; e < nrow * RL; e += NT) g[e] = sm[(e / RL) * RP + (e % RL)];
 }
 
+// lines along y and z in one pass: a block stages the (z, y) planes of XB
+// consecutive x (IL interleaved values each) of one cube in shared memory --
+// each (z, y) row of XB * IL values is one contiguous run in HBM -- transforms
+// every y line, then every z line, in place, and writes the planes back.  One
+// read and one write of the data instead of two of each.
+template <typename T, int L, int DIR, int IL, int XB, int NT>
+__global__ void __launch_bounds__(NT) k_fft_yz(C<T>* __restrict__ data, long long ncubes) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);  // [z][y][xi][i]
+  constexpr int RUN = XB * IL;                    // contiguous values per (z, y) row
+  constexpr int NE = L * L * RUN;
+  constexpr int NLINE = L * RUN;                  // lines per direction
+  const long long cube = blockIdx.x / (L / XB);
+  const int x0 = (int)(blockIdx.x % (L / XB)) * XB;
+  if (cube >= ncubes) return;
+  C<T>* g = data + cube * (long long)L * L * L * IL + (long long)x0 * IL;
+  for (int e = threadIdx.x; e < NE; e += NT) {
+    const int zy = e / RUN, r = e % RUN;
+    sm[e] = g[(long long)zy * L * IL + r];
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < NLINE; l += NT) {  // y lines: (z, run offset)
+    C<T>* row = sm + (l / RUN) * L * RUN + (l % RUN);
+    C<T> x[L];
+    LoadPerm<T, L>::run(x, row, RUN);
+    Stage<T, L, DIR, 0>::run(x);
+#pragma unroll
+    for (int p = 0; p < L; ++p) row[p * RUN] = x[p];
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < NLINE; l += NT) {  // z lines: (y, run offset)
+    C<T>* row = sm + (l / RUN) * RUN + (l % RUN);
+    C<T> x[L];
+    LoadPerm<T, L>::run(x, row, L * RUN);
+    Stage<T, L, DIR, 0>::run(x);
+#pragma unroll
+    for (int p = 0; p < L; ++p) row[p * L * RUN] = x[p];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NE; e += NT) {
+    const int zy = e / RUN, r = e % RUN;
+    g[(long long)zy * L * IL + r] = sm[e];
+  }
+}
+
+// x values per block of the fused y/z pass: the planes take about 64 KB
+template <typename T, int L, int IL>
+constexpr int yz_xb() {
+  int xb = (int)(65536 / ((long long)L * L * IL * (int)sizeof(C<T>)));
+  if (xb < 1) xb = 1;
+  while (L % xb) --xb;
+  return xb;
+}
+
 // batch cubes of L^3 elements, each element a vector of IL interleaved values
 // sb: threads per block of the two strided passes (64, 128 or 256; a tuning parameter)
 template <typename T, int L, int DIR, int IL>
@@ -197,6 +251,20 @@ cudaError_t run3d(C<T>* data, long long nbatch, int sb, cudaStream_t st) {
     kern<<<(unsigned)blocks, NT, sm, st>>>(data, nlines);
   }
   if (sb != 64 && sb != 128 && sb != 256) return cudaErrorInvalidValue;
+  if constexpr (L >= 16) {  // y and z in one pass through shared memory
+    constexpr int XB = yz_xb<T, L, IL>();
+    constexpr int NT = 256;
+    const size_t sm = (size_t)L * L * XB * IL * sizeof(C<T>);
+    auto kern = k_fft_yz<T, L, DIR, IL, XB, NT>;
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    const long long blocks = nbatch * (L / XB);
+    if (blocks > 2147483647LL) return cudaErrorInvalidValue;
+    kern<<<(unsigned)blocks, NT, sm, st>>>(data, nbatch);
+    return cudaGetLastError();
+  }
   // y: lines (batch, z, x, i): inner = IL*L, group = IL*L^2, stride IL*L
   {
     long long blocks = (nlines + sb - 1) / sb;

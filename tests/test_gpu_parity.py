@@ -404,3 +404,17 @@ def test_potential_stencil(nbs):
                       ratio=False)
     Ko, _ = O.potential_stencil(R[0], R[1], R[2], L, 0.1, -1.0, 0.2)
     assert rel(K.cpu().numpy(), Ko) < 1e-13
+
+
+def test_24cube_sampled_r(nbs):
+    """24^3 (radix-3 FFT, the fused y/z pass with 3 x-values per block; the batched workload's size):
+    FP64 and FP32 against the oracle on sampled separations for the pn channel."""
+    L = 24
+    Sl, Ss = I.propagator(1608, "l", L, 3, 0.5), I.propagator(1608, "s", L, 3, 0.5)
+    F64 = gpu_correlate(nbs, [0], L, [(Sl, Ss)], nbs.NBS_FP64)
+    F32 = gpu_correlate(nbs, [0], L, [(Sl, Ss)], nbs.NBS_FP32)
+    rs = [(0, 0, 0), (1, 0, 0), (0, 23, 0), (12, 12, 12), (5, 17, 9)]
+    idx = [x + L * (y + L * z) for x, y, z in rs]
+    ref = O.correlator(("p", "n", "p", "n"), {"u": Sl, "d": Sl, "s": Ss}, L, rs)
+    assert rel(F64[0, 0][..., idx], ref) < FP64_TOL
+    assert rel(F32[0, 0][..., idx], ref) < FP32_TOL
