@@ -498,7 +498,7 @@ def run_batched(args, rank, world, P, prec, ids, dist=None):
             "config": {"workload": "6 configurations, %d timeslices, all %d channels" % (len(jobs), nch),
                        "launch": "one captured CUDA graph per (configuration, timeslice)" if graphs else
                                  "nbs_correlate per (configuration, timeslice)"},
-            "gpu_launches": sum(12 if BATCH[ci][0] > 1 else 6 for ci, _ in jobs),
+            "gpu_launches": sum((9 if BATCH[ci][0] >= 16 and prec != P.NBS_FP64 else 11) for ci, _ in jobs),
             "clocks": clocks.summary()}), flush=True)
 
 

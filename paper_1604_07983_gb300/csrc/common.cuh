@@ -65,6 +65,10 @@ struct TypeRecipeSet { TypeRecipe t[NBS_MAX_TYPES]; };
 template <typename T>
 cudaError_t launch_field_blocks(const C<T>* props, const C<T>* Q, const int* cells, int ncells,
                                 const TypeRecipeSet& recipes, int V, int nflav, C<T>* FB, cudaStream_t st);
+// diquarks and field blocks in one site-tiled kernel (no diquark array in HBM)
+template <typename T>
+cudaError_t launch_blocks_tiled(const C<T>* props, const int* cells, int ncells, const TypeRecipeSet& recipes, int V,
+                                int nflav, C<T>* FB, cudaStream_t st);
 // fft.cu
 cudaError_t fft_init();
 bool fft_supported(int L);

@@ -251,7 +251,8 @@ cudaError_t run3d(C<T>* data, long long nbatch, int sb, cudaStream_t st) {
     kern<<<(unsigned)blocks, NT, sm, st>>>(data, nlines);
   }
   if (sb != 64 && sb != 128 && sb != 256) return cudaErrorInvalidValue;
-  if constexpr (L >= 16) {  // y and z in one pass through shared memory
+  if constexpr (L >= 16 && sizeof(T) == 4) {  // FP32: y and z in one pass through shared memory (for FP64
+                                              // the planes leave one block per SM and the strided passes win)
     constexpr int XB = yz_xb<T, L, IL>();
     constexpr int NT = 256;
     const size_t sm = (size_t)L * L * XB * IL * sizeof(C<T>);

@@ -171,7 +171,125 @@ __global__ void __launch_bounds__(128) k_field_blocks(const C<T>* __restrict__ P
   for (int al = 0; al < 4; ++al) o[al] = out[al];
 }
 
+// Site-tiled form of the two kernels above: a block owns TS consecutive sites,
+// stages their scaled propagators ([flavour][144][TS]) in shared memory, forms
+// their diquarks there ([diquark][c][144][TS]) and writes every stored cell of
+// those sites.  Propagators are read from HBM once and the diquarks never
+// leave the SM; the cell loop reads its 15 values per term from shared memory
+// instead of L2.
+template <typename T, int NF, int TS>
+__global__ void __launch_bounds__(256) k_blocks_tiled(const C<T>* __restrict__ P, const int* __restrict__ cells,
+                                                      int ncells, const TypeRecipeSet rs, int V, const DiquarkPairs dp,
+                                                      C<T>* __restrict__ FB) {
+  constexpr int NT = 256;
+  constexpr int ND = NF == 2 ? 2 : 5;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* Ps = reinterpret_cast<C<T>*>(smem_raw);  // [NF][144][TS]
+  C<T>* Qs = Ps + NF * 144 * TS;                  // [ND][3][144][TS]
+  const int site0 = blockIdx.x * TS;
+  const int ns = min(TS, V - site0);
+  for (int e = threadIdx.x; e < NF * 144 * TS; e += NT) {
+    const int row = e / TS, st = e % TS;
+    Ps[e] = st < ns ? P[(long long)row * V + site0 + st] : czero<T>();
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < ND * 12 * TS; it += NT) {  // (d, j1, site), loop over j2
+    const int st = it % TS, j1 = (it / TS) % 12, d = it / (12 * TS);
+    const C<T>* S1 = Ps + dp.f0[d] * 144 * TS + st;
+    const C<T>* S2 = Ps + dp.f1[d] * 144 * TS + st;
+    C<T> a[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) a[i] = S1[(i * 12 + j1) * TS];
+    for (int j2 = 0; j2 < 12; ++j2) {
+      C<T> b[12];
+#pragma unroll
+      for (int i = 0; i < 12; ++i) b[i] = S2[(i * 12 + j2) * TS];
+      C<T> D[3][3];
+#pragma unroll
+      for (int ca = 0; ca < 3; ++ca)
+#pragma unroll
+        for (int cb = 0; cb < 3; ++cb) {
+          if (ca == cb) continue;
+          C<T> acc = czero<T>();
+          cfma<T>(acc, a[0 * 3 + ca], b[1 * 3 + cb]);
+          cfma<T>(acc, a[1 * 3 + ca], cmake<T>(-b[0 * 3 + cb].x, -b[0 * 3 + cb].y));
+          cfma<T>(acc, a[2 * 3 + ca], b[3 * 3 + cb]);
+          cfma<T>(acc, a[3 * 3 + ca], cmake<T>(-b[2 * 3 + cb].x, -b[2 * 3 + cb].y));
+          D[ca][cb] = acc;
+        }
+      C<T>* q = Qs + ((d * 3) * 144 + j1 * 12 + j2) * TS + st;
+      q[0] = csub<T>(D[1][2], D[2][1]);
+      q[144 * TS] = csub<T>(D[2][0], D[0][2]);
+      q[288 * TS] = csub<T>(D[0][1], D[1][0]);
+    }
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < ncells * TS; it += NT) {
+    const int st = it % TS, g = it / TS;
+    const int code = cells[g];
+    const int key = code & 2047;
+    const int y[3] = {key % 12, (key / 12) % 12, key / 144};
+    const TypeRecipe& R = rs.t[code >> 11];
+    C<T> out[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
+    for (int t = 0; t < R.nterms; ++t) {
+      const int pat = R.pat[t], arg = R.arg[t];
+      const T coef = (T)R.coef[t];
+      const int j1 = y[arg & 3], j2 = y[(arg >> 2) & 3], j3 = y[(arg >> 4) & 3];
+      const int d = pat / NF, f3 = pat % NF;
+      const C<T>* S3 = Ps + f3 * 144 * TS + st;
+      const C<T>* q = Qs + ((d * 3) * 144 + j1 * 12 + j2) * TS + st;
+      const C<T> q0 = q[0], q1 = q[144 * TS], q2 = q[288 * TS];
+#pragma unroll
+      for (int al = 0; al < 4; ++al) {
+        C<T> n = czero<T>();
+        cfma<T>(n, q0, S3[((3 * al + 0) * 12 + j3) * TS]);
+        cfma<T>(n, q1, S3[((3 * al + 1) * 12 + j3) * TS]);
+        cfma<T>(n, q2, S3[((3 * al + 2) * 12 + j3) * TS]);
+        crfma<T>(out[al], coef, n);
+      }
+    }
+    if (st < ns) {
+      C<T>* o = FB + ((long long)g * V + site0 + st) * 4;
+#pragma unroll
+      for (int al = 0; al < 4; ++al) o[al] = out[al];
+    }
+  }
+}
+
+template <typename T, int NF>
+constexpr int tiled_sites() { return (sizeof(T) == 8 && NF == 3) ? 4 : 8; }
+
 }  // namespace
+
+template <typename T>
+size_t blocks_tiled_smem(int nflav) {
+  const int ts = nflav == 2 ? tiled_sites<T, 2>() : tiled_sites<T, 3>();
+  return (size_t)(nflav + 3 * n_diquarks(nflav)) * 144 * ts * sizeof(C<T>);
+}
+
+template <typename T>
+cudaError_t launch_blocks_tiled(const C<T>* props, const int* cells, int ncells, const TypeRecipeSet& recipes, int V,
+                                int nflav, C<T>* FB, cudaStream_t st) {
+  DiquarkPairs dp = {};
+  for (int d = 0; d < n_diquarks(nflav); ++d) diquark_flavours(nflav, d, dp.f0[d], dp.f1[d]);
+  const size_t sm = blocks_tiled_smem<T>(nflav);
+  if (nflav == 2) {
+    constexpr int TS = tiled_sites<T, 2>();
+    auto kern = k_blocks_tiled<T, 2, TS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<(V + TS - 1) / TS, 256, sm, st>>>(props, cells, ncells, recipes, V, dp, FB);
+  } else if (nflav == 3) {
+    constexpr int TS = tiled_sites<T, 3>();
+    auto kern = k_blocks_tiled<T, 3, TS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<(V + TS - 1) / TS, 256, sm, st>>>(props, cells, ncells, recipes, V, dp, FB);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_props_maxabs(const PropPtrs& props, int nflav, int in_c64, int V, unsigned long long* maxbits,
                                 int* flags, cudaStream_t st) {
@@ -224,6 +342,10 @@ template cudaError_t launch_props_scale<float>(const PropPtrs&, int, int, int, c
                                                float2*, cudaStream_t);
 template cudaError_t launch_props_scale<double>(const PropPtrs&, int, int, int, const unsigned long long*, int*,
                                                 double2*, cudaStream_t);
+template cudaError_t launch_blocks_tiled<float>(const float2*, const int*, int, const TypeRecipeSet&, int, int, float2*,
+                                                cudaStream_t);
+template cudaError_t launch_blocks_tiled<double>(const double2*, const int*, int, const TypeRecipeSet&, int, int,
+                                                 double2*, cudaStream_t);
 template cudaError_t launch_diquarks<float>(const float2*, int, int, float2*, cudaStream_t);
 template cudaError_t launch_diquarks<double>(const double2*, int, int, double2*, cudaStream_t);
 template cudaError_t launch_field_blocks<float>(const float2*, const float2*, const int*, int,

@@ -178,6 +178,9 @@ int ensure(nbs_ctx* h, DevBuf& b, size_t bytes, const char* what) {
   return NBS_OK;
 }
 
+// kernel launches of one 3-D FFT (fft.cu): x pass, then y and z fused for FP32 and L >= 16
+int fft_passes(int L, bool f32) { return L == 1 ? 0 : (L >= 16 && f32 ? 2 : 3); }
+
 // FP32 and BF16X3 share the FP32 blocks and FFTs
 bool is_f32(int mode) { return mode == NBS_FP32 || mode == NBS_BF16X3; }
 
@@ -318,7 +321,6 @@ int build_blocks(nbs_ctx* h, int t) {
   int rc;
   const int nf = h->nflav;
   if ((rc = ensure(h, h->propsT, (size_t)nf * 144 * V * sizeof(C<T>), "scaled propagators"))) return rc;
-  if ((rc = ensure(h, h->Q, (size_t)n_diquarks(nf) * 3 * 144 * V * sizeof(C<T>), "diquarks"))) return rc;
   if ((rc = ensure(h, h->FB, 4ull * P.ncells * V * sizeof(C<T>), "baryon blocks"))) return rc;
   const char* base = (const char*)h->props.p + (size_t)t * nf * V * 144 * sizeof(double2);
   PropPtrs pp = {};
@@ -330,15 +332,14 @@ int build_blocks(nbs_ctx* h, int t) {
   CK(launch_props_scale<T>(pp, nf, c64, V, h->maxbits, h->exps, (C<T>*)h->propsT.p, h->st), "rescale");
   stage_end(h, 0, e0);
   cudaEvent_t e1 = stage_begin(h);
-  CK(launch_diquarks<T>((const C<T>*)h->propsT.p, V, nf, (C<T>*)h->Q.p, h->st), "diquarks");
-  CK(launch_field_blocks<T>((const C<T>*)h->propsT.p, (const C<T>*)h->Q.p, (const int*)h->d_cells.p, P.ncells,
-                            h->recipes, V, nf, (C<T>*)h->FB.p, h->st),
-     "field blocks");
+  CK(launch_blocks_tiled<T>((const C<T>*)h->propsT.p, (const int*)h->d_cells.p, P.ncells, h->recipes, V, nf,
+                            (C<T>*)h->FB.p, h->st),
+     "diquarks and field blocks");
   stage_end(h, 1, e1);
   cudaEvent_t e2 = stage_begin(h);
   CK(fft3d_blocks<T>((C<T>*)h->FB.p, P.ncells, h->L, h->st, h->fft_block), "forward FFT");
   stage_end(h, 2, e2);
-  h->launches += 4 + (h->L > 1 ? 3 : 0);
+  h->launches += 3 + fft_passes(h->L, sizeof(T) == 4);  // max|S|, rescale, tiled blocks, forward FFT
   h->blocks_t = t;
   h->blocks_mode = h->mode;
   h->blocks_gen = h->plan_gen;
@@ -351,7 +352,6 @@ int prepare(nbs_ctx* h, int nch) {
   const int V = h->V;
   int rc;
   if ((rc = ensure(h, h->propsT, (size_t)h->nflav * 144 * V * sizeof(C<T>), "scaled propagators"))) return rc;
-  if ((rc = ensure(h, h->Q, (size_t)n_diquarks(h->nflav) * 3 * 144 * V * sizeof(C<T>), "diquarks"))) return rc;
   if ((rc = ensure(h, h->FB, 4ull * h->plan.ncells * V * sizeof(C<T>), "baryon blocks"))) return rc;
   if ((rc = ensure(h, h->Ft, (size_t)nch * 64 * V * sizeof(C<T>), "momentum-space correlators"))) return rc;
   return ensure(h, h->zm, (size_t)nch * 64 * sizeof(C<T>), "zero momentum");
@@ -430,7 +430,7 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
          "contraction");
     }
     stage_end(h, 3, e3);
-    h->launches += 1 + (h->L > 1 ? 3 : 0) + 1;
+    h->launches += 1 + fft_passes(h->L, sizeof(T) == 4) + 1;  // contraction, inverse FFT, restore
     if (t == t1 - 1) {
       // F~(q = 0) of every (channel, spin) before the inverse transform
       CK(cudaMemcpy2DAsync(h->zm.p, sizeof(C<T>), h->Ft.p, (size_t)V * sizeof(C<T>), sizeof(C<T>), (size_t)nch * 64,
