@@ -8,14 +8,17 @@
  *   F_{a1 a2, a3 a4}(r, t) = sum_X < B1_a1(X + r, t) B2_a2(X, t) Jbar_{B3 a3, B4 a4}(t0) >
  *
  * (Sec. 2, first equation) from wall-source light (u = d) and strange quark
- * propagators, following the paper's pipeline: baryon blocks per site
+ * propagators (or separate u, d, s propagators: flavours = 3), following the
+ * paper's pipeline: baryon blocks per site
  * (Eq. (4.1), Sec. 4 (i)), a forward 3-D FFT per block component (Eq. (2.6)),
  * effective blocks and their product in momentum space (Eqs. (4.2)-(4.3),
  * Sec. 4 (ii)-(iii)) and an inverse FFT.
  *
  * Conventions: Dirac representation with C gamma5 =
  * [[0,1,0,0],[-1,0,0,0],[0,0,0,1],[0,0,-1,0]]; source spins a3, a4 in {0,1}
- * (upper components); forward FFT e^{-iq.x} unnormalised, inverse
+ * (upper components) for channel ids below nbs_channel_count(), the other
+ * three pairs for ids c + k nbs_channel_count() (k = 1, 2, 3; see
+ * nbs_correlate); forward FFT e^{-iq.x} unnormalised, inverse
  * e^{+iq.r}/V; X + r periodic; site = x + L*(y + L*z).
  *
  * Errors: every call returns NBS_OK (0) or a negative NBS_E* code; the text of
