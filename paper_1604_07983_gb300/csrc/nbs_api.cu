@@ -73,7 +73,7 @@ struct nbs_ctx {
 
   DevBuf props;                 // [T][2][V*144] complex128 slots
   std::vector<signed char> have;  // -1 none, NBS_C128, NBS_C64
-  DevBuf propsT, Q, FB, Ft, zm, small;
+  DevBuf propsT, FB, Ft, zm, small;
   DevBuf stage[2];
   unsigned long long* maxbits = nullptr;  // [2]
   int* flags = nullptr;                   // [1]
@@ -546,7 +546,7 @@ int nbs_destroy(nbs_ctx* h) {
   if (!h) return NBS_OK;
   cudaStreamSynchronize(h->st);
   if (h->cst) cudaStreamSynchronize(h->cst);
-  DevBuf* bufs[] = {&h->props, &h->propsT, &h->Q, &h->FB, &h->Ft, &h->zm, &h->small, &h->stage[0], &h->stage[1],
+  DevBuf* bufs[] = {&h->props, &h->propsT, &h->FB, &h->Ft, &h->zm, &h->small, &h->stage[0], &h->stage[1],
                     &h->d_terms, &h->d_chtb, &h->d_chnl, &h->d_e1, &h->d_e2, &h->d_cells, &h->d_groups,
                     &h->d_gch, &h->d_items, &h->d_chunks, &h->d_qchunks, &h->d_ctab, &h->d_citems, &h->d_ctoff,
                     &h->d_codes};
