@@ -386,7 +386,7 @@ def run_ours(args, rank, world, local_rank):
             peak_src = "nominal GB300 FP64 1.25 TFLOP/s"
         ach = flops_per_launch / (per_launch_ms["contract"] / 1e3) / 1e12
         cfg = tuned["cfg"] if tuned else args.contract_cfg
-        kname = {0: "k_contract_quad", 5: "k_contract_quad", 2: "k_contract_chunk", 3: "k_contract_chunk2",
+        kname = {0: "k_contract_qseg", 5: "k_contract_quad", 2: "k_contract_chunk", 3: "k_contract_chunk2",
                  1: "k_contract_slab"}.get(cfg, "k_contract") if prec == P.NBS_FP32 else \
             ("k_contract_slab" if cfg == 1 else "k_contract")
         traffic = None

@@ -161,9 +161,10 @@ int nbs_zero_momentum(nbs_ctx* h, double* out);
 
 /* Launch-shape parameters (for tuning; results agree to rounding).
  * NBS_PARAM_CONTRACT_CFG selects the contraction kernel:
- *   0 = default: the quad-lane chunk kernel (5) in FP32 when the channel
- *       tables fit its shared memory, the thread-per-momentum kernel
- *       (A = 2, W = 1) in FP64;
+ *   0 = default: in FP32, when the channel tables fit its shared memory, the
+ *       quad-lane chunk kernel driven by per-warp term runs (the steps of 5,
+ *       same order, same results; the term form is dispatched once per run);
+ *       in FP64 the thread-per-momentum kernel (A = 2, W = 1);
  *   1 = the momentum-slab kernel (one block per momentum and channel group,
  *       stored blocks staged in shared memory);
  *   2 = the chunk kernel (FP32; persistent blocks that keep a chunk of
@@ -173,7 +174,7 @@ int nbs_zero_momentum(nbs_ctx* h, double* out);
  *   3 = the chunk kernel's second form (FP32; same work split, cheaper inner
  *       loops: signed coefficient table, no divergence), else the default;
  *   5 = the quad-lane chunk kernel (FP32; four lanes per shared index, one
- *       sink spin each, 16 warps per block), else the default;
+ *       sink spin each, 16 warps per block; walks work items), else the default;
  *   A*10 + W = the thread-per-momentum kernel with A sink spins alpha1 per
  *       thread (1, 2 or 4) and W warps per block (1, 2 or 4).
  * In NBS_BF16X3 mode the tensor-core kernels run: the quad-lane form
@@ -285,7 +286,13 @@ int nbs_plan_sizes(const nbs_plan* p, long long* sizes);
                                  quad-lane kernels: base1, ncell1, base2, ncell2, ch_off, nch,
                                  tab_off, tab_len, item_off, nslot, wi0[16], kb0[16], wi1[16],
                                  kb1[16] (warp w: 8-index steps kb0..kb1 of chunk items wi0..wi1),
-                                 out_base[17], cfirst[16], ch_local0, padding              */
+                                 out_base[17], cfirst[16], ch_local0, seg_base[17] (warp w's
+                                 term runs are quad segments seg_base[w] .. seg_base[w+1]),
+                                 padding                                                      */
+#define NBS_PX_QUADSEGS  19   /* int32 [quad_chunks[nchunks-1].seg_base[16]][8]: per-warp runs of
+                                 one term: form (0..3 shape, 4..7 the fixed-length forms), side-1
+                                 and side-2 table offsets, first and end shared index, chunk-local
+                                 channel, n1, n2                                               */
 int nbs_plan_export(const nbs_plan* p, int what, void* dst);
 
 #ifdef __cplusplus

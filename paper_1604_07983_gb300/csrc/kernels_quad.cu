@@ -280,7 +280,169 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_quad(
   }
 }
 
+// ---- segment-driven form ----------------------------------------------------
+// The same lanes, steps and partial-sum slots, but each warp walks its range as
+// runs of one term (QuadSeg, plan.h) staged in shared memory once per CTA: the
+// term form is dispatched once per run, the step loop only advances two table
+// pointers, and the channel flush indexes alpha2 = a ^ d directly instead of
+// permuting the accumulator first (the reduction never mixes spins a, so both
+// orders give the same sums).
+
+template <int SHAPE, int I1, int I2>
+__device__ __forceinline__ void qseg_run(const QuadSeg& sg, int kq, const unsigned short* TAB,
+                                         const unsigned short* ZROW, const float2* S1a, const float2* S2a,
+                                         const float* sc, float (&acc)[32]) {
+  constexpr int NH1 = 1 << ((SHAPE & 1) + ((SHAPE >> 1) & 1));
+  constexpr int NH2 = 4 / NH1;
+  const int n1 = I1 ? 2 * I1 : sg.n1, n2 = I2 ? 2 * I2 : sg.n2;
+  const int r1 = NH1 * n1, r2 = NH2 * n2;  // entries per shared index
+  const unsigned short* p1 = TAB + sg.t1 + (sg.kbeg + kq) * r1;
+  const unsigned short* p2 = TAB + sg.t2 + (sg.kbeg + kq) * r2;
+#pragma unroll 1
+  for (int k0 = sg.kbeg; k0 < sg.kend; k0 += 8, p1 += 8 * r1, p2 += 8 * r2) {
+    const bool active = k0 + kq < sg.kend;  // the four lanes of a quad agree
+    quad_step<SHAPE, I1, I2>(n1, n2, active ? p1 : ZROW, active ? p2 : ZROW, S1a, S2a, sc, acc);
+  }
+}
+
+// reduce over the eight shared-index lanes, add into slot [alpha1][alpha2][s];
+// acc holds complex 4 d + s with alpha2 = a ^ d
+__device__ __forceinline__ void qseg_flush(float (&acc)[32], int lane, float2* slot) {
+  const int a = lane & 3, kq = lane >> 2;
+  quad_reduce<16>(acc, lane);  // lane keeps complex 2 kq, 2 kq + 1: d = kq >> 1, s = 2 (kq & 1) + {0, 1}
+  float2* o = slot + 16 * a + 4 * (a ^ (kq >> 1)) + 2 * (kq & 1);
+  o[0].x += acc[0];
+  o[0].y += acc[1];
+  o[1].x += acc[2];
+  o[1].y += acc[3];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
+    const float2* __restrict__ FB, int L, int nchunks, int qb, const QuadChunkHdr* __restrict__ chunks,
+    const QuadSeg* __restrict__ segs, const int* __restrict__ group_ch, const unsigned short* __restrict__ tab,
+    const float* __restrict__ codes, int max_slot, int max_tab, float2* __restrict__ Ft) {
+  constexpr int NT = NW * 32;
+  constexpr int slab = 2 * 2 * QUAD_ST;  // uint4 per buffer: two sides x cells x 32 bytes
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned short* TAB = reinterpret_cast<unsigned short*>(smem_raw);
+  unsigned short* ZROW = TAB + max_tab;  // max_tab % 8 == 0
+  uint4* SB = reinterpret_cast<uint4*>(smem_raw + (size_t)(max_tab + QUAD_ZROW) * 2);
+  float2* OUT = reinterpret_cast<float2*>(SB + 2 * slab);
+  float* SC = reinterpret_cast<float*>(OUT + max_slot * 64);
+  QuadSeg* SEG = reinterpret_cast<QuadSeg*>(SC + 64);
+  if (threadIdx.x < 64) {
+    const float m = codes[threadIdx.x >> 1];
+    SC[threadIdx.x] = (threadIdx.x & 1) ? -m : m;
+  }
+  for (int i = threadIdx.x; i < QUAD_ZROW; i += NT) ZROW[i] = (unsigned short)(31u << 11);
+  const long long V = (long long)L * L * L;
+  const int ci = blockIdx.x % nchunks;
+  const long long q_begin = (long long)(blockIdx.x / nchunks) * qb;
+  const long long q_end = min(V, q_begin + qb);
+  const QuadChunkHdr& ck = chunks[ci];
+  const int base1 = ck.base1, n1c = ck.ncell1, base2 = ck.base2, n2c = ck.ncell2;
+  const int seg0 = ck.seg_base[0], nseg = ck.seg_base[NW] - seg0;
+
+  auto issue_slabs = [&](long long q, uint4* S) {
+    const int qx = (int)(q % L), qy = (int)((q / L) % L), qz = (int)(q / ((long long)L * L));
+    const long long qm = (L - qx) % L + L * ((L - qy) % L + (long long)L * ((L - qz) % L));
+    for (int i = threadIdx.x; i < 2 * n1c; i += NT)
+      cp_async16q(S + i, reinterpret_cast<const char*>(FB + ((long long)(base1 + (i >> 1)) * V + q) * 4) + 16 * (i & 1));
+    uint4* S2 = S + 2 * QUAD_ST;
+    for (int i = threadIdx.x; i < 2 * n2c; i += NT)
+      cp_async16q(S2 + i, reinterpret_cast<const char*>(FB + ((long long)(base2 + (i >> 1)) * V + qm) * 4) + 16 * (i & 1));
+  };
+
+  for (int i = threadIdx.x; i < ck.tab_len / 8; i += NT) cp_async16q(TAB + 8 * i, tab + ck.tab_off + 8 * i);
+  for (int i = threadIdx.x; i < 2 * nseg; i += NT)
+    cp_async16q(reinterpret_cast<uint4*>(SEG) + i, reinterpret_cast<const uint4*>(segs + seg0) + i);
+  if (q_begin < q_end) issue_slabs(q_begin, SB);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (int i = threadIdx.x; i < ck.nslot * 64; i += NT) OUT[i] = make_float2(0.f, 0.f);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a = lane & 3, kq = lane >> 2;
+  const int s_begin = ck.seg_base[w] - seg0, s_end = ck.seg_base[w + 1] - seg0;
+  float2* const out_w = OUT + (ck.out_base[w] - ck.cfirst[w]) * 64;
+  for (long long q = q_begin; q < q_end; ++q) {
+    uint4* S = SB + ((q - q_begin) & 1) * slab;
+    if (q + 1 < q_end) issue_slabs(q + 1, SB + ((q + 1 - q_begin) & 1) * slab);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    const float2* S1a = reinterpret_cast<const float2*>(S) + a;
+    const float2* S2a = reinterpret_cast<const float2*>(S + 2 * QUAD_ST) + a;
+    float acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+    int cur = -1;
+    for (int si = s_begin; si < s_end; ++si) {
+      const QuadSeg sg = SEG[si];
+      if (sg.local != cur) {
+        if (cur >= 0) qseg_flush(acc, lane, out_w + cur * 64);
+        cur = sg.local;
+      }
+      switch (sg.form) {
+        case 4: qseg_run<0, 4, 1>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
+        case 5: qseg_run<1, 1, 1>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
+        case 6: qseg_run<2, 1, 1>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
+        case 7: qseg_run<3, 1, 4>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
+        case 0: qseg_run<0, 0, 0>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
+        case 1: qseg_run<1, 0, 0>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
+        case 2: qseg_run<2, 0, 0>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
+        default: qseg_run<3, 0, 0>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
+      }
+    }
+    if (cur >= 0) qseg_flush(acc, lane, out_w + cur * 64);
+    __syncthreads();
+    for (int i = threadIdx.x; i < ck.nch * 64; i += NT) {
+      const int c = i / 64, m = i % 64;
+      float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int ww = 0; ww < NW; ++ww) {  // fixed order
+        const int r = c - ck.cfirst[ww];
+        if (r >= 0 && r < ck.out_base[ww + 1] - ck.out_base[ww]) {
+          float2& v = OUT[(ck.out_base[ww] + r) * 64 + m];
+          sum.x += v.x;
+          sum.y += v.y;
+          v = make_float2(0.f, 0.f);
+        }
+      }
+      const int spin = (m & ~3) + 2 * (m & 1) + ((m >> 1) & 1);
+      Ft[((long long)group_ch[ck.ch_off + c] * 64 + spin) * V + q] = sum;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+size_t qseg_smem_bytes(int max_slot, int max_tab, int max_segs) {
+  return (size_t)(max_tab + QUAD_ZROW) * 2 + (size_t)2 * 2 * 2 * QUAD_ST * 16 + (size_t)max_slot * 64 * sizeof(float2) +
+         64 * sizeof(float) + (size_t)max_segs * sizeof(QuadSeg);
+}
+
+cudaError_t launch_contract_qseg(const float2* FB, int L, int nchunks, int qb, const void* chunks, const void* segs,
+                                 int max_segs, const int* group_ch, const unsigned short* tab, const float* codes,
+                                 int max_cells, int max_slot, int max_tab, int max_row, float2* Ft, cudaStream_t st) {
+  const long long V = (long long)L * L * L;
+  if (max_row > QUAD_ZROW || max_tab % 8 || max_cells > QUAD_ST || max_cells > 1024 || max_segs < 0)
+    return cudaErrorInvalidValue;
+  const size_t sm = qseg_smem_bytes(max_slot, max_tab, max_segs);
+  auto kern = k_contract_qseg<NBS_QUAD_WARPS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const long long nqb = (V + qb - 1) / qb;
+  if (nqb * nchunks > 2147483647LL) return cudaErrorInvalidValue;
+  kern<<<(unsigned)(nqb * nchunks), NBS_QUAD_WARPS * 32, sm, st>>>(FB, L, nchunks, qb, (const QuadChunkHdr*)chunks,
+                                                                   (const QuadSeg*)segs, group_ch, tab, codes,
+                                                                   max_slot, max_tab, Ft);
+  return cudaGetLastError();
+}
 
 size_t quad_smem_bytes(int max_slot, int max_tab) {
   return (size_t)(max_tab + QUAD_ZROW) * 2 + (size_t)2 * 2 * 2 * QUAD_ST * 16 + (size_t)max_slot * 64 * sizeof(float2) +

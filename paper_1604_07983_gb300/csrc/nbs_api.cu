@@ -87,7 +87,7 @@ struct nbs_ctx {
   int plan_gen = 0;
   DevBuf d_terms, d_chtb, d_chnl, d_e1, d_e2, d_cells, d_groups, d_gch, d_items;
   int slab_st1 = 0, slab_st2 = 0, slab_nch = 0;
-  DevBuf d_chunks, d_qchunks, d_ctab, d_citems, d_ctoff, d_codes;
+  DevBuf d_chunks, d_qchunks, d_qsegs, d_ctab, d_citems, d_ctoff, d_codes;
   int chunk_st1 = 0, chunk_st2 = 0, chunk_slot = 0, chunk_tab = 0, chunk_row = 0, quad_slot = 0;
   int chunk_qb = 32;
   int fft_block = 128;  // NBS_PARAM_FFT_BLOCK
@@ -221,6 +221,8 @@ int upload_tables(nbs_ctx* h) {
     if ((rc = ensure(h, h->d_chunks, std::max<size_t>(P.chunks.size(), 1) * sizeof(ChunkHdr), "chunks"))) return rc;
     if ((rc = ensure(h, h->d_qchunks, std::max<size_t>(P.quad_chunks.size(), 1) * sizeof(QuadChunkHdr), "quad chunks")))
       return rc;
+    if ((rc = ensure(h, h->d_qsegs, std::max<size_t>(P.quad_segs.size(), 1) * sizeof(QuadSeg), "quad segments")))
+      return rc;
     if ((rc = ensure(h, h->d_ctab, std::max<size_t>(P.chunk_tab.size(), 8) * 2, "chunk tables"))) return rc;
     if ((rc = ensure(h, h->d_citems, std::max<size_t>(P.chunk_items.size(), 1) * sizeof(int), "chunk items"))) return rc;
     if ((rc = ensure(h, h->d_ctoff, std::max<size_t>(P.term_tab_off.size(), 1) * sizeof(int), "table offsets"))) return rc;
@@ -229,6 +231,9 @@ int upload_tables(nbs_ctx* h) {
     CK(cudaMemcpyAsync(h->d_qchunks.p, P.quad_chunks.data(), P.quad_chunks.size() * sizeof(QuadChunkHdr),
                        cudaMemcpyHostToDevice, h->st),
        "upload quad chunks");
+    CK(cudaMemcpyAsync(h->d_qsegs.p, P.quad_segs.data(), P.quad_segs.size() * sizeof(QuadSeg), cudaMemcpyHostToDevice,
+                       h->st),
+       "upload quad segments");
     CK(cudaMemcpyAsync(h->d_ctab.p, P.chunk_tab.data(), P.chunk_tab.size() * 2, cudaMemcpyHostToDevice, h->st), "upload chunk tables");
     CK(cudaMemcpyAsync(h->d_citems.p, P.chunk_items.data(), P.chunk_items.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload chunk items");
     CK(cudaMemcpyAsync(h->d_ctoff.p, P.term_tab_off.data(), P.term_tab_off.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload table offsets");
@@ -378,7 +383,8 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
     cudaEvent_t e3 = stage_begin(h);
     // default in FP32: the quad-lane chunk kernel when the tables fit; FP64: the thread-per-momentum kernel
     const bool f32_chunks = sizeof(T) == 4 && h->plan.chunks_ok;
-    const bool use_quad = f32_chunks && (h->contract_cfg == 0 || h->contract_cfg == 5);
+    const bool use_qseg = f32_chunks && h->contract_cfg == 0;
+    const bool use_quad = f32_chunks && h->contract_cfg == 5;
     if (h->mode == NBS_BF16X3 && h->plan.chunks_ok && h->contract_cfg != 2) {
       CK(launch_contract_tcq((const float2*)h->FB.p, h->L, (int)h->plan.quad_chunks.size(), h->chunk_qb,
                              h->d_qchunks.p, (const int*)h->d_gch.p, (const int*)h->d_citems.p,
@@ -394,6 +400,13 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
                             (const int*)h->d_ctoff.p, (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
                             h->chunk_st1, h->chunk_st2, h->chunk_slot, h->chunk_tab, (float2*)h->Ft.p, h->st),
          "contraction (tensor cores)");
+    } else if (use_qseg) {
+      CK(launch_contract_qseg((const float2*)h->FB.p, h->L, (int)h->plan.quad_chunks.size(), h->chunk_qb,
+                              h->d_qchunks.p, h->d_qsegs.p, h->plan.max_quad_segs, (const int*)h->d_gch.p,
+                              (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
+                              std::max(h->chunk_st1, h->chunk_st2), h->quad_slot, h->chunk_tab, h->chunk_row,
+                              (float2*)h->Ft.p, h->st),
+         "contraction");
     } else if (use_quad) {
       CK(launch_contract_quad((const float2*)h->FB.p, h->L, (int)h->plan.quad_chunks.size(), h->chunk_qb,
                               h->d_qchunks.p, (const int*)h->d_gch.p, (const int*)h->d_citems.p,
@@ -548,7 +561,7 @@ int nbs_destroy(nbs_ctx* h) {
   if (h->cst) cudaStreamSynchronize(h->cst);
   DevBuf* bufs[] = {&h->props, &h->propsT, &h->FB, &h->Ft, &h->zm, &h->small, &h->stage[0], &h->stage[1],
                     &h->d_terms, &h->d_chtb, &h->d_chnl, &h->d_e1, &h->d_e2, &h->d_cells, &h->d_groups,
-                    &h->d_gch, &h->d_items, &h->d_chunks, &h->d_qchunks, &h->d_ctab, &h->d_citems, &h->d_ctoff,
+                    &h->d_gch, &h->d_items, &h->d_chunks, &h->d_qchunks, &h->d_qsegs, &h->d_ctab, &h->d_citems, &h->d_ctoff,
                     &h->d_codes};
   for (DevBuf* b : bufs) dev_free(b->p, h->free_fn, h->free_user);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
@@ -922,6 +935,10 @@ int nbs_plan_export(const nbs_plan* p, int what, void* dst) {
     case NBS_PX_QUADCHUNKS:
       static_assert(sizeof(QuadChunkHdr) == 128 * sizeof(int), "quad chunk header layout");
       if (P.chunks_ok) std::memcpy(I, P.quad_chunks.data(), P.quad_chunks.size() * sizeof(QuadChunkHdr));
+      return NBS_OK;
+    case NBS_PX_QUADSEGS:
+      static_assert(sizeof(QuadSeg) == 8 * sizeof(int), "quad segment layout");
+      if (P.chunks_ok) std::memcpy(I, P.quad_segs.data(), P.quad_segs.size() * sizeof(QuadSeg));
       return NBS_OK;
     default: return fail(nullptr, NBS_EINVAL, "unknown export");
   }

@@ -261,6 +261,99 @@ const std::vector<ChannelDef>& channel_table() {
 
 namespace {
 
+// Reorder one term's compressed gather lists (entries [xi][i][held], side 1
+// and side 2) for the shared-memory banks of the quad-lane kernels.  There a
+// half-warp gathers, for one entry slot (i, held), the cells of four
+// consecutive shared indices, each a 32-byte run (four spins) of the slab: the
+// four cells take one pass of the banks when their cell indices differ mod 4
+// (or coincide), else one pass per cell of the most used residue.  Any order
+// of the shared indices (the same on both sides, they are paired) and of the
+// entries of each sum gives the same product, and a zero-coefficient entry
+// may name any cell: so, greedily, each group of four indices is filled with
+// the candidate (among the next 48 unused) that adds the fewest passes, its
+// entries put into the slots where they add the fewest, and its zero entries
+// pointed at a cell the slot already reads.
+void order_for_banks(int K, int n1, int nh1, int n2, int nh2, std::vector<unsigned short>& e1,
+                     std::vector<unsigned short>& e2) {
+  const int n[2] = {n1, n2}, nh[2] = {nh1, nh2}, r1 = n1 * nh1, r2 = n2 * nh2;
+  if (K < 2 || (int)e1.size() != K * r1 || (int)e2.size() != K * r2) return;
+  std::vector<unsigned short>* src[2] = {&e1, &e2};
+  std::vector<unsigned short> out[2] = {std::vector<unsigned short>(e1.size()), std::vector<unsigned short>(e2.size())};
+  struct Slot { int cell[4]; int nc; };
+  std::vector<Slot> st(r1 + r2);
+  auto slot_of = [&](int side, int i, int h) { return side == 0 ? i * nh1 + h : r1 + i * nh2 + h; };
+  auto increase = [&](const Slot& s, int c) {
+    int cnt[4] = {0, 0, 0, 0}, mx = 0;
+    for (int j = 0; j < s.nc; ++j) {
+      if (s.cell[j] == c) return 0;
+      mx = std::max(mx, ++cnt[s.cell[j] & 3]);
+    }
+    return std::max(mx, cnt[c & 3] + 1) - mx;
+  };
+  auto add = [&](Slot& s, int c) {
+    for (int j = 0; j < s.nc; ++j)
+      if (s.cell[j] == c) return;
+    if (s.nc < 4) s.cell[s.nc++] = c;
+  };
+  // cost of index k in the current group; with pos >= 0 also write it there
+  auto place = [&](int k, int pos) {
+    int tot = 0;
+    for (int side = 0; side < 2; ++side) {
+      const int nn = n[side], hh = nh[side];
+      for (int h = 0; h < hh; ++h) {
+        int slot_used[64] = {0};
+        int assign[64];
+        for (int pass = 0; pass < 2; ++pass)  // real entries first, then zeros
+          for (int i = 0; i < nn; ++i) {
+            const unsigned short e = (*src[side])[(k * nn + i) * hh + h];
+            const bool zero = (e >> 11) == 31;
+            if (zero != (pass == 1)) continue;
+            int best = -1, best_inc = 1 << 30;
+            for (int sl = 0; sl < nn; ++sl) {
+              if (slot_used[sl]) continue;
+              const int inc = zero ? 0 : increase(st[slot_of(side, sl, h)], e & 1023);
+              if (inc < best_inc) { best_inc = inc; best = sl; }
+            }
+            slot_used[best] = 1;
+            assign[i] = best;
+            tot += best_inc;
+          }
+        if (pos < 0) continue;
+        for (int i = 0; i < nn; ++i) {
+          unsigned short e = (*src[side])[(k * nn + i) * hh + h];
+          Slot& s = st[slot_of(side, assign[i], h)];
+          if ((e >> 11) == 31 && s.nc > 0) e = (unsigned short)((e & ~1023u) | (unsigned)s.cell[0]);
+          add(s, e & 1023);
+          out[side][(pos * nn + assign[i]) * hh + h] = e;
+        }
+      }
+    }
+    return tot;
+  };
+  if (n1 > 64 || n2 > 64) return;
+  std::vector<char> used(K, 0);
+  int seed = 0, pos = 0;
+  while (pos < K) {
+    for (Slot& s : st) s.nc = 0;
+    while (used[seed]) ++seed;
+    place(seed, pos++);
+    used[seed] = 1;
+    for (int gi = 1; gi < 4 && pos < K; ++gi) {
+      int best = -1, best_cost = 1 << 30;
+      for (int k = seed, seen = 0; k < K && seen < 48; ++k) {
+        if (used[k]) continue;
+        ++seen;
+        const int c = place(k, -1);
+        if (c < best_cost) { best_cost = c; best = k; }
+      }
+      place(best, pos++);
+      used[best] = 1;
+    }
+  }
+  e1.swap(out[0]);
+  e2.swap(out[1]);
+}
+
 // Split every slab group into chunks of whole channels whose compressed
 // tables fit NBS_CHUNK_ENTRIES, and balance each chunk's items over warps.
 void build_chunks(Plan& plan) {
@@ -268,6 +361,8 @@ void build_chunks(Plan& plan) {
   plan.chunk_tab.clear();
   plan.chunk_items.clear();
   plan.quad_chunks.clear();
+  plan.quad_segs.clear();
+  plan.max_quad_segs = 0;
   plan.term_tab_off.assign(2 * plan.terms.size(), 0);
   plan.coef_codes.clear();
   plan.chunks_ok = false;
@@ -312,13 +407,13 @@ void build_chunks(Plan& plan) {
         for (int t = plan.ch_term_begin[ci]; t < plan.ch_term_begin[ci + 1]; ++t) {
           const TermHdr& th = plan.terms[t];
           const int nh1 = 1 << ((th.shape & 1) + (th.shape >> 1 & 1)), nh2 = 4 / nh1;
+          std::vector<unsigned short> ents[2];
           for (int side = 0; side < 2; ++side) {
             const int n = side == 0 ? th.K * nh1 * th.n1 : th.K * nh2 * th.n2;
             const int off = side == 0 ? th.off1 : th.off2;
             const int base = side == 0 ? g.base1 : g.base2;
             const auto& cells = side == 0 ? plan.ent1_cell : plan.ent2_cell;
             const auto& coefs = side == 0 ? plan.ent1_coef : plan.ent2_coef;
-            plan.term_tab_off[2 * t + side] = (int)plan.chunk_tab.size() - ck.tab_off;
             for (int i = 0; i < n; ++i) {
               const int cell = cells[off + i] - base;
               const double cf = coefs[off + i];
@@ -328,8 +423,13 @@ void build_chunks(Plan& plan) {
                 code = code_of(cf);
                 if (code >= 31) return;
               }
-              plan.chunk_tab.push_back((unsigned short)(cell | ((cf < 0) << 10) | (code << 11)));
+              ents[side].push_back((unsigned short)(cell | ((cf < 0) << 10) | (code << 11)));
             }
+          }
+          order_for_banks(th.K, th.n1, nh1, th.n2, nh2, ents[0], ents[1]);
+          for (int side = 0; side < 2; ++side) {
+            plan.term_tab_off[2 * t + side] = (int)plan.chunk_tab.size() - ck.tab_off;
+            plan.chunk_tab.insert(plan.chunk_tab.end(), ents[side].begin(), ents[side].end());
             while ((plan.chunk_tab.size() - ck.tab_off) % 8) plan.chunk_tab.push_back((unsigned short)(0x1F << 11));
           }
           for (int k0 = 0; k0 < th.K; k0 += 32) {
@@ -422,6 +522,40 @@ void build_chunks(Plan& plan) {
           qk.out_base[ww + 1] = qk.out_base[ww] + n;
         }
         qk.nslot = qk.out_base[NBS_QUAD_WARPS];
+        // the warp ranges as runs of one term: [kbeg, kend) of consecutive steps
+        const int seg0 = (int)plan.quad_segs.size();
+        for (int ww = 0; ww < NBS_QUAD_WARPS; ++ww) {
+          qk.seg_base[ww] = (int)plan.quad_segs.size();
+          for (int g = cut[ww]; g < cut[ww + 1]; ++g) {
+            int item, kb;
+            locate(g, item, kb);
+            const int t = its[item].first;
+            const TermHdr& th = plan.terms[t];
+            const int k = its[item].second + 8 * kb;
+            const int kend = std::min(th.K, k + 8);
+            QuadSeg* last = plan.quad_segs.size() > (size_t)qk.seg_base[ww] ? &plan.quad_segs.back() : nullptr;
+            if (last && last->t1 == plan.term_tab_off[2 * t] && last->kend == k && last->local == th.pad - c &&
+                last->t2 == plan.term_tab_off[2 * t + 1]) {
+              last->kend = kend;
+              continue;
+            }
+            QuadSeg sg;
+            sg.form = th.shape;
+            if ((th.shape == 0 && th.n1 == 8 && th.n2 == 2) || (th.shape == 1 && th.n1 == 2 && th.n2 == 2) ||
+                (th.shape == 2 && th.n1 == 2 && th.n2 == 2) || (th.shape == 3 && th.n1 == 2 && th.n2 == 8))
+              sg.form += 4;
+            sg.t1 = plan.term_tab_off[2 * t];
+            sg.t2 = plan.term_tab_off[2 * t + 1];
+            sg.kbeg = k;
+            sg.kend = kend;
+            sg.local = th.pad - c;
+            sg.n1 = th.n1;
+            sg.n2 = th.n2;
+            plan.quad_segs.push_back(sg);
+          }
+        }
+        qk.seg_base[NBS_QUAD_WARPS] = (int)plan.quad_segs.size();
+        plan.max_quad_segs = std::max(plan.max_quad_segs, (int)plan.quad_segs.size() - seg0);
       }
       plan.quad_chunks.push_back(qk);
       for (auto& it : its) {

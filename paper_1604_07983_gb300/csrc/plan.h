@@ -99,8 +99,18 @@ struct QuadChunkHdr {
   int out_base[NBS_QUAD_WARPS + 1];
   int cfirst[NBS_QUAD_WARPS];
   int ch_local0;
-  int pad[20];  // 128 ints
+  // the same ranges as runs of one term each: warp w's segments are
+  // Plan::quad_segs[seg_base[w] .. seg_base[w + 1])
+  int seg_base[NBS_QUAD_WARPS + 1];
+  int pad[3];  // 128 ints
 };
+
+// One run of consecutive 8-index steps of one term inside a warp's range:
+// shared indices [kbeg, kend) (kbeg a multiple of 8, kend <= K), table offsets
+// of the two gather lists inside the chunk table, the chunk-local channel and
+// the term form (0..3: shape with run-time lengths; 4..7: the straight-line
+// forms (shape 0, n 8/2), (1, 2/2), (2, 2/2), (3, 2/8)).
+struct QuadSeg { int form, t1, t2, kbeg, kend, local, n1, n2; };
 
 struct Plan {
   std::vector<int> channels;                  // built-in ids, in request order
@@ -123,6 +133,8 @@ struct Plan {
   std::vector<int> term_tab_off;              // per term: side-1, side-2 offsets inside its chunk's table
   std::vector<double> coef_codes;             // |coefficient| of each code
   std::vector<QuadChunkHdr> quad_chunks;      // one per chunk (valid when chunks_ok)
+  std::vector<QuadSeg> quad_segs;             // per-warp term runs of every quad chunk
+  int max_quad_segs = 0;                      // most segments of one chunk
   // flops of the contraction per q (complex multiply-adds), for rooflines
   double cmac_per_q = 0, gathers_per_q = 0;
 };

@@ -133,12 +133,14 @@ def test_contraction_variants_all_channels(nbs, cfg):
 def test_chunk_kernel_forms_agree_bitwise(nbs):
     """The two forms of the chunk contraction (configs 2, 3) do the same FP32 operations in the same
     order: identical results, here with a momentum block (24) that leaves a ragged last block at 4^3.
-    The quad-lane form (config 5, the default) sums in another order: equal to FP32 rounding."""
+    The quad-lane form sums in another order: equal to FP32 rounding.  Its segment-driven kernel
+    (config 0, the default) and its item-driven kernel (config 5) take the same steps in the same order:
+    identical results."""
     L = 4
     props = seeded(1723, L, 1, decay=0.5)
     ids = list(range(nbs.channel_count()))
     out = []
-    for cfg in (2, 3, 5):
+    for cfg in (2, 3, 5, 0):
         with nbs.Context(L, 1, precision=nbs.NBS_FP32) as ctx:
             ctx.set_param(ctx.PARAM_CONTRACT_CFG, cfg)
             ctx.set_param(ctx.PARAM_CHUNK_QBLOCK, 24)
@@ -151,6 +153,7 @@ def test_chunk_kernel_forms_agree_bitwise(nbs):
     assert np.array_equal(out[0], out[1])
     for c in ids:
         assert rel(out[2][c], out[0][c]) < 1e-6, c
+    assert np.array_equal(out[2], out[3])
 
 
 @pytest.mark.parametrize("cfg", [0, 2])

@@ -131,8 +131,10 @@ def test_slab_work_split_covers_every_term_once(lib, ids):
 @pytest.mark.parametrize("ids", [list(range(52)), [0], [24, 25, 51]])
 def test_chunk_tables_decode_to_the_gather_tables(lib, ids):
     """The 16-bit shared-memory tables of the chunk contraction decode to the
-    full gather tables, every read stays in its slab, every shared index of
-    every term is visited once, and the shared memory fits a GB300 block."""
+    full gather tables up to the order of the shared indices (the same on both
+    sides) and of the entries of each sum, every read stays in its slab, every
+    shared index of every term is visited once, and the shared memory fits a
+    GB300 block."""
     tb = nbs.plan_tables(ids)
     chunks, ctab, items, toff, codes = tb["chunks"], tb["chunk_tab"], tb["chunk_items"], tb["term_tab_off"], tb["codes"]
     terms = tb["terms"]
@@ -156,18 +158,23 @@ def test_chunk_tables_decode_to_the_gather_tables(lib, ids):
             ch, K, shape, nn1, nn2, off1, off2, gl = terms[t]
             nh1 = 1 << ((shape & 1) + ((shape >> 1) & 1))
             nh2 = 4 // nh1
-            for side, (n, off, base, ncell) in enumerate([(K * nh1 * nn1, off1, base1, n1), (K * nh2 * nn2, off2, base2, n2)]):
+            got_keys, want_keys = [[] for _ in range(K)], [[] for _ in range(K)]
+            for side, (nn, nh, off, base, ncell) in enumerate([(nn1, nh1, off1, base1, n1), (nn2, nh2, off2, base2, n2)]):
+                n = K * nh * nn
                 o = toff[t, side]
                 assert o % 8 == 0 and o + n <= tab_len
                 e = ctab[tab_off + o: tab_off + o + n].astype(np.int64)
-                cell = (e & 1023) + base
-                coef = codes[e >> 11] * np.where(e & 1024, -1.0, 1.0)
-                want_cell = tb["ent%d_cell" % (side + 1)][off: off + n]
-                want_coef = tb["ent%d_coef" % (side + 1)][off: off + n]
                 assert ((e & 1023) < ncell).all()
-                nz = want_coef != 0
-                assert (cell[nz] == want_cell[nz]).all()
-                assert np.allclose(coef, want_coef, rtol=1e-6, atol=0)
+                cell = ((e & 1023) + base).reshape(K, nn, nh)
+                coef = (codes[e >> 11] * np.where(e & 1024, -1.0, 1.0)).reshape(K, nn, nh)
+                want_cell = tb["ent%d_cell" % (side + 1)][off: off + n].reshape(K, nn, nh)
+                want_coef = tb["ent%d_coef" % (side + 1)][off: off + n].reshape(K, nn, nh)
+                for k in range(K):
+                    for h in range(nh):
+                        for keys, c, f in ((got_keys, cell, coef), (want_keys, want_cell, want_coef)):
+                            keys[k].append(tuple(sorted((int(c[k, i, h]), round(float(f[k, i, h]), 9))
+                                                        for i in range(nn) if f[k, i, h] != 0)))
+            assert sorted(map(tuple, got_keys)) == sorted(map(tuple, want_keys))
     assert (seen == terms[:, 1]).all()
 
 
@@ -257,3 +264,38 @@ def test_quad_warp_ranges_cover_every_step_once(lib):
                         seen[it][st] += 1
         assert all(x == 1 for row in seen for x in row)
         assert qk[9] == out_base[16]
+
+
+def test_quad_segments_replay_the_warp_ranges(lib):
+    """The segment-driven quad kernel walks each warp's range as runs of one term: expanded into
+    8-index steps, the runs give exactly the steps of the item-based ranges, in the same order, with
+    the term's form, lengths, table offsets and chunk-local channel."""
+    tb = nbs.plan_tables(list(range(52)))
+    T, items, toff, segs = tb["terms"], tb["chunk_items"], tb["term_tab_off"], tb["quad_segs"]
+    fixed = {(0, 8, 2): 4, (1, 2, 2): 5, (2, 2, 2): 6, (3, 2, 8): 7}
+    assert len(segs) == tb["quad_chunks"][-1][108 + 16]
+    for ck, qk in zip(tb["chunks"], tb["quad_chunks"]):
+        item_off, nit = ck[8], ck[10 + 8]
+        its = [tuple(x) for x in items[item_off:item_off + nit]]
+        nks = [(min(32, T[t][1] - k0) + 7) // 8 for t, k0 in its]
+        wi0, kb0, wi1, kb1 = qk[10:26], qk[26:42], qk[42:58], qk[58:74]
+        ch_local0, seg_base = qk[107], qk[108:125]
+        by_off = {(toff[t][0], toff[t][1]): t for t, _ in its}
+        for w in range(16):
+            want = []
+            if wi0[w] < wi1[w] or (wi0[w] == wi1[w] and kb0[w] < kb1[w]):
+                for it in range(wi0[w], wi1[w] + 1):
+                    t, k0 = its[it]
+                    for st in range(kb0[w] if it == wi0[w] else 0, kb1[w] if it == wi1[w] else 4):
+                        if st < nks[it]:
+                            want.append((t, k0 + 8 * st))
+            got = []
+            for form, t1, t2, kbeg, kend, local, n1, n2 in segs[seg_base[w]:seg_base[w + 1]]:
+                t = by_off[(t1, t2)]
+                ch, K, shape = T[t][0], T[t][1], T[t][2]
+                assert (n1, n2) == (T[t][3], T[t][4])
+                assert form == fixed.get((shape, n1, n2), shape)
+                assert local == T[t][7] - ch_local0
+                assert kbeg % 8 == 0 and kbeg < kend <= K
+                got += [(t, k) for k in range(kbeg, kend, 8)]
+            assert got == want, w
