@@ -36,7 +36,7 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes per momentum of the FP32 contraction kernels, from one ncu capture of
 # `python bench.py --L 16 --T 2 --steps 1 --warmup 1 --e2e-steps 1 --no-cpu-baseline`
 # (dram__bytes_read.sum + dram__bytes_write.sum / 4096 momenta; profiles/k_contract_16cube_fp32.md)
-DRAM_BYTES_PER_Q = {"k_contract_quad": 1.206875e9 / 4096}
+DRAM_BYTES_PER_Q = {}
 
 
 def parse():
@@ -386,7 +386,7 @@ def run_ours(args, rank, world, local_rank):
             peak_src = "nominal GB300 FP64 1.25 TFLOP/s"
         ach = flops_per_launch / (per_launch_ms["contract"] / 1e3) / 1e12
         cfg = tuned["cfg"] if tuned else args.contract_cfg
-        kname = {0: "k_contract_qseg", 5: "k_contract_quad", 2: "k_contract_chunk", 3: "k_contract_chunk2",
+        kname = {0: "k_contract_qseg", 2: "k_contract_chunk", 3: "k_contract_chunk2",
                  1: "k_contract_slab"}.get(cfg, "k_contract") if prec == P.NBS_FP32 else \
             ("k_contract_slab" if cfg == 1 else "k_contract")
         traffic = None

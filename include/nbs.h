@@ -162,9 +162,10 @@ int nbs_zero_momentum(nbs_ctx* h, double* out);
 /* Launch-shape parameters (for tuning; results agree to rounding).
  * NBS_PARAM_CONTRACT_CFG selects the contraction kernel:
  *   0 = default: in FP32, when the channel tables fit its shared memory, the
- *       quad-lane chunk kernel driven by per-warp term runs (the steps of 5,
- *       same order, same results; the term form is dispatched once per run);
- *       in FP64 the thread-per-momentum kernel (A = 2, W = 1);
+ *       quad-lane chunk kernel (persistent blocks of 16 warps, four lanes per
+ *       shared index, one sink spin each; each warp walks its share of the
+ *       steps as runs of one table run); in BF16X3 its tensor-core form; in
+ *       FP64 the thread-per-momentum kernel (A = 2, W = 1);
  *   1 = the momentum-slab kernel (one block per momentum and channel group,
  *       stored blocks staged in shared memory);
  *   2 = the chunk kernel (FP32; persistent blocks that keep a chunk of
@@ -173,8 +174,6 @@ int nbs_zero_momentum(nbs_ctx* h, double* out);
  *       else the default;
  *   3 = the chunk kernel's second form (FP32; same work split, cheaper inner
  *       loops: signed coefficient table, no divergence), else the default;
- *   5 = the quad-lane chunk kernel (FP32; four lanes per shared index, one
- *       sink spin each, 16 warps per block; walks work items), else the default;
  *   A*10 + W = the thread-per-momentum kernel with A sink spins alpha1 per
  *       thread (1, 2 or 4) and W warps per block (1, 2 or 4).
  * In NBS_BF16X3 mode the tensor-core kernels run: the quad-lane form
@@ -282,17 +281,16 @@ int nbs_plan_sizes(const nbs_plan* p, long long* sizes);
 #define NBS_PX_CHUNKITEMS 15  /* int32 [nchunkitems][2]: term, first shared index            */
 #define NBS_PX_TERMTABOFF 16  /* int32 [nterms][2]: side-1, side-2 offset in the chunk table */
 #define NBS_PX_CODES     17   /* double [32]: |coefficient| of each code (code 31 = 0)       */
-#define NBS_PX_QUADCHUNKS 18  /* int32 [nchunks][128]: the chunks split over the 16 warps of the
+#define NBS_PX_QUADCHUNKS 18  /* int32 [nchunks][64]: the chunks split over the 16 warps of the
                                  quad-lane kernels: base1, ncell1, base2, ncell2, ch_off, nch,
-                                 tab_off, tab_len, item_off, nslot, wi0[16], kb0[16], wi1[16],
-                                 kb1[16] (warp w: 8-index steps kb0..kb1 of chunk items wi0..wi1),
-                                 out_base[17], cfirst[16], ch_local0, seg_base[17] (warp w's
-                                 term runs are quad segments seg_base[w] .. seg_base[w+1]),
-                                 padding                                                      */
+                                 tab_off, tab_len, nslot, ch_local0, out_base[17], cfirst[16],
+                                 seg_base[17] (warp w walks the quad segments seg_base[w] ..
+                                 seg_base[w+1]), padding                                      */
 #define NBS_PX_QUADSEGS  19   /* int32 [quad_chunks[nchunks-1].seg_base[16]][8]: per-warp runs of
-                                 one term: form (0..3 shape, 4..7 the fixed-length forms), side-1
-                                 and side-2 table offsets, first and end shared index, chunk-local
-                                 channel, n1, n2                                               */
+                                 steps of one table run (a channel's terms of one fixed form,
+                                 back to back, or one term): form (0..3 shape, 4..7 the fixed
+                                 forms), side-1 and side-2 table offsets, first and end shared
+                                 index, chunk-local channel, n1, n2                            */
 int nbs_plan_export(const nbs_plan* p, int what, void* dst);
 
 #ifdef __cplusplus

@@ -21,7 +21,7 @@ CACHE = os.path.join(os.path.expanduser("~"), ".cache", "nbs_gb300", "autotune.j
 
 #: (contraction config, momentum block) candidates per precision mode
 CANDIDATES = {
-    NBS_FP32: [(0, 32), (0, 64), (5, 32), (2, 32), (3, 32), (0, 16), (42, 0), (22, 0), (1, 0)],
+    NBS_FP32: [(0, 32), (0, 64), (2, 32), (3, 32), (0, 16), (42, 0), (22, 0), (1, 0)],
     NBS_BF16X3: [(0, 16), (0, 32), (0, 64), (2, 32)],
     NBS_FP64: [(21, 0), (12, 0), (22, 0), (11, 0), (1, 0)],
 }

@@ -105,25 +105,18 @@ cudaError_t launch_contract_chunk2(const float2* FB, int L, int nchunks, int qb,
                                    const int* group_ch, const int* items, const DevTerm* terms, const int* tab_off,
                                    const unsigned short* tab, const float* codes, int st1, int st2, int max_slot,
                                    int max_tab, int max_row, float2* Ft, cudaStream_t st);
-// quad-lane chunk contraction (FP32): chunks points to QuadChunkHdr[nchunks]
-// (plan.h); max_cells = the largest stored type's cell count (<= 944)
-size_t quad_smem_bytes(int max_slot, int max_tab);
-cudaError_t launch_contract_quad(const float2* FB, int L, int nchunks, int qb, const void* chunks, const int* group_ch,
-                                 const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
-                                 const float* codes, int max_cells, int max_slot, int max_tab, int max_row, float2* Ft,
-                                 cudaStream_t st);
-// the same product driven by per-warp term runs (segs: QuadSeg[], plan.h):
-// dispatch on the term form once per run instead of once per step
+// quad-lane chunk contraction (FP32): chunks points to QuadChunkHdr[nchunks],
+// segs to the per-warp runs QuadSeg[] (plan.h), max_segs = the most runs of one
+// chunk; max_cells = the largest stored type's cell count (<= 944)
 size_t qseg_smem_bytes(int max_slot, int max_tab, int max_segs);
 cudaError_t launch_contract_qseg(const float2* FB, int L, int nchunks, int qb, const void* chunks, const void* segs,
                                  int max_segs, const int* group_ch, const unsigned short* tab, const float* codes,
                                  int max_cells, int max_slot, int max_tab, int max_row, float2* Ft, cudaStream_t st);
-// quad-lane tensor-core contraction (split-BF16 x 3): same arguments as launch_contract_quad
-size_t tcq_smem_bytes(int max_slot, int max_tab);
-cudaError_t launch_contract_tcq(const float2* FB, int L, int nchunks, int qb, const void* chunks, const int* group_ch,
-                                const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
-                                const float* codes, int max_cells, int max_slot, int max_tab, int max_row, float2* Ft,
-                                cudaStream_t st);
+// quad-lane tensor-core contraction (split-BF16 x 3): same arguments
+size_t tcq_smem_bytes(int max_slot, int max_tab, int max_segs);
+cudaError_t launch_contract_tcq(const float2* FB, int L, int nchunks, int qb, const void* chunks, const void* segs,
+                                int max_segs, const int* group_ch, const unsigned short* tab, const float* codes,
+                                int max_cells, int max_slot, int max_tab, int max_row, float2* Ft, cudaStream_t st);
 cudaError_t launch_contract_tc(const float2* FB, int L, int nchunks, int qb, const void* chunks, const int* group_ch,
                                const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
                                const float* codes, int st1, int st2, int max_slot, int max_tab, float2* Ft,

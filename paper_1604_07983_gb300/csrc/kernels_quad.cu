@@ -1,19 +1,21 @@
 // kernels_quad.cu -- the effective-block product of Eq. (4.3), FP32, with four
-// lanes per shared index (the quad-lane form of the chunk contraction).
+// lanes per shared index (the quad-lane contraction).
 //
-// Work split as in the chunk contraction (kernels_contract.cu): a CTA keeps one
-// chunk of channels' compressed gather tables in shared memory and sweeps a
-// block of momenta, staging the two momentum slabs of each q (B1's stored type
-// at q, B2's at -q) with cp.async into a double buffer.  Inside a warp, lane
-// 4 kq + a owns shared index k0 + kq of the current 8-index step and spin a:
-// it builds E1[alpha1 = a][h1] and E2[alpha2 = a][h2] (one 8-byte load and two
-// FMAs per gather entry), takes the other three alpha2 rows of E2 from the
-// lanes of its quad by warp shuffles, and accumulates its 16 complex products
-// F[alpha1 = a][alpha2][alpha3 alpha4] += E1 E2 in 32 registers.  The small
-// accumulator keeps a thread under 128 registers, so one CTA of 16 warps fits
-// an SM.  When a warp moves to another channel it sums its partial products
-// over the eight shared-index lanes and adds them to the channel's slot in
-// shared memory; the slots of all warps are added in a fixed order.
+// A CTA of 16 warps keeps one chunk of channels' compressed gather tables in
+// shared memory and sweeps a block of momenta, staging the two momentum slabs
+// of each q (B1's stored type at q, B2's at -q) with cp.async into a double
+// buffer.  Inside a warp, lane 4 kq + a owns shared index k0 + kq of the
+// current 8-index step and spin a: it builds E1[alpha1 = a][h1] and
+// E2[alpha2 = a][h2] (one 8-byte load and two FMAs per gather entry), takes
+// the other three alpha2 rows of E2 from the lanes of its quad by warp
+// shuffles, and accumulates its 16 complex products F[alpha1 = a][alpha2]
+// [alpha3 alpha4] += E1 E2 in 32 registers.  The small accumulator keeps a
+// thread under 128 registers, so one CTA of 16 warps fits an SM.  Each warp
+// walks its range of steps as runs of one table run (QuadSeg, plan.h), staged
+// in shared memory once per CTA, so the term form is dispatched once per run;
+// when a warp moves to another channel it sums its partial products over the
+// eight shared-index lanes and adds them to the channel's slot in shared
+// memory; the slots of all warps are added in a fixed order.
 #include "common.cuh"
 #include "plan.h"
 
@@ -131,162 +133,9 @@ __device__ __forceinline__ void quad_reduce(float (&acc)[32], int lane) {
   }
 }
 
-// lane-relative alpha2 (d = alpha2 ^ a) back to alpha2 order, then the reduce
-// and the add into the channel slot [alpha1][alpha2][s]
-__device__ __forceinline__ void quad_flush(float (&acc)[32], int lane, float2* slot) {
-  const int a = lane & 3, kq = lane >> 2;
-#pragma unroll
-  for (int bit = 1; bit <= 2; bit <<= 1) {
-    const bool sw = a & bit;
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      if (d & bit) continue;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float x = acc[8 * d + j], y = acc[8 * (d | bit) + j];
-        acc[8 * d + j] = sw ? y : x;
-        acc[8 * (d | bit) + j] = sw ? x : y;
-      }
-    }
-  }
-  quad_reduce<16>(acc, lane);
-  float2* o = slot + 16 * a + 2 * kq;
-  o[0].x += acc[0];
-  o[0].y += acc[1];
-  o[1].x += acc[2];
-  o[1].y += acc[3];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-}
-
-template <int NW>
-__global__ void __launch_bounds__(NW * 32, 1) k_contract_quad(
-    const float2* __restrict__ FB, int L, int nchunks, int qb, const QuadChunkHdr* __restrict__ chunks,
-    const int* __restrict__ group_ch, const int* __restrict__ items, const DevTerm* __restrict__ terms,
-    const int* __restrict__ tab_off, const unsigned short* __restrict__ tab, const float* __restrict__ codes,
-    int max_slot, int max_tab, float2* __restrict__ Ft) {
-  constexpr int NT = NW * 32;
-  constexpr int slab = 2 * 2 * QUAD_ST;  // uint4 per buffer: two sides x cells x 32 bytes
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned short* TAB = reinterpret_cast<unsigned short*>(smem_raw);
-  unsigned short* ZROW = TAB + max_tab;  // max_tab % 8 == 0
-  uint4* SB = reinterpret_cast<uint4*>(smem_raw + (size_t)(max_tab + QUAD_ZROW) * 2);
-  float2* OUT = reinterpret_cast<float2*>(SB + 2 * slab);
-  float* SC = reinterpret_cast<float*>(OUT + max_slot * 64);
-  if (threadIdx.x < 64) {
-    const float m = codes[threadIdx.x >> 1];
-    SC[threadIdx.x] = (threadIdx.x & 1) ? -m : m;
-  }
-  for (int i = threadIdx.x; i < QUAD_ZROW; i += NT) ZROW[i] = (unsigned short)(31u << 11);
-  const long long V = (long long)L * L * L;
-  const int ci = blockIdx.x % nchunks;
-  const long long q_begin = (long long)(blockIdx.x / nchunks) * qb;
-  const long long q_end = min(V, q_begin + qb);
-  const QuadChunkHdr& ck = chunks[ci];
-  const int base1 = ck.base1, n1c = ck.ncell1, base2 = ck.base2, n2c = ck.ncell2;
-
-  // slab: side 1 cells then side 2 cells, 32 bytes (four spins) per cell
-  auto issue_slabs = [&](long long q, uint4* S) {
-    const int qx = (int)(q % L), qy = (int)((q / L) % L), qz = (int)(q / ((long long)L * L));
-    const long long qm = (L - qx) % L + L * ((L - qy) % L + (long long)L * ((L - qz) % L));
-    for (int i = threadIdx.x; i < 2 * n1c; i += NT)
-      cp_async16q(S + i, reinterpret_cast<const char*>(FB + ((long long)(base1 + (i >> 1)) * V + q) * 4) + 16 * (i & 1));
-    uint4* S2 = S + 2 * QUAD_ST;
-    for (int i = threadIdx.x; i < 2 * n2c; i += NT)
-      cp_async16q(S2 + i, reinterpret_cast<const char*>(FB + ((long long)(base2 + (i >> 1)) * V + qm) * 4) + 16 * (i & 1));
-  };
-
-  for (int i = threadIdx.x; i < ck.tab_len / 8; i += NT) cp_async16q(TAB + 8 * i, tab + ck.tab_off + 8 * i);
-  if (q_begin < q_end) issue_slabs(q_begin, SB);
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-  for (int i = threadIdx.x; i < ck.nslot * 64; i += NT) OUT[i] = make_float2(0.f, 0.f);
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  __syncthreads();
-
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int a = lane & 3, kq = lane >> 2;
-  // this warp's steps: from step kb0 of item wi0 to step kb1 (exclusive) of item wi1
-  const int it0 = ck.item_off + ck.wi0[w], it1 = ck.item_off + ck.wi1[w];
-  const int sb0 = ck.kb0[w], sb1 = ck.kb1[w];
-  const bool has_work = it0 < it1 || (it0 == it1 && sb0 < sb1);
-  for (long long q = q_begin; q < q_end; ++q) {
-    uint4* S = SB + ((q - q_begin) & 1) * slab;
-    if (q + 1 < q_end) issue_slabs(q + 1, SB + ((q + 1 - q_begin) & 1) * slab);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    const float2* S1a = reinterpret_cast<const float2*>(S) + a;
-    const float2* S2a = reinterpret_cast<const float2*>(S + 2 * QUAD_ST) + a;
-    float acc[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-    int cur = -1;
-    for (int it = it0; has_work && it <= it1; ++it) {
-      const int term = items[2 * it], k0 = items[2 * it + 1];
-      const DevTerm h = terms[term];
-      const int local = h.pad - ck.ch_local0;
-      if (local != cur) {
-        if (cur >= 0) quad_flush(acc, lane, OUT + (ck.out_base[w] + cur - ck.cfirst[w]) * 64);
-        cur = local;
-      }
-      const unsigned short* T1 = TAB + tab_off[2 * term];
-      const unsigned short* T2 = TAB + tab_off[2 * term + 1];
-      const int nh1 = 1 << ((h.shape & 1) + ((h.shape >> 1) & 1));
-      const int kb_end = 8 * (it == it1 ? sb1 : 4);
-      for (int kb = it == it0 ? 8 * sb0 : 0; kb < kb_end && k0 + kb < h.K; kb += 8) {
-        const int k = k0 + kb + kq;
-        const bool active = k < h.K;  // the four lanes of a quad agree
-        const unsigned short* p1 = active ? T1 + k * nh1 * h.n1 : ZROW;
-        const unsigned short* p2 = active ? T2 + k * (4 / nh1) * h.n2 : ZROW;
-        // straight-line forms for the four (shape, n1, n2) that carry ~97 % of sum |xi~|
-        switch (h.shape) {
-          case 0:
-            if (h.n1 == 8 && h.n2 == 2) quad_step<0, 4, 1>(h.n1, h.n2, p1, p2, S1a, S2a, SC, acc);
-            else quad_step<0, 0, 0>(h.n1, h.n2, p1, p2, S1a, S2a, SC, acc);
-            break;
-          case 1:
-            if (h.n1 == 2 && h.n2 == 2) quad_step<1, 1, 1>(h.n1, h.n2, p1, p2, S1a, S2a, SC, acc);
-            else quad_step<1, 0, 0>(h.n1, h.n2, p1, p2, S1a, S2a, SC, acc);
-            break;
-          case 2:
-            if (h.n1 == 2 && h.n2 == 2) quad_step<2, 1, 1>(h.n1, h.n2, p1, p2, S1a, S2a, SC, acc);
-            else quad_step<2, 0, 0>(h.n1, h.n2, p1, p2, S1a, S2a, SC, acc);
-            break;
-          default:
-            if (h.n1 == 2 && h.n2 == 8) quad_step<3, 1, 4>(h.n1, h.n2, p1, p2, S1a, S2a, SC, acc);
-            else quad_step<3, 0, 0>(h.n1, h.n2, p1, p2, S1a, S2a, SC, acc);
-            break;
-        }
-      }
-    }
-    if (cur >= 0) quad_flush(acc, lane, OUT + (ck.out_base[w] + cur - ck.cfirst[w]) * 64);
-    __syncthreads();
-    for (int i = threadIdx.x; i < ck.nch * 64; i += NT) {
-      const int c = i / 64, m = i % 64;
-      float2 sum = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int ww = 0; ww < NW; ++ww) {  // fixed order
-        const int r = c - ck.cfirst[ww];
-        if (r >= 0 && r < ck.out_base[ww + 1] - ck.out_base[ww]) {
-          float2& v = OUT[(ck.out_base[ww] + r) * 64 + m];
-          sum.x += v.x;
-          sum.y += v.y;
-          v = make_float2(0.f, 0.f);
-        }
-      }
-      const int spin = (m & ~3) + 2 * (m & 1) + ((m >> 1) & 1);
-      Ft[((long long)group_ch[ck.ch_off + c] * 64 + spin) * V + q] = sum;
-    }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
-  }
-}
-
-// ---- segment-driven form ----------------------------------------------------
-// The same lanes, steps and partial-sum slots, but each warp walks its range as
-// runs of one term (QuadSeg, plan.h) staged in shared memory once per CTA: the
-// term form is dispatched once per run, the step loop only advances two table
-// pointers, and the channel flush indexes alpha2 = a ^ d directly instead of
-// permuting the accumulator first (the reduction never mixes spins a, so both
-// orders give the same sums).
+// ---- runs, flush, kernel -----------------------------------------------------
+// The step loop of a run only advances two table pointers; the channel flush
+// indexes alpha2 = a ^ d directly (the reduction never mixes spins a).
 
 template <int SHAPE, int I1, int I2>
 __device__ __forceinline__ void qseg_run(const QuadSeg& sg, int kq, const unsigned short* TAB,
@@ -379,12 +228,15 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc[j] = 0.f;
     int cur = -1;
-    for (int si = s_begin; si < s_end; ++si) {
-      const QuadSeg sg = SEG[si];
-      if (sg.local != cur) {
+    for (int si = s_begin;; ++si) {
+      // one flush site: on a channel change and after the last run
+      const int local = si < s_end ? SEG[si].local : -1;
+      if (local != cur) {
         if (cur >= 0) qseg_flush(acc, lane, out_w + cur * 64);
-        cur = sg.local;
+        cur = local;
       }
+      if (si >= s_end) break;
+      const QuadSeg sg = SEG[si];
       switch (sg.form) {
         case 4: qseg_run<0, 4, 1>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
         case 5: qseg_run<1, 1, 1>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
@@ -396,7 +248,6 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
         default: qseg_run<3, 0, 0>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
       }
     }
-    if (cur >= 0) qseg_flush(acc, lane, out_w + cur * 64);
     __syncthreads();
     for (int i = threadIdx.x; i < ck.nch * 64; i += NT) {
       const int c = i / 64, m = i % 64;
@@ -441,29 +292,6 @@ cudaError_t launch_contract_qseg(const float2* FB, int L, int nchunks, int qb, c
   kern<<<(unsigned)(nqb * nchunks), NBS_QUAD_WARPS * 32, sm, st>>>(FB, L, nchunks, qb, (const QuadChunkHdr*)chunks,
                                                                    (const QuadSeg*)segs, group_ch, tab, codes,
                                                                    max_slot, max_tab, Ft);
-  return cudaGetLastError();
-}
-
-size_t quad_smem_bytes(int max_slot, int max_tab) {
-  return (size_t)(max_tab + QUAD_ZROW) * 2 + (size_t)2 * 2 * 2 * QUAD_ST * 16 + (size_t)max_slot * 64 * sizeof(float2) +
-         64 * sizeof(float);
-}
-
-cudaError_t launch_contract_quad(const float2* FB, int L, int nchunks, int qb, const void* chunks, const int* group_ch,
-                                 const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
-                                 const float* codes, int max_cells, int max_slot, int max_tab, int max_row, float2* Ft,
-                                 cudaStream_t st) {
-  const long long V = (long long)L * L * L;
-  if (max_row > QUAD_ZROW || max_tab % 8 || max_cells > QUAD_ST || max_cells > 1024) return cudaErrorInvalidValue;
-  const size_t sm = quad_smem_bytes(max_slot, max_tab);
-  auto kern = k_contract_quad<NBS_QUAD_WARPS>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  const long long nqb = (V + qb - 1) / qb;
-  if (nqb * nchunks > 2147483647LL) return cudaErrorInvalidValue;
-  kern<<<(unsigned)(nqb * nchunks), NBS_QUAD_WARPS * 32, sm, st>>>(FB, L, nchunks, qb, (const QuadChunkHdr*)chunks,
-                                                                   group_ch, items, terms, tab_off, tab, codes, max_slot,
-                                                                   max_tab, Ft);
   return cudaGetLastError();
 }
 

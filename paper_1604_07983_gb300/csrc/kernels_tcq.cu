@@ -1,8 +1,8 @@
 // kernels_tcq.cu -- the effective-block product of Eq. (4.3) on the tensor
 // cores (split-BF16 x 3, FP32 accumulation) with the quad-lane work split.
 //
-// Work split, tables, slabs and zero row as in the quad-lane FP32 contraction
-// (kernels_quad.cu): lane 4 kq + a gathers, for shared index k0 + kq of an
+// Work split (per-warp runs), tables, slabs and zero row as in the quad-lane
+// FP32 contraction (kernels_quad.cu): lane 4 kq + a gathers, for shared index k0 + kq of an
 // 8-index step, the rows E1[alpha1 = a][h1] and E2[alpha2 = a][h2].  Seen
 // across the warp, the complex rows of one held spin h form an 8 x 8 matrix
 // M[k][2 alpha + re/im] whose row k is held by the lanes of quad k in exactly
@@ -178,9 +178,8 @@ __device__ __forceinline__ void tcq_flush_all(float (&D)[4][2][4], unsigned used
 template <int NW>
 __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
     const float2* __restrict__ FB, int L, int nchunks, int qb, const QuadChunkHdr* __restrict__ chunks,
-    const int* __restrict__ group_ch, const int* __restrict__ items, const DevTerm* __restrict__ terms,
-    const int* __restrict__ tab_off, const unsigned short* __restrict__ tab, const float* __restrict__ codes,
-    int max_slot, int max_tab, float2* __restrict__ Ft) {
+    const QuadSeg* __restrict__ segs, const int* __restrict__ group_ch, const unsigned short* __restrict__ tab,
+    const float* __restrict__ codes, int max_slot, int max_tab, float2* __restrict__ Ft) {
   constexpr int NT = NW * 32;
   constexpr int slab = 2 * 2 * TCQ_ST;  // uint4 per buffer: two sides x cells x 32 bytes
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -189,6 +188,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
   uint4* SB = reinterpret_cast<uint4*>(smem_raw + (size_t)(max_tab + TCQ_ZROW) * 2);
   float2* OUT = reinterpret_cast<float2*>(SB + 2 * slab);
   float* SC = reinterpret_cast<float*>(OUT + max_slot * 64);
+  QuadSeg* SEG = reinterpret_cast<QuadSeg*>(SC + 64);
   if (threadIdx.x < 64) {
     const float m = codes[threadIdx.x >> 1];
     SC[threadIdx.x] = (threadIdx.x & 1) ? -m : m;
@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
   const long long q_end = min(V, q_begin + qb);
   const QuadChunkHdr& ck = chunks[ci];
   const int base1 = ck.base1, n1c = ck.ncell1, base2 = ck.base2, n2c = ck.ncell2;
+  const int seg0 = ck.seg_base[0], nseg = ck.seg_base[NW] - seg0;
 
   // slab: side 1 cells then side 2 cells, 32 bytes (four spins) per cell
   auto issue_slabs = [&](long long q, uint4* S) {
@@ -213,6 +214,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
   };
 
   for (int i = threadIdx.x; i < ck.tab_len / 8; i += NT) cp_async16t(TAB + 8 * i, tab + ck.tab_off + 8 * i);
+  for (int i = threadIdx.x; i < 2 * nseg; i += NT)
+    cp_async16t(reinterpret_cast<uint4*>(SEG) + i, reinterpret_cast<const uint4*>(segs + seg0) + i);
   if (q_begin < q_end) issue_slabs(q_begin, SB);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   for (int i = threadIdx.x; i < ck.nslot * 64; i += NT) OUT[i] = make_float2(0.f, 0.f);
@@ -221,10 +224,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
 
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a = lane & 3, kq = lane >> 2;
-  // this warp's steps: from step kb0 of item wi0 to step kb1 (exclusive) of item wi1
-  const int it0 = ck.item_off + ck.wi0[w], it1 = ck.item_off + ck.wi1[w];
-  const int sb0 = ck.kb0[w], sb1 = ck.kb1[w];
-  const bool has_work = it0 < it1 || (it0 == it1 && sb0 < sb1);
+  const int s_begin = ck.seg_base[w] - seg0, s_end = ck.seg_base[w + 1] - seg0;
+  float2* const out_w = OUT + (ck.out_base[w] - ck.cfirst[w]) * 64;
   for (long long q = q_begin; q < q_end; ++q) {
     uint4* S = SB + ((q - q_begin) & 1) * slab;
     if (q + 1 < q_end) issue_slabs(q + 1, SB + ((q + 1 - q_begin) & 1) * slab);
@@ -240,34 +241,34 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
         for (int z = 0; z < 4; ++z) D[x][y][z] = 0.f;
     unsigned used = 0;  // shapes accumulated since the last flush (warp-uniform)
     int cur = -1;
-    for (int it = it0; has_work && it <= it1; ++it) {
-      const int term = items[2 * it], k0 = items[2 * it + 1];
-      const DevTerm h = terms[term];
-      const int local = h.pad - ck.ch_local0;
+    for (int si = s_begin;; ++si) {
+      // one flush site: on a channel change and after the last run
+      const int local = si < s_end ? SEG[si].local : -1;
       if (local != cur) {
-        if (cur >= 0) tcq_flush_all(D, used, lane, OUT + (ck.out_base[w] + cur - ck.cfirst[w]) * 64);
+        if (cur >= 0) tcq_flush_all(D, used, lane, out_w + cur * 64);
         used = 0;
         cur = local;
       }
-      used |= 1u << h.shape;
-      const unsigned short* T1 = TAB + tab_off[2 * term];
-      const unsigned short* T2 = TAB + tab_off[2 * term + 1];
-      const int nh1 = 1 << ((h.shape & 1) + ((h.shape >> 1) & 1));
-      const int kb_end = 8 * (it == it1 ? sb1 : 4);
-      for (int kb = it == it0 ? 8 * sb0 : 0; kb < kb_end && k0 + kb < h.K; kb += 8) {
-        const int k = k0 + kb + kq;
-        const bool active = k < h.K;  // the four lanes of a quad agree
-        const unsigned short* p1 = active ? T1 + k * nh1 * h.n1 : ZROW;
-        const unsigned short* p2 = active ? T2 + k * (4 / nh1) * h.n2 : ZROW;
-        switch (h.shape) {
-          case 0: tcq_step<0>(h.n1, h.n2, p1, p2, S1a, S2a, SC, D[0]); break;
-          case 1: tcq_step<1>(h.n1, h.n2, p1, p2, S1a, S2a, SC, D[1]); break;
-          case 2: tcq_step<2>(h.n1, h.n2, p1, p2, S1a, S2a, SC, D[2]); break;
-          default: tcq_step<3>(h.n1, h.n2, p1, p2, S1a, S2a, SC, D[3]); break;
+      if (si >= s_end) break;
+      const QuadSeg sg = SEG[si];
+      const int shape = sg.form & 3;
+      used |= 1u << shape;
+      const int nh1 = 1 << ((shape & 1) + ((shape >> 1) & 1));
+      const int r1 = nh1 * sg.n1, r2 = (4 / nh1) * sg.n2;  // entries per shared index
+      const unsigned short* p1 = TAB + sg.t1 + (sg.kbeg + kq) * r1;
+      const unsigned short* p2 = TAB + sg.t2 + (sg.kbeg + kq) * r2;
+      for (int k0 = sg.kbeg; k0 < sg.kend; k0 += 8, p1 += 8 * r1, p2 += 8 * r2) {
+        const bool active = k0 + kq < sg.kend;  // the four lanes of a quad agree
+        const unsigned short* q1 = active ? p1 : ZROW;
+        const unsigned short* q2 = active ? p2 : ZROW;
+        switch (shape) {
+          case 0: tcq_step<0>(sg.n1, sg.n2, q1, q2, S1a, S2a, SC, D[0]); break;
+          case 1: tcq_step<1>(sg.n1, sg.n2, q1, q2, S1a, S2a, SC, D[1]); break;
+          case 2: tcq_step<2>(sg.n1, sg.n2, q1, q2, S1a, S2a, SC, D[2]); break;
+          default: tcq_step<3>(sg.n1, sg.n2, q1, q2, S1a, S2a, SC, D[3]); break;
         }
       }
     }
-    if (cur >= 0) tcq_flush_all(D, used, lane, OUT + (ck.out_base[w] + cur - ck.cfirst[w]) * 64);
     __syncthreads();
     for (int i = threadIdx.x; i < ck.nch * 64; i += NT) {
       const int c = i / 64, m = i % 64;
@@ -292,25 +293,25 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
 
 }  // namespace
 
-size_t tcq_smem_bytes(int max_slot, int max_tab) {
+size_t tcq_smem_bytes(int max_slot, int max_tab, int max_segs) {
   return (size_t)(max_tab + TCQ_ZROW) * 2 + (size_t)2 * 2 * 2 * TCQ_ST * 16 + (size_t)max_slot * 64 * sizeof(float2) +
-         64 * sizeof(float);
+         64 * sizeof(float) + (size_t)max_segs * sizeof(QuadSeg);
 }
 
-cudaError_t launch_contract_tcq(const float2* FB, int L, int nchunks, int qb, const void* chunks, const int* group_ch,
-                                const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
-                                const float* codes, int max_cells, int max_slot, int max_tab, int max_row, float2* Ft,
-                                cudaStream_t st) {
+cudaError_t launch_contract_tcq(const float2* FB, int L, int nchunks, int qb, const void* chunks, const void* segs,
+                                int max_segs, const int* group_ch, const unsigned short* tab, const float* codes,
+                                int max_cells, int max_slot, int max_tab, int max_row, float2* Ft, cudaStream_t st) {
   const long long V = (long long)L * L * L;
-  if (max_row > TCQ_ZROW || max_tab % 8 || max_cells > TCQ_ST || max_cells > 1024) return cudaErrorInvalidValue;
-  const size_t sm = tcq_smem_bytes(max_slot, max_tab);
+  if (max_row > TCQ_ZROW || max_tab % 8 || max_cells > TCQ_ST || max_cells > 1024 || max_segs < 0)
+    return cudaErrorInvalidValue;
+  const size_t sm = tcq_smem_bytes(max_slot, max_tab, max_segs);
   auto kern = k_contract_tcq<NBS_QUAD_WARPS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const long long nqb = (V + qb - 1) / qb;
   if (nqb * nchunks > 2147483647LL) return cudaErrorInvalidValue;
   kern<<<(unsigned)(nqb * nchunks), NBS_QUAD_WARPS * 32, sm, st>>>(FB, L, nchunks, qb, (const QuadChunkHdr*)chunks,
-                                                                  group_ch, items, terms, tab_off, tab, codes, max_slot,
+                                                                  (const QuadSeg*)segs, group_ch, tab, codes, max_slot,
                                                                   max_tab, Ft);
   return cudaGetLastError();
 }

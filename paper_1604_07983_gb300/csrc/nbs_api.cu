@@ -384,11 +384,9 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
     // default in FP32: the quad-lane chunk kernel when the tables fit; FP64: the thread-per-momentum kernel
     const bool f32_chunks = sizeof(T) == 4 && h->plan.chunks_ok;
     const bool use_qseg = f32_chunks && h->contract_cfg == 0;
-    const bool use_quad = f32_chunks && h->contract_cfg == 5;
     if (h->mode == NBS_BF16X3 && h->plan.chunks_ok && h->contract_cfg != 2) {
       CK(launch_contract_tcq((const float2*)h->FB.p, h->L, (int)h->plan.quad_chunks.size(), h->chunk_qb,
-                             h->d_qchunks.p, (const int*)h->d_gch.p, (const int*)h->d_citems.p,
-                             (const DevTerm*)h->d_terms.p, (const int*)h->d_ctoff.p,
+                             h->d_qchunks.p, h->d_qsegs.p, h->plan.max_quad_segs, (const int*)h->d_gch.p,
                              (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
                              std::max(h->chunk_st1, h->chunk_st2), h->quad_slot, h->chunk_tab, h->chunk_row,
                              (float2*)h->Ft.p, h->st),
@@ -403,14 +401,6 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
     } else if (use_qseg) {
       CK(launch_contract_qseg((const float2*)h->FB.p, h->L, (int)h->plan.quad_chunks.size(), h->chunk_qb,
                               h->d_qchunks.p, h->d_qsegs.p, h->plan.max_quad_segs, (const int*)h->d_gch.p,
-                              (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
-                              std::max(h->chunk_st1, h->chunk_st2), h->quad_slot, h->chunk_tab, h->chunk_row,
-                              (float2*)h->Ft.p, h->st),
-         "contraction");
-    } else if (use_quad) {
-      CK(launch_contract_quad((const float2*)h->FB.p, h->L, (int)h->plan.quad_chunks.size(), h->chunk_qb,
-                              h->d_qchunks.p, (const int*)h->d_gch.p, (const int*)h->d_citems.p,
-                              (const DevTerm*)h->d_terms.p, (const int*)h->d_ctoff.p,
                               (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
                               std::max(h->chunk_st1, h->chunk_st2), h->quad_slot, h->chunk_tab, h->chunk_row,
                               (float2*)h->Ft.p, h->st),
@@ -437,7 +427,7 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
          "contraction");
     } else {
       // configs 1 and 2 name other kernels; where the chunk kernel cannot run (FP64) use the default shape
-      const int cfg = h->contract_cfg <= 5 ? 0 : h->contract_cfg;
+      const int cfg = h->contract_cfg <= 3 ? 0 : h->contract_cfg;
       CK(launch_contract<T>((const C<T>*)h->FB.p, h->L, (const DevTerm*)h->d_terms.p, (const int*)h->d_chtb.p, nch,
                             (const Ent<T>*)h->d_e1.p, (const Ent<T>*)h->d_e2.p, (C<T>*)h->Ft.p, cfg, h->st),
          "contraction");
@@ -758,8 +748,8 @@ int nbs_set_param(nbs_ctx* h, int param, int value) {
   switch (param) {
     case NBS_PARAM_CONTRACT_CFG: {
       const int a = value / 10, w = value % 10;
-      if (!(value >= 0 && value <= 5 && value != 4) && !((a == 1 || a == 2 || a == 4) && (w == 1 || w == 2 || w == 4)))
-        return fail(h, NBS_EINVAL, "contraction config must be 0, 1, 2, 3, 5 or A*10+W with A, W in {1, 2, 4}");
+      if (!(value >= 0 && value <= 3) && !((a == 1 || a == 2 || a == 4) && (w == 1 || w == 2 || w == 4)))
+        return fail(h, NBS_EINVAL, "contraction config must be 0, 1, 2, 3 or A*10+W with A, W in {1, 2, 4}");
       h->contract_cfg = value;
       return NBS_OK;
     }
@@ -933,7 +923,7 @@ int nbs_plan_export(const nbs_plan* p, int what, void* dst) {
       for (int i = 0; i < 32; ++i) D[i] = i < (int)P.coef_codes.size() && i < 31 ? P.coef_codes[i] : 0.0;
       return NBS_OK;
     case NBS_PX_QUADCHUNKS:
-      static_assert(sizeof(QuadChunkHdr) == 128 * sizeof(int), "quad chunk header layout");
+      static_assert(sizeof(QuadChunkHdr) == 64 * sizeof(int), "quad chunk header layout");
       if (P.chunks_ok) std::memcpy(I, P.quad_chunks.data(), P.quad_chunks.size() * sizeof(QuadChunkHdr));
       return NBS_OK;
     case NBS_PX_QUADSEGS:

@@ -356,6 +356,29 @@ void order_for_banks(int K, int n1, int nh1, int n2, int nh2, std::vector<unsign
 
 // Split every slab group into chunks of whole channels whose compressed
 // tables fit NBS_CHUNK_ENTRIES, and balance each chunk's items over warps.
+// Measured cost of one 8-index step of the quad-lane contraction per term
+// form (SM cycles of one of 16 warps, fitted to per-warp timings of the
+// 52-channel tables at 16^3), of starting a run, and of a channel flush.
+double quad_step_cost(int form, int ent, int nh2) {
+  switch (form) {
+    case 4: return 1164;
+    case 5: return 721;
+    case 6: return 807;
+    case 7: return 857;
+    default: return 580 + 30.0 * ent + 102.0 * nh2;  // run-time lengths
+  }
+}
+constexpr double QUAD_RUN_COST = 1500, QUAD_FLUSH_COST = 340;
+
+int quad_form(const TermHdr& th) {
+  if ((th.shape == 0 && th.n1 == 8 && th.n2 == 2) || (th.shape == 1 && th.n1 == 2 && th.n2 == 2) ||
+      (th.shape == 2 && th.n1 == 2 && th.n2 == 2) || (th.shape == 3 && th.n1 == 2 && th.n2 == 8))
+    return th.shape + 4;
+  return th.shape;
+}
+
+// Split every slab group into chunks of whole channels whose compressed
+// tables fit NBS_CHUNK_ENTRIES, and balance each chunk's work over warps.
 void build_chunks(Plan& plan) {
   plan.chunks.clear();
   plan.chunk_tab.clear();
@@ -373,11 +396,19 @@ void build_chunks(Plan& plan) {
     plan.coef_codes.push_back(a);
     return (int)plan.coef_codes.size() - 1;
   };
+  auto held = [](const TermHdr& th, int& nh1, int& nh2) {
+    nh1 = 1 << ((th.shape & 1) + (th.shape >> 1 & 1));
+    nh2 = 4 / nh1;
+  };
   auto term_entries = [&](const TermHdr& th) {
-    const int nh1 = 1 << ((th.shape & 1) + (th.shape >> 1 & 1)), nh2 = 4 / nh1;
+    int nh1, nh2;
+    held(th, nh1, nh2);
     auto pad8 = [](int n) { return (n + 7) / 8 * 8; };
     return pad8(th.K * nh1 * th.n1) + pad8(th.K * nh2 * th.n2);
   };
+  // one table run: a channel's terms of one fixed form (lists of whole 16-byte
+  // rows), or a single term
+  struct Run { int form, n1, n2, nh1, nh2, K, local, t1, t2; };
   for (const GroupHdr& g : plan.groups) {
     if (g.ncell1 > 1024 || g.ncell2 > 1024) return;
     int c = 0;
@@ -401,160 +432,211 @@ void build_chunks(Plan& plan) {
       ck.tab_off = (int)plan.chunk_tab.size();
       ck.item_off = (int)plan.chunk_items.size() / 2;
       std::vector<std::pair<int, int>> its;
-      std::vector<double> cost, qcost;
+      std::vector<double> cost;
+      std::vector<Run> runs;
       for (int local = c; local < c_end; ++local) {
         const int ci = plan.group_ch[g.ch_off + local];
+        // the channel's runs: terms of one fixed form whose lists are whole
+        // 16-byte rows go together, in order of first appearance
+        std::vector<std::vector<int>> members;
+        std::vector<int> run_form;
         for (int t = plan.ch_term_begin[ci]; t < plan.ch_term_begin[ci + 1]; ++t) {
           const TermHdr& th = plan.terms[t];
-          const int nh1 = 1 << ((th.shape & 1) + (th.shape >> 1 & 1)), nh2 = 4 / nh1;
+          int nh1, nh2;
+          held(th, nh1, nh2);
+          const int form = quad_form(th);
+          const bool whole = (th.K * nh1 * th.n1) % 8 == 0 && (th.K * nh2 * th.n2) % 8 == 0;
+          int r = -1;
+          if (form >= 4 && whole)
+            for (size_t j = 0; j < members.size(); ++j)
+              if (run_form[j] == form) r = (int)j;
+          if (r < 0) {
+            members.emplace_back();
+            run_form.push_back(form >= 4 && whole ? form : -1);
+            r = (int)members.size() - 1;
+          }
+          members[r].push_back(t);
+        }
+        for (const std::vector<int>& mem : members) {
+          const TermHdr& t0 = plan.terms[mem[0]];
+          Run run;
+          run.form = quad_form(t0);
+          run.n1 = t0.n1;
+          run.n2 = t0.n2;
+          held(t0, run.nh1, run.nh2);
+          run.K = 0;
+          run.local = t0.pad - c;
           std::vector<unsigned short> ents[2];
-          for (int side = 0; side < 2; ++side) {
-            const int n = side == 0 ? th.K * nh1 * th.n1 : th.K * nh2 * th.n2;
-            const int off = side == 0 ? th.off1 : th.off2;
-            const int base = side == 0 ? g.base1 : g.base2;
-            const auto& cells = side == 0 ? plan.ent1_cell : plan.ent2_cell;
-            const auto& coefs = side == 0 ? plan.ent1_coef : plan.ent2_coef;
-            for (int i = 0; i < n; ++i) {
-              const int cell = cells[off + i] - base;
-              const double cf = coefs[off + i];
-              if (cell < 0 || cell >= 1024) return;
-              int code = 31;  // code 31: zero coefficient (padding)
-              if (cf != 0.0) {
-                code = code_of(cf);
-                if (code >= 31) return;
+          std::vector<int> koff;
+          for (int t : mem) {
+            const TermHdr& th = plan.terms[t];
+            koff.push_back(run.K);
+            run.K += th.K;
+            for (int side = 0; side < 2; ++side) {
+              const int n = side == 0 ? th.K * run.nh1 * th.n1 : th.K * run.nh2 * th.n2;
+              const int off = side == 0 ? th.off1 : th.off2;
+              const int base = side == 0 ? g.base1 : g.base2;
+              const auto& cells = side == 0 ? plan.ent1_cell : plan.ent2_cell;
+              const auto& coefs = side == 0 ? plan.ent1_coef : plan.ent2_coef;
+              for (int i = 0; i < n; ++i) {
+                const int cell = cells[off + i] - base;
+                const double cf = coefs[off + i];
+                if (cell < 0 || cell >= 1024) return;
+                int code = 31;  // code 31: zero coefficient (padding)
+                if (cf != 0.0) {
+                  code = code_of(cf);
+                  if (code >= 31) return;
+                }
+                ents[side].push_back((unsigned short)(cell | ((cf < 0) << 10) | (code << 11)));
               }
-              ents[side].push_back((unsigned short)(cell | ((cf < 0) << 10) | (code << 11)));
             }
           }
-          order_for_banks(th.K, th.n1, nh1, th.n2, nh2, ents[0], ents[1]);
-          for (int side = 0; side < 2; ++side) {
-            plan.term_tab_off[2 * t + side] = (int)plan.chunk_tab.size() - ck.tab_off;
-            plan.chunk_tab.insert(plan.chunk_tab.end(), ents[side].begin(), ents[side].end());
-            while ((plan.chunk_tab.size() - ck.tab_off) % 8) plan.chunk_tab.push_back((unsigned short)(0x1F << 11));
+          // the members of a run share channel and form: any of the run's
+          // shared indices may stand at any member's position
+          order_for_banks(run.K, run.n1, run.nh1, run.n2, run.nh2, ents[0], ents[1]);
+          const int r1 = run.nh1 * run.n1, r2 = run.nh2 * run.n2;
+          run.t1 = (int)plan.chunk_tab.size() - ck.tab_off;
+          plan.chunk_tab.insert(plan.chunk_tab.end(), ents[0].begin(), ents[0].end());
+          while ((plan.chunk_tab.size() - ck.tab_off) % 8) plan.chunk_tab.push_back((unsigned short)(0x1F << 11));
+          run.t2 = (int)plan.chunk_tab.size() - ck.tab_off;
+          plan.chunk_tab.insert(plan.chunk_tab.end(), ents[1].begin(), ents[1].end());
+          while ((plan.chunk_tab.size() - ck.tab_off) % 8) plan.chunk_tab.push_back((unsigned short)(0x1F << 11));
+          for (size_t j = 0; j < mem.size(); ++j) {
+            const int t = mem[j];
+            const TermHdr& th = plan.terms[t];
+            plan.term_tab_off[2 * t] = run.t1 + koff[j] * r1;
+            plan.term_tab_off[2 * t + 1] = run.t2 + koff[j] * r2;
+            for (int k0 = 0; k0 < th.K; k0 += 32) {
+              // warp instructions per step of the pair-lane kernels ~ a fixed part
+              // plus one part per gather entry of a shared index
+              const int nkb = (std::min(32, th.K - k0) + 15) / 16;  // 16 indices per step
+              its.push_back({t, k0});
+              cost.push_back(nkb * (26.0 + r1 + r2));
+            }
           }
-          for (int k0 = 0; k0 < th.K; k0 += 32) {
-            // warp instructions per step ~ a fixed part (products, loop control) plus
-            // one part per gather entry of a shared index (ratios from instruction counts)
-            const double ent = nh1 * th.n1 + nh2 * th.n2;
-            const int nkb = (std::min(32, th.K - k0) + 15) / 16;  // pair lanes: 16 indices per step
-            its.push_back({t, k0});
-            cost.push_back(nkb * (26.0 + ent));
-            const int nks = (std::min(32, th.K - k0) + 7) / 8;    // quad lanes: 8 indices per step
-            qcost.push_back(nks * (23.0 + ent));
-          }
+          runs.push_back(run);
         }
       }
       ck.tab_len = (int)plan.chunk_tab.size() - ck.tab_off;
       // contiguous per-warp item ranges of about equal cost, and the partial-sum
       // slots each warp needs (one per channel its range touches)
-      auto split = [&](const std::vector<double>& cst, int nw, int* warp_off, int* out_base, int* cfirst) {
+      {
         double total = 0;
-        for (double x : cst) total += x;
+        for (double x : cost) total += x;
         int w = 0;
         double acc = 0;
-        warp_off[0] = 0;
+        ck.warp_off[0] = 0;
         for (size_t i = 0; i < its.size(); ++i) {
-          acc += cst[i];
-          if (w < nw - 1 && acc >= total * (w + 1) / nw) warp_off[++w] = (int)i + 1;
+          acc += cost[i];
+          if (w < NBS_CHUNK_WARPS - 1 && acc >= total * (w + 1) / NBS_CHUNK_WARPS) ck.warp_off[++w] = (int)i + 1;
         }
-        while (w < nw) warp_off[++w] = (int)its.size();
-        out_base[0] = 0;
-        for (int ww = 0; ww < nw; ++ww) {
+        while (w < NBS_CHUNK_WARPS) ck.warp_off[++w] = (int)its.size();
+        ck.out_base[0] = 0;
+        for (int ww = 0; ww < NBS_CHUNK_WARPS; ++ww) {
           int n = 0;
-          cfirst[ww] = 0;
-          if (warp_off[ww + 1] > warp_off[ww]) {
-            const int c0 = plan.terms[its[warp_off[ww]].first].pad - c;
-            const int c1 = plan.terms[its[warp_off[ww + 1] - 1].first].pad - c;
-            cfirst[ww] = c0;
+          ck.cfirst[ww] = 0;
+          if (ck.warp_off[ww + 1] > ck.warp_off[ww]) {
+            const int c0 = plan.terms[its[ck.warp_off[ww]].first].pad - c;
+            const int c1 = plan.terms[its[ck.warp_off[ww + 1] - 1].first].pad - c;
+            ck.cfirst[ww] = c0;
             n = c1 - c0 + 1;
           }
-          out_base[ww + 1] = out_base[ww] + n;
+          ck.out_base[ww + 1] = ck.out_base[ww] + n;
         }
-        return out_base[nw];
-      };
-      ck.nslot = split(cost, NBS_CHUNK_WARPS, ck.warp_off, ck.out_base, ck.cfirst);
+        ck.nslot = ck.out_base[NBS_CHUNK_WARPS];
+      }
       QuadChunkHdr qk = {};
       qk.base1 = ck.base1; qk.ncell1 = ck.ncell1; qk.base2 = ck.base2; qk.ncell2 = ck.ncell2;
       qk.ch_off = ck.ch_off; qk.nch = ck.nch; qk.tab_off = ck.tab_off; qk.tab_len = ck.tab_len;
-      qk.item_off = ck.item_off; qk.ch_local0 = ck.ch_local0;
+      qk.ch_local0 = ck.ch_local0;
       {
-        // split the chunk's 8-index steps (qcost[i] / nsteps[i] each) into NBS_QUAD_WARPS
-        // contiguous ranges of about equal cost
-        std::vector<int> first(its.size() + 1, 0);  // first global step of each item
-        std::vector<double> step_cost;
-        for (size_t i = 0; i < its.size(); ++i) {
-          const TermHdr& th = plan.terms[its[i].first];
-          const int nks = (std::min(32, th.K - its[i].second) + 7) / 8;
-          first[i + 1] = first[i] + nks;
-          for (int j = 0; j < nks; ++j) step_cost.push_back(qcost[i] / nks);
+        // the runs' 8-index steps in order, each with its measured cost; a warp's
+        // range also pays one run start per run and one flush per channel it
+        // touches.  Cut into NBS_QUAD_WARPS contiguous ranges whose largest
+        // cost is smallest (bisection on that cost, greedy fill).
+        std::vector<int> srun, sk;
+        std::vector<double> scost;
+        for (size_t r = 0; r < runs.size(); ++r) {
+          const Run& run = runs[r];
+          const double sc = quad_step_cost(run.form, run.nh1 * run.n1 + run.nh2 * run.n2, run.nh2);
+          for (int k = 0; k < run.K; k += 8) {
+            srun.push_back((int)r);
+            sk.push_back(k);
+            scost.push_back(sc);
+          }
         }
-        const int nsteps = first.back();
-        double total = 0;
-        for (double x : step_cost) total += x;
-        std::vector<int> cut(NBS_QUAD_WARPS + 1, nsteps);
-        cut[0] = 0;
-        int w = 0;
-        double acc = 0;
-        for (int g = 0; g < nsteps; ++g) {
-          acc += step_cost[g];
-          if (w < NBS_QUAD_WARPS - 1 && acc >= total * (w + 1) / NBS_QUAD_WARPS) cut[++w] = g + 1;
-        }
-        auto locate = [&](int g, int& item, int& kb) {  // global step -> (item, step inside it)
-          item = (int)(std::upper_bound(first.begin(), first.end(), g) - first.begin()) - 1;
-          kb = g - first[item];
+        const int nsteps = (int)scost.size();
+        auto add_cost = [&](int s, bool first) {  // cost of step s appended to a range
+          double x = scost[s];
+          if (first || srun[s] != srun[s - 1]) x += QUAD_RUN_COST;
+          if (first || runs[srun[s]].local != runs[srun[s - 1]].local) x += QUAD_FLUSH_COST;
+          return x;
         };
+        auto fill = [&](double cap, std::vector<int>* cut) {  // warps used by a greedy fill
+          int w = 0;
+          double acc = 0;
+          if (cut) (*cut)[0] = 0;
+          for (int s = 0; s < nsteps; ++s) {
+            const bool first = s == 0 || (cut && (*cut)[w] == s);
+            double x = add_cost(s, first);
+            if (!first && acc + x > cap) {
+              ++w;
+              if (w >= NBS_QUAD_WARPS) return w + 1;
+              if (cut) (*cut)[w] = s;
+              x = add_cost(s, true);
+              acc = 0;
+            }
+            acc += x;
+          }
+          if (cut)
+            for (int ww = w + 1; ww <= NBS_QUAD_WARPS; ++ww) (*cut)[ww] = nsteps;
+          return w + 1;
+        };
+        double lo = 0, hi = 0;
+        for (int s = 0; s < nsteps; ++s) {
+          hi += add_cost(s, true);
+          lo = std::max(lo, add_cost(s, true));
+        }
+        for (int it = 0; it < 60 && hi - lo > 1e-6 * hi; ++it) {
+          const double mid = 0.5 * (lo + hi);
+          if (fill(mid, nullptr) <= NBS_QUAD_WARPS) hi = mid;
+          else lo = mid;
+        }
+        std::vector<int> cut(NBS_QUAD_WARPS + 1, nsteps);
+        fill(hi, &cut);
+        const int seg0 = (int)plan.quad_segs.size();
         qk.out_base[0] = 0;
         for (int ww = 0; ww < NBS_QUAD_WARPS; ++ww) {
+          qk.seg_base[ww] = (int)plan.quad_segs.size();
           int n = 0;
           qk.cfirst[ww] = 0;
           if (cut[ww + 1] > cut[ww]) {
-            locate(cut[ww], qk.wi0[ww], qk.kb0[ww]);
-            locate(cut[ww + 1] - 1, qk.wi1[ww], qk.kb1[ww]);
-            ++qk.kb1[ww];  // exclusive
-            const int c0 = plan.terms[its[qk.wi0[ww]].first].pad - c;
-            const int c1 = plan.terms[its[qk.wi1[ww]].first].pad - c;
+            const int c0 = runs[srun[cut[ww]]].local, c1 = runs[srun[cut[ww + 1] - 1]].local;
             qk.cfirst[ww] = c0;
             n = c1 - c0 + 1;
-          } else {
-            qk.wi0[ww] = qk.wi1[ww] = 0;
-            qk.kb0[ww] = qk.kb1[ww] = 0;  // no steps
           }
           qk.out_base[ww + 1] = qk.out_base[ww] + n;
-        }
-        qk.nslot = qk.out_base[NBS_QUAD_WARPS];
-        // the warp ranges as runs of one term: [kbeg, kend) of consecutive steps
-        const int seg0 = (int)plan.quad_segs.size();
-        for (int ww = 0; ww < NBS_QUAD_WARPS; ++ww) {
-          qk.seg_base[ww] = (int)plan.quad_segs.size();
-          for (int g = cut[ww]; g < cut[ww + 1]; ++g) {
-            int item, kb;
-            locate(g, item, kb);
-            const int t = its[item].first;
-            const TermHdr& th = plan.terms[t];
-            const int k = its[item].second + 8 * kb;
-            const int kend = std::min(th.K, k + 8);
-            QuadSeg* last = plan.quad_segs.size() > (size_t)qk.seg_base[ww] ? &plan.quad_segs.back() : nullptr;
-            if (last && last->t1 == plan.term_tab_off[2 * t] && last->kend == k && last->local == th.pad - c &&
-                last->t2 == plan.term_tab_off[2 * t + 1]) {
-              last->kend = kend;
+          for (int s = cut[ww]; s < cut[ww + 1]; ++s) {
+            const Run& run = runs[srun[s]];
+            const int kend = std::min(run.K, sk[s] + 8);
+            if (s > cut[ww] && srun[s - 1] == srun[s]) {
+              plan.quad_segs.back().kend = kend;
               continue;
             }
             QuadSeg sg;
-            sg.form = th.shape;
-            if ((th.shape == 0 && th.n1 == 8 && th.n2 == 2) || (th.shape == 1 && th.n1 == 2 && th.n2 == 2) ||
-                (th.shape == 2 && th.n1 == 2 && th.n2 == 2) || (th.shape == 3 && th.n1 == 2 && th.n2 == 8))
-              sg.form += 4;
-            sg.t1 = plan.term_tab_off[2 * t];
-            sg.t2 = plan.term_tab_off[2 * t + 1];
-            sg.kbeg = k;
+            sg.form = run.form;
+            sg.t1 = run.t1;
+            sg.t2 = run.t2;
+            sg.kbeg = sk[s];
             sg.kend = kend;
-            sg.local = th.pad - c;
-            sg.n1 = th.n1;
-            sg.n2 = th.n2;
+            sg.local = run.local;
+            sg.n1 = run.n1;
+            sg.n2 = run.n2;
             plan.quad_segs.push_back(sg);
           }
         }
         qk.seg_base[NBS_QUAD_WARPS] = (int)plan.quad_segs.size();
+        qk.nslot = qk.out_base[NBS_QUAD_WARPS];
         plan.max_quad_segs = std::max(plan.max_quad_segs, (int)plan.quad_segs.size() - seg0);
       }
       plan.quad_chunks.push_back(qk);

@@ -83,33 +83,31 @@ struct ChunkHdr {
   int pad[3];
 };
 
-// The same chunks split over NBS_QUAD_WARPS warps for the quad-lane contraction
-// (four lanes per shared index, eight indices per warp step): same tables and
-// items, its own per-warp item ranges and partial-sum slots.
+// The same chunks split over NBS_QUAD_WARPS warps for the quad-lane kernels
+// (four lanes per shared index, eight indices per warp step).  Their tables
+// hold the terms of a channel that share one fixed form as one run (the
+// members' lists back to back, each member still addressable by its own table
+// offsets), and the chunk's 8-index steps are cut into NBS_QUAD_WARPS
+// contiguous ranges of about equal measured cost.  Warp w walks its range as
+// the runs Plan::quad_segs[seg_base[w] .. seg_base[w + 1]) and adds its
+// partial sums into slots out_base[w] + local - cfirst[w].
 #define NBS_QUAD_WARPS 16
-// Warp w takes the 8-index steps from step kb0[w] of item wi0[w] up to (not
-// including) step kb1[w] of item wi1[w] (items relative to item_off): ranges are
-// cut at steps, not items, so the warps get nearly equal work.
 struct QuadChunkHdr {
   int base1, ncell1, base2, ncell2;
   int ch_off, nch;
   int tab_off, tab_len;
-  int item_off, nslot;
-  int wi0[NBS_QUAD_WARPS], kb0[NBS_QUAD_WARPS], wi1[NBS_QUAD_WARPS], kb1[NBS_QUAD_WARPS];
+  int nslot, ch_local0;
   int out_base[NBS_QUAD_WARPS + 1];
   int cfirst[NBS_QUAD_WARPS];
-  int ch_local0;
-  // the same ranges as runs of one term each: warp w's segments are
-  // Plan::quad_segs[seg_base[w] .. seg_base[w + 1])
   int seg_base[NBS_QUAD_WARPS + 1];
-  int pad[3];  // 128 ints
+  int pad[4];  // 64 ints
 };
 
-// One run of consecutive 8-index steps of one term inside a warp's range:
-// shared indices [kbeg, kend) (kbeg a multiple of 8, kend <= K), table offsets
-// of the two gather lists inside the chunk table, the chunk-local channel and
-// the term form (0..3: shape with run-time lengths; 4..7: the straight-line
-// forms (shape 0, n 8/2), (1, 2/2), (2, 2/2), (3, 2/8)).
+// One run of consecutive 8-index steps inside a warp's range: shared indices
+// [kbeg, kend) (kbeg a multiple of 8) of one table run, the table offsets of
+// its two gather lists inside the chunk table, the chunk-local channel and the
+// form (0..3: shape with run-time lengths; 4..7: the fixed forms (shape 0,
+// n 8/2), (1, 2/2), (2, 2/2), (3, 2/8)).
 struct QuadSeg { int form, t1, t2, kbeg, kend, local, n1, n2; };
 
 struct Plan {

@@ -145,8 +145,8 @@ def plan_tables(channel_ids, flavours: int = 2):
             ent2_coef=get("ENT2_COEF", (ne2,), np.float64), channels=get("CHANNELS", (nch, 4), np.int32),
             groups=get("GROUPS", (ngr, 24), np.int32), items=get("ITEMS", (nit, 2), np.int32),
             group_ch=get("GROUPCH", (nch,), np.int32), chunks=get("CHUNKS", (nck, 40), np.int32),
-            quad_chunks=(qc := get("QUADCHUNKS", (nck, 128), np.int32)),
-            quad_segs=get("QUADSEGS", (int(qc[-1, 108 + 16]) if nck else 0, 8), np.int32),
+            quad_chunks=(qc := get("QUADCHUNKS", (nck, 64), np.int32)),
+            quad_segs=get("QUADSEGS", (int(qc[-1, 43 + 16]) if nck else 0, 8), np.int32),
             chunk_tab=get("CHUNKTAB", (max(nctab, 1),), np.uint16), chunk_items=get("CHUNKITEMS", (ncit, 2), np.int32),
             term_tab_off=get("TERMTABOFF", (nterm, 2), np.int32), codes=get("CODES", (32,), np.float64))
     finally:

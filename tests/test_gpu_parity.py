@@ -115,7 +115,7 @@ def test_fp32_all_channels_L4(nbs):
         assert rel(F32[c, 0], ref) < FP32_TOL, names[c]
 
 
-@pytest.mark.parametrize("cfg", [1, 2, 3, 5, 22, 11])
+@pytest.mark.parametrize("cfg", [1, 2, 3, 22, 11])
 def test_contraction_variants_all_channels(nbs, cfg):
     """Every contraction kernel and launch shape against the oracle, FP64 and FP32, all 52 channels."""
     L = 3
@@ -133,14 +133,12 @@ def test_contraction_variants_all_channels(nbs, cfg):
 def test_chunk_kernel_forms_agree_bitwise(nbs):
     """The two forms of the chunk contraction (configs 2, 3) do the same FP32 operations in the same
     order: identical results, here with a momentum block (24) that leaves a ragged last block at 4^3.
-    The quad-lane form sums in another order: equal to FP32 rounding.  Its segment-driven kernel
-    (config 0, the default) and its item-driven kernel (config 5) take the same steps in the same order:
-    identical results."""
+    The quad-lane kernel (config 0, the default) sums in another order: equal to FP32 rounding."""
     L = 4
     props = seeded(1723, L, 1, decay=0.5)
     ids = list(range(nbs.channel_count()))
     out = []
-    for cfg in (2, 3, 5, 0):
+    for cfg in (2, 3, 0):
         with nbs.Context(L, 1, precision=nbs.NBS_FP32) as ctx:
             ctx.set_param(ctx.PARAM_CONTRACT_CFG, cfg)
             ctx.set_param(ctx.PARAM_CHUNK_QBLOCK, 24)
@@ -153,7 +151,6 @@ def test_chunk_kernel_forms_agree_bitwise(nbs):
     assert np.array_equal(out[0], out[1])
     for c in ids:
         assert rel(out[2][c], out[0][c]) < 1e-6, c
-    assert np.array_equal(out[2], out[3])
 
 
 @pytest.mark.parametrize("cfg", [0, 2])

@@ -132,9 +132,9 @@ def test_slab_work_split_covers_every_term_once(lib, ids):
 def test_chunk_tables_decode_to_the_gather_tables(lib, ids):
     """The 16-bit shared-memory tables of the chunk contraction decode to the
     full gather tables up to the order of the shared indices (the same on both
-    sides) and of the entries of each sum, every read stays in its slab, every
-    shared index of every term is visited once, and the shared memory fits a
-    GB300 block."""
+    sides; terms of one channel and form may exchange them) and of the entries
+    of each sum, every read stays in its slab, every shared index of every term
+    is visited once, and the shared memory fits a GB300 block."""
     tb = nbs.plan_tables(ids)
     chunks, ctab, items, toff, codes = tb["chunks"], tb["chunk_tab"], tb["chunk_items"], tb["term_tab_off"], tb["codes"]
     terms = tb["terms"]
@@ -154,11 +154,15 @@ def test_chunk_tables_decode_to_the_gather_tables(lib, ids):
                 r = gl - local0 - cfirst[w]
                 assert 0 <= gl - local0 < nch and 0 <= r < out_base[w + 1] - out_base[w]
                 seen[t] += min(32, K - k0)
+        got_keys, want_keys = {}, {}
         for t in set(int(x) for x in items[item_off:item_off + warp_off[8], 0]):
             ch, K, shape, nn1, nn2, off1, off2, gl = terms[t]
             nh1 = 1 << ((shape & 1) + ((shape >> 1) & 1))
             nh2 = 4 // nh1
-            got_keys, want_keys = [[] for _ in range(K)], [[] for _ in range(K)]
+            got = [[] for _ in range(K)]
+            want = [[] for _ in range(K)]
+            got_keys.setdefault((ch, shape, nn1, nn2), []).append(got)
+            want_keys.setdefault((ch, shape, nn1, nn2), []).append(want)
             for side, (nn, nh, off, base, ncell) in enumerate([(nn1, nh1, off1, base1, n1), (nn2, nh2, off2, base2, n2)]):
                 n = K * nh * nn
                 o = toff[t, side]
@@ -171,10 +175,13 @@ def test_chunk_tables_decode_to_the_gather_tables(lib, ids):
                 want_coef = tb["ent%d_coef" % (side + 1)][off: off + n].reshape(K, nn, nh)
                 for k in range(K):
                     for h in range(nh):
-                        for keys, c, f in ((got_keys, cell, coef), (want_keys, want_cell, want_coef)):
+                        for keys, c, f in ((got, cell, coef), (want, want_cell, want_coef)):
                             keys[k].append(tuple(sorted((int(c[k, i, h]), round(float(f[k, i, h]), 9))
                                                         for i in range(nn) if f[k, i, h] != 0)))
-            assert sorted(map(tuple, got_keys)) == sorted(map(tuple, want_keys))
+        # the terms of one channel and form may share their shared indices (one table run)
+        for key in want_keys:
+            flat = lambda lists: sorted(tuple(x) for lst in lists for x in lst)
+            assert flat(got_keys[key]) == flat(want_keys[key]), key
     assert (seen == terms[:, 1]).all()
 
 
@@ -242,60 +249,49 @@ def test_three_flavours_reproduce_oracle(lib):
     assert np.linalg.norm(Fl - F2) <= 1e-12 * np.linalg.norm(F2)
 
 
-def test_quad_warp_ranges_cover_every_step_once(lib):
-    """The quad-lane kernels cut each chunk's 8-index steps into 16 contiguous warp ranges: every step of
-    every item is taken by exactly one warp and each warp's channels fit its partial-sum slots."""
+def test_quad_runs_cover_every_step_once(lib):
+    """The quad-lane kernels walk each chunk's table runs (a channel's terms of one fixed form back to
+    back, or one term) in 8-index steps cut into 16 warp ranges: every shared index of every run is taken
+    by exactly one warp, each segment stays inside one run and names the run's form, lengths and channel,
+    and each warp's channels fit its partial-sum slots.  The runs are the terms' tables laid end to end."""
     tb = nbs.plan_tables(list(range(52)))
-    T, items = tb["terms"], tb["chunk_items"]
-    for ck, qk in zip(tb["chunks"], tb["quad_chunks"]):
-        item_off, nit = ck[8], ck[10 + 8]
-        nks = [(min(32, T[t][1] - k0) + 7) // 8 for t, k0 in items[item_off:item_off + nit]]
-        wi0, kb0, wi1, kb1 = qk[10:26], qk[26:42], qk[42:58], qk[58:74]
-        out_base, cfirst, ch_local0 = qk[74:91], qk[91:107], qk[107]
-        seen = [[0] * n for n in nks]
-        for w in range(16):
-            if not (wi0[w] < wi1[w] or (wi0[w] == wi1[w] and kb0[w] < kb1[w])):
-                continue
-            for it in range(wi0[w], wi1[w] + 1):
-                local = T[items[item_off + it][0]][7] - ch_local0
-                assert 0 <= local - cfirst[w] < out_base[w + 1] - out_base[w]
-                for st in range(kb0[w] if it == wi0[w] else 0, kb1[w] if it == wi1[w] else 4):
-                    if st < nks[it]:
-                        seen[it][st] += 1
-        assert all(x == 1 for row in seen for x in row)
-        assert qk[9] == out_base[16]
-
-
-def test_quad_segments_replay_the_warp_ranges(lib):
-    """The segment-driven quad kernel walks each warp's range as runs of one term: expanded into
-    8-index steps, the runs give exactly the steps of the item-based ranges, in the same order, with
-    the term's form, lengths, table offsets and chunk-local channel."""
-    tb = nbs.plan_tables(list(range(52)))
-    T, items, toff, segs = tb["terms"], tb["chunk_items"], tb["term_tab_off"], tb["quad_segs"]
+    T, toff, segs = tb["terms"], tb["term_tab_off"], tb["quad_segs"]
     fixed = {(0, 8, 2): 4, (1, 2, 2): 5, (2, 2, 2): 6, (3, 2, 8): 7}
-    assert len(segs) == tb["quad_chunks"][-1][108 + 16]
+    assert len(segs) == tb["quad_chunks"][-1][43 + 16]
     for ck, qk in zip(tb["chunks"], tb["quad_chunks"]):
-        item_off, nit = ck[8], ck[10 + 8]
-        its = [tuple(x) for x in items[item_off:item_off + nit]]
-        nks = [(min(32, T[t][1] - k0) + 7) // 8 for t, k0 in its]
-        wi0, kb0, wi1, kb1 = qk[10:26], qk[26:42], qk[42:58], qk[58:74]
-        ch_local0, seg_base = qk[107], qk[108:125]
-        by_off = {(toff[t][0], toff[t][1]): t for t, _ in its}
+        item_off, nit, local0 = ck[8], ck[10 + 8], ck[36]
+        nslot, out_base, cfirst, seg_base = qk[8], qk[10:27], qk[27:43], qk[43:60]
+        assert qk[9] == local0 and nslot == out_base[16]
+        terms_here = sorted(set(int(t) for t in tb["chunk_items"][item_off:item_off + nit, 0]))
+        # runs: maximal chains of terms whose side-1 and side-2 tables continue each other
+        start = {}
+        for t in terms_here:
+            ch, K, shape, n1, n2 = T[t][:5]
+            nh1 = 1 << ((shape & 1) + ((shape >> 1) & 1))
+            start[(toff[t][0], toff[t][1])] = (t, K, nh1 * n1, (4 // nh1) * n2)
+        runs = {}
+        for (o1, o2), (t, K, r1, r2) in start.items():
+            if any(o1 == p1 + k * a and o2 == p2 + k * b for (p1, p2), (_, k, a, b) in start.items() if (p1, p2) != (o1, o2)):
+                continue  # continues another member
+            members, k_tot, c1, c2 = [t], K, o1 + K * r1, o2 + K * r2
+            while (c1, c2) in start:
+                t2, K2, _, _ = start[(c1, c2)]
+                members.append(t2)
+                k_tot += K2
+                c1, c2 = c1 + K2 * r1, c2 + K2 * r2
+            runs[(o1, o2)] = (members, k_tot)
+        assert sum(len(m) for m, _ in runs.values()) == len(terms_here)
+        seen = {key: np.zeros(k, dtype=int) for key, (_, k) in runs.items()}
         for w in range(16):
-            want = []
-            if wi0[w] < wi1[w] or (wi0[w] == wi1[w] and kb0[w] < kb1[w]):
-                for it in range(wi0[w], wi1[w] + 1):
-                    t, k0 = its[it]
-                    for st in range(kb0[w] if it == wi0[w] else 0, kb1[w] if it == wi1[w] else 4):
-                        if st < nks[it]:
-                            want.append((t, k0 + 8 * st))
-            got = []
             for form, t1, t2, kbeg, kend, local, n1, n2 in segs[seg_base[w]:seg_base[w + 1]]:
-                t = by_off[(t1, t2)]
-                ch, K, shape = T[t][0], T[t][1], T[t][2]
-                assert (n1, n2) == (T[t][3], T[t][4])
-                assert form == fixed.get((shape, n1, n2), shape)
-                assert local == T[t][7] - ch_local0
-                assert kbeg % 8 == 0 and kbeg < kend <= K
-                got += [(t, k) for k in range(kbeg, kend, 8)]
-            assert got == want, w
+                members, k_tot = runs[(t1, t2)]
+                shapes = {tuple(T[m][2:5]) for m in members}
+                assert len(shapes) == 1 and len({T[m][7] for m in members}) == 1
+                shape, nn1, nn2 = shapes.pop()
+                assert (n1, n2) == (nn1, nn2) and form == fixed.get((shape, n1, n2), shape)
+                assert len(members) == 1 or form >= 4
+                assert local == T[members[0]][7] - local0
+                assert 0 <= local - cfirst[w] < out_base[w + 1] - out_base[w]
+                assert kbeg % 8 == 0 and kbeg < kend <= k_tot
+                seen[(t1, t2)][kbeg:kend] += 1
+        assert all((v == 1).all() for v in seen.values())
