@@ -155,11 +155,13 @@ __device__ __forceinline__ void qseg_run(const QuadSeg& sg, int kq, const unsign
 }
 
 // reduce over the eight shared-index lanes, add into slot [alpha1][alpha2][s];
-// acc holds complex 4 d + s with alpha2 = a ^ d
-__device__ __forceinline__ void qseg_flush(float (&acc)[32], int lane, float2* slot) {
+// acc holds complex 4 d + s with (alpha1, alpha2) = (a, a ^ d), or
+// (a ^ d, a) after a run with exchanged sides (swapped)
+__device__ __forceinline__ void qseg_flush(float (&acc)[32], int lane, bool swapped, float2* slot) {
   const int a = lane & 3, kq = lane >> 2;
   quad_reduce<16>(acc, lane);  // lane keeps complex 2 kq, 2 kq + 1: d = kq >> 1, s = 2 (kq & 1) + {0, 1}
-  float2* o = slot + 16 * a + 4 * (a ^ (kq >> 1)) + 2 * (kq & 1);
+  const int b = a ^ (kq >> 1);
+  float2* o = slot + (swapped ? 16 * b + 4 * a : 16 * a + 4 * b) + 2 * (kq & 1);
   o[0].x += acc[0];
   o[0].y += acc[1];
   o[1].x += acc[2];
@@ -195,9 +197,18 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
   const int base1 = ck.base1, n1c = ck.ncell1, base2 = ck.base2, n2c = ck.ncell2;
   const int seg0 = ck.seg_base[0], nseg = ck.seg_base[NW] - seg0;
 
+  // coordinates of the next momentum to stage (slabs are issued for q_begin,
+  // q_begin + 1, ... in order)
+  int nqx = (int)(q_begin % L), nqy = (int)((q_begin / L) % L), nqz = (int)(q_begin / ((long long)L * L));
   auto issue_slabs = [&](long long q, uint4* S) {
-    const int qx = (int)(q % L), qy = (int)((q / L) % L), qz = (int)(q / ((long long)L * L));
-    const long long qm = (L - qx) % L + L * ((L - qy) % L + (long long)L * ((L - qz) % L));
+    const long long qm = (nqx ? L - nqx : 0) + L * ((nqy ? L - nqy : 0) + (long long)L * (nqz ? L - nqz : 0));
+    if (++nqx == L) {
+      nqx = 0;
+      if (++nqy == L) {
+        nqy = 0;
+        ++nqz;
+      }
+    }
     for (int i = threadIdx.x; i < 2 * n1c; i += NT)
       cp_async16q(S + i, reinterpret_cast<const char*>(FB + ((long long)(base1 + (i >> 1)) * V + q) * 4) + 16 * (i & 1));
     uint4* S2 = S + 2 * QUAD_ST;
@@ -227,25 +238,24 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
     float acc[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-    int cur = -1;
+    int cur = -1;  // 2 * channel + sides exchanged, of the accumulated products
     for (int si = s_begin;; ++si) {
-      // one flush site: on a channel change and after the last run
-      const int local = si < s_end ? SEG[si].local : -1;
-      if (local != cur) {
-        if (cur >= 0) qseg_flush(acc, lane, out_w + cur * 64);
-        cur = local;
+      // one flush site: on a change of channel or of side order, and after the last run
+      const int key = si < s_end ? 2 * SEG[si].local + ((SEG[si].form >> 3) & 1) : -1;
+      if (key != cur) {
+        if (cur >= 0) qseg_flush(acc, lane, cur & 1, out_w + (cur >> 1) * 64);
+        cur = key;
       }
       if (si >= s_end) break;
       const QuadSeg sg = SEG[si];
-      switch (sg.form) {
-        case 4: qseg_run<0, 4, 1>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
-        case 5: qseg_run<1, 1, 1>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
-        case 6: qseg_run<2, 1, 1>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
-        case 7: qseg_run<3, 1, 4>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
-        case 0: qseg_run<0, 0, 0>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
-        case 1: qseg_run<1, 0, 0>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
-        case 2: qseg_run<2, 0, 0>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
-        default: qseg_run<3, 0, 0>(sg, kq, TAB, ZROW, S1a, S2a, SC, acc); break;
+      const bool sw = sg.form & 8;
+      const float2* Sa = sw ? S2a : S1a;  // the lanes' own list
+      const float2* Sb = sw ? S1a : S2a;  // the exchanged list
+      switch (sg.form & 7) {
+        case 5: qseg_run<1, 1, 1>(sg, kq, TAB, ZROW, Sa, Sb, SC, acc); break;
+        case 7: qseg_run<3, 1, 4>(sg, kq, TAB, ZROW, Sa, Sb, SC, acc); break;
+        case 1: qseg_run<1, 0, 0>(sg, kq, TAB, ZROW, Sa, Sb, SC, acc); break;
+        default: qseg_run<3, 0, 0>(sg, kq, TAB, ZROW, Sa, Sb, SC, acc); break;
       }
     }
     __syncthreads();

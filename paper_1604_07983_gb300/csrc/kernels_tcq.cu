@@ -203,9 +203,18 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
   const int seg0 = ck.seg_base[0], nseg = ck.seg_base[NW] - seg0;
 
   // slab: side 1 cells then side 2 cells, 32 bytes (four spins) per cell
+  // coordinates of the next momentum to stage (slabs are issued for q_begin,
+  // q_begin + 1, ... in order)
+  int nqx = (int)(q_begin % L), nqy = (int)((q_begin / L) % L), nqz = (int)(q_begin / ((long long)L * L));
   auto issue_slabs = [&](long long q, uint4* S) {
-    const int qx = (int)(q % L), qy = (int)((q / L) % L), qz = (int)(q / ((long long)L * L));
-    const long long qm = (L - qx) % L + L * ((L - qy) % L + (long long)L * ((L - qz) % L));
+    const long long qm = (nqx ? L - nqx : 0) + L * ((nqy ? L - nqy : 0) + (long long)L * (nqz ? L - nqz : 0));
+    if (++nqx == L) {
+      nqx = 0;
+      if (++nqy == L) {
+        nqy = 0;
+        ++nqz;
+      }
+    }
     for (int i = threadIdx.x; i < 2 * n1c; i += NT)
       cp_async16t(S + i, reinterpret_cast<const char*>(FB + ((long long)(base1 + (i >> 1)) * V + q) * 4) + 16 * (i & 1));
     uint4* S2 = S + 2 * TCQ_ST;
@@ -251,21 +260,24 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
       }
       if (si >= s_end) break;
       const QuadSeg sg = SEG[si];
-      const int shape = sg.form & 3;
+      // a run with exchanged sides (bit 3) is taken back to its own shape and side order
+      const bool sw = sg.form & 8;
+      const int shape = sw ? (sg.form & 3) ^ 3 : sg.form & 3;
+      const int n1 = sw ? sg.n2 : sg.n1, n2 = sw ? sg.n1 : sg.n2;
       used |= 1u << shape;
       const int nh1 = 1 << ((shape & 1) + ((shape >> 1) & 1));
-      const int r1 = nh1 * sg.n1, r2 = (4 / nh1) * sg.n2;  // entries per shared index
-      const unsigned short* p1 = TAB + sg.t1 + (sg.kbeg + kq) * r1;
-      const unsigned short* p2 = TAB + sg.t2 + (sg.kbeg + kq) * r2;
+      const int r1 = nh1 * n1, r2 = (4 / nh1) * n2;  // entries per shared index
+      const unsigned short* p1 = TAB + (sw ? sg.t2 : sg.t1) + (sg.kbeg + kq) * r1;
+      const unsigned short* p2 = TAB + (sw ? sg.t1 : sg.t2) + (sg.kbeg + kq) * r2;
       for (int k0 = sg.kbeg; k0 < sg.kend; k0 += 8, p1 += 8 * r1, p2 += 8 * r2) {
         const bool active = k0 + kq < sg.kend;  // the four lanes of a quad agree
         const unsigned short* q1 = active ? p1 : ZROW;
         const unsigned short* q2 = active ? p2 : ZROW;
         switch (shape) {
-          case 0: tcq_step<0>(sg.n1, sg.n2, q1, q2, S1a, S2a, SC, D[0]); break;
-          case 1: tcq_step<1>(sg.n1, sg.n2, q1, q2, S1a, S2a, SC, D[1]); break;
-          case 2: tcq_step<2>(sg.n1, sg.n2, q1, q2, S1a, S2a, SC, D[2]); break;
-          default: tcq_step<3>(sg.n1, sg.n2, q1, q2, S1a, S2a, SC, D[3]); break;
+          case 0: tcq_step<0>(n1, n2, q1, q2, S1a, S2a, SC, D[0]); break;
+          case 1: tcq_step<1>(n1, n2, q1, q2, S1a, S2a, SC, D[1]); break;
+          case 2: tcq_step<2>(n1, n2, q1, q2, S1a, S2a, SC, D[2]); break;
+          default: tcq_step<3>(n1, n2, q1, q2, S1a, S2a, SC, D[3]); break;
         }
       }
     }

@@ -408,7 +408,7 @@ void build_chunks(Plan& plan) {
   };
   // one table run: a channel's terms of one fixed form (lists of whole 16-byte
   // rows), or a single term
-  struct Run { int form, n1, n2, nh1, nh2, K, local, t1, t2; };
+  struct Run { int form, n1, n2, nh1, nh2, K, local, t1, t2, swap; };
   for (const GroupHdr& g : plan.groups) {
     if (g.ncell1 > 1024 || g.ncell2 > 1024) return;
     int c = 0;
@@ -457,6 +457,12 @@ void build_chunks(Plan& plan) {
           }
           members[r].push_back(t);
         }
+        // shapes 0 and 2 run as shapes 3 and 1 with the two sides exchanged
+        // (the product then lands transposed in alpha1, alpha2): a channel's
+        // runs with exchanged sides go last, so a warp flushes at most twice
+        std::stable_sort(members.begin(), members.end(), [&](const std::vector<int>& x, const std::vector<int>& y) {
+          return (plan.terms[x[0]].shape % 2 == 0) < (plan.terms[y[0]].shape % 2 == 0);
+        });
         for (const std::vector<int>& mem : members) {
           const TermHdr& t0 = plan.terms[mem[0]];
           Run run;
@@ -466,6 +472,7 @@ void build_chunks(Plan& plan) {
           held(t0, run.nh1, run.nh2);
           run.K = 0;
           run.local = t0.pad - c;
+          run.swap = t0.shape % 2 == 0;
           std::vector<unsigned short> ents[2];
           std::vector<int> koff;
           for (int t : mem) {
@@ -558,7 +565,8 @@ void build_chunks(Plan& plan) {
         std::vector<double> scost;
         for (size_t r = 0; r < runs.size(); ++r) {
           const Run& run = runs[r];
-          const double sc = quad_step_cost(run.form, run.nh1 * run.n1 + run.nh2 * run.n2, run.nh2);
+          const double sc = quad_step_cost(run.swap ? (run.form ^ 3) : run.form, run.nh1 * run.n1 + run.nh2 * run.n2,
+                                           run.swap ? run.nh1 : run.nh2);
           for (int k = 0; k < run.K; k += 8) {
             srun.push_back((int)r);
             sk.push_back(k);
@@ -569,7 +577,8 @@ void build_chunks(Plan& plan) {
         auto add_cost = [&](int s, bool first) {  // cost of step s appended to a range
           double x = scost[s];
           if (first || srun[s] != srun[s - 1]) x += QUAD_RUN_COST;
-          if (first || runs[srun[s]].local != runs[srun[s - 1]].local) x += QUAD_FLUSH_COST;
+          if (first || runs[srun[s]].local != runs[srun[s - 1]].local || runs[srun[s]].swap != runs[srun[s - 1]].swap)
+            x += QUAD_FLUSH_COST;
           return x;
         };
         auto fill = [&](double cap, std::vector<int>* cut) {  // warps used by a greedy fill
@@ -624,14 +633,14 @@ void build_chunks(Plan& plan) {
               continue;
             }
             QuadSeg sg;
-            sg.form = run.form;
-            sg.t1 = run.t1;
-            sg.t2 = run.t2;
+            sg.form = run.swap ? (run.form ^ 3) | 8 : run.form;  // 0 <-> 3, 2 <-> 1, 4 <-> 7, 6 <-> 5
+            sg.t1 = run.swap ? run.t2 : run.t1;
+            sg.t2 = run.swap ? run.t1 : run.t2;
             sg.kbeg = sk[s];
             sg.kend = kend;
             sg.local = run.local;
-            sg.n1 = run.n1;
-            sg.n2 = run.n2;
+            sg.n1 = run.swap ? run.n2 : run.n1;
+            sg.n2 = run.swap ? run.n1 : run.n2;
             plan.quad_segs.push_back(sg);
           }
         }

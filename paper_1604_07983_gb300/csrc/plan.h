@@ -105,9 +105,13 @@ struct QuadChunkHdr {
 
 // One run of consecutive 8-index steps inside a warp's range: shared indices
 // [kbeg, kend) (kbeg a multiple of 8) of one table run, the table offsets of
-// its two gather lists inside the chunk table, the chunk-local channel and the
-// form (0..3: shape with run-time lengths; 4..7: the fixed forms (shape 0,
-// n 8/2), (1, 2/2), (2, 2/2), (3, 2/8)).
+// its two gather lists inside the chunk table (t1 for the lanes' own spin,
+// t2 for the rows they exchange), their lengths n1, n2, the chunk-local
+// channel and the form: bits 0..2 = 0..3 shape with run-time lengths, 4..7
+// the fixed forms (shape 0, n 8/2), (1, 2/2), (2, 2/2), (3, 2/8); bit 3 set =
+// sides exchanged (B2's list first: the run computes the transpose in
+// alpha1, alpha2 of a shape-0 or shape-2 term as a shape-3 or shape-1 one).
+// Only shapes 1 and 3 (forms 1, 3, 5, 7) occur.
 struct QuadSeg { int form, t1, t2, kbeg, kend, local, n1, n2; };
 
 struct Plan {

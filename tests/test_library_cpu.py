@@ -252,8 +252,9 @@ def test_three_flavours_reproduce_oracle(lib):
 def test_quad_runs_cover_every_step_once(lib):
     """The quad-lane kernels walk each chunk's table runs (a channel's terms of one fixed form back to
     back, or one term) in 8-index steps cut into 16 warp ranges: every shared index of every run is taken
-    by exactly one warp, each segment stays inside one run and names the run's form, lengths and channel,
-    and each warp's channels fit its partial-sum slots.  The runs are the terms' tables laid end to end."""
+    by exactly one warp, each segment stays inside one run and names the run's form, lengths and channel
+    (shapes 0 and 2 with the sides exchanged), and each warp's channels fit its partial-sum slots.  The runs
+    are the terms' tables laid end to end."""
     tb = nbs.plan_tables(list(range(52)))
     T, toff, segs = tb["terms"], tb["term_tab_off"], tb["quad_segs"]
     fixed = {(0, 8, 2): 4, (1, 2, 2): 5, (2, 2, 2): 6, (3, 2, 8): 7}
@@ -283,15 +284,25 @@ def test_quad_runs_cover_every_step_once(lib):
         assert sum(len(m) for m, _ in runs.values()) == len(terms_here)
         seen = {key: np.zeros(k, dtype=int) for key, (_, k) in runs.items()}
         for w in range(16):
+            keys = []
             for form, t1, t2, kbeg, kend, local, n1, n2 in segs[seg_base[w]:seg_base[w + 1]]:
+                swapped = bool(form & 8)
+                if swapped:  # shapes 0 and 2 run as 3 and 1 with B2's list first
+                    t1, t2, n1, n2 = t2, t1, n2, n1
                 members, k_tot = runs[(t1, t2)]
                 shapes = {tuple(T[m][2:5]) for m in members}
                 assert len(shapes) == 1 and len({T[m][7] for m in members}) == 1
                 shape, nn1, nn2 = shapes.pop()
-                assert (n1, n2) == (nn1, nn2) and form == fixed.get((shape, n1, n2), shape)
-                assert len(members) == 1 or form >= 4
+                assert swapped == (shape % 2 == 0)
+                want = fixed.get((shape, n1, n2), shape)
+                assert (n1, n2) == (nn1, nn2) and form == (want ^ 3 | 8 if swapped else want)
+                assert (form & 3) in (1, 3)
+                assert len(members) == 1 or want >= 4
                 assert local == T[members[0]][7] - local0
                 assert 0 <= local - cfirst[w] < out_base[w + 1] - out_base[w]
                 assert kbeg % 8 == 0 and kbeg < kend <= k_tot
                 seen[(t1, t2)][kbeg:kend] += 1
+                keys.append((local, swapped))
+            # a warp's runs visit each (channel, side order) once: one flush each
+            assert len(set(keys)) == len([k for i, k in enumerate(keys) if i == 0 or keys[i - 1] != k])
         assert all((v == 1).all() for v in seen.values())
