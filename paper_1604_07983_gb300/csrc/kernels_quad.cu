@@ -174,7 +174,7 @@ template <int NW>
 __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
     const float2* __restrict__ FB, int L, int nchunks, int qb, const QuadChunkHdr* __restrict__ chunks,
     const QuadSeg* __restrict__ segs, const int* __restrict__ group_ch, const unsigned short* __restrict__ tab,
-    const float* __restrict__ codes, int max_slot, int max_tab, float2* __restrict__ Ft) {
+    const float* __restrict__ codes, int max_slot, int max_tab, int max_segs, float2* __restrict__ Ft) {
   constexpr int NT = NW * 32;
   constexpr int slab = 2 * 2 * QUAD_ST;  // uint4 per buffer: two sides x cells x 32 bytes
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -184,6 +184,11 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
   float2* OUT = reinterpret_cast<float2*>(SB + 2 * slab);
   float* SC = reinterpret_cast<float*>(OUT + max_slot * 64);
   QuadSeg* SEG = reinterpret_cast<QuadSeg*>(SC + 64);
+  // per chunk-local channel c: its partial-sum slots SL[CS[c] .. CS[c + 1]) in
+  // warp order, and its request-order channel GC[c]
+  int* CS = reinterpret_cast<int*>(SEG + max_segs);
+  int* SL = CS + max_slot + 1;
+  int* GC = SL + max_slot;
   if (threadIdx.x < 64) {
     const float m = codes[threadIdx.x >> 1];
     SC[threadIdx.x] = (threadIdx.x & 1) ? -m : m;
@@ -196,6 +201,18 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
   const QuadChunkHdr& ck = chunks[ci];
   const int base1 = ck.base1, n1c = ck.ncell1, base2 = ck.base2, n2c = ck.ncell2;
   const int seg0 = ck.seg_base[0], nseg = ck.seg_base[NW] - seg0;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int c = 0; c < ck.nch; ++c) {
+      CS[c] = n;
+      for (int ww = 0; ww < NW; ++ww) {
+        const int r = c - ck.cfirst[ww];
+        if (r >= 0 && r < ck.out_base[ww + 1] - ck.out_base[ww]) SL[n++] = ck.out_base[ww] + r;
+      }
+      GC[c] = group_ch[ck.ch_off + c];
+    }
+    CS[ck.nch] = n;
+  }
 
   // coordinates of the next momentum to stage (slabs are issued for q_begin,
   // q_begin + 1, ... in order)
@@ -260,20 +277,16 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ck.nch * 64; i += NT) {
-      const int c = i / 64, m = i % 64;
+      const int c = i >> 6, m = i & 63;
       float2 sum = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int ww = 0; ww < NW; ++ww) {  // fixed order
-        const int r = c - ck.cfirst[ww];
-        if (r >= 0 && r < ck.out_base[ww + 1] - ck.out_base[ww]) {
-          float2& v = OUT[(ck.out_base[ww] + r) * 64 + m];
-          sum.x += v.x;
-          sum.y += v.y;
-          v = make_float2(0.f, 0.f);
-        }
+      for (int k = CS[c]; k < CS[c + 1]; ++k) {  // warp order: a fixed summation order
+        float2& v = OUT[SL[k] * 64 + m];
+        sum.x += v.x;
+        sum.y += v.y;
+        v = make_float2(0.f, 0.f);
       }
       const int spin = (m & ~3) + 2 * (m & 1) + ((m >> 1) & 1);
-      Ft[((long long)group_ch[ck.ch_off + c] * 64 + spin) * V + q] = sum;
+      Ft[((long long)GC[c] * 64 + spin) * V + q] = sum;
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
@@ -284,7 +297,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
 
 size_t qseg_smem_bytes(int max_slot, int max_tab, int max_segs) {
   return (size_t)(max_tab + QUAD_ZROW) * 2 + (size_t)2 * 2 * 2 * QUAD_ST * 16 + (size_t)max_slot * 64 * sizeof(float2) +
-         64 * sizeof(float) + (size_t)max_segs * sizeof(QuadSeg);
+         64 * sizeof(float) + (size_t)max_segs * sizeof(QuadSeg) + (size_t)(3 * max_slot + 1) * sizeof(int);
 }
 
 cudaError_t launch_contract_qseg(const float2* FB, int L, int nchunks, int qb, const void* chunks, const void* segs,
@@ -301,7 +314,7 @@ cudaError_t launch_contract_qseg(const float2* FB, int L, int nchunks, int qb, c
   if (nqb * nchunks > 2147483647LL) return cudaErrorInvalidValue;
   kern<<<(unsigned)(nqb * nchunks), NBS_QUAD_WARPS * 32, sm, st>>>(FB, L, nchunks, qb, (const QuadChunkHdr*)chunks,
                                                                    (const QuadSeg*)segs, group_ch, tab, codes,
-                                                                   max_slot, max_tab, Ft);
+                                                                   max_slot, max_tab, max_segs, Ft);
   return cudaGetLastError();
 }
 

@@ -356,19 +356,18 @@ void order_for_banks(int K, int n1, int nh1, int n2, int nh2, std::vector<unsign
 
 // Split every slab group into chunks of whole channels whose compressed
 // tables fit NBS_CHUNK_ENTRIES, and balance each chunk's items over warps.
-// Measured cost of one 8-index step of the quad-lane contraction per term
+// Measured cost of one 8-index step of the quad-lane contraction per run
 // form (SM cycles of one of 16 warps, fitted to per-warp timings of the
-// 52-channel tables at 16^3), of starting a run, and of a channel flush.
-double quad_step_cost(int form, int ent, int nh2) {
+// 52-channel tables at 16^3; shapes 0 and 2 run as their mirrors 3 and 1),
+// of starting a run, and of a channel flush.
+double quad_step_cost(int form, int ent) {
   switch (form) {
-    case 4: return 1164;
-    case 5: return 721;
-    case 6: return 807;
-    case 7: return 857;
-    default: return 580 + 30.0 * ent + 102.0 * nh2;  // run-time lengths
+    case 5: return 779;
+    case 7: return 1033;
+    default: return 747 + 46.4 * ent;  // run-time lengths
   }
 }
-constexpr double QUAD_RUN_COST = 1500, QUAD_FLUSH_COST = 340;
+constexpr double QUAD_RUN_COST = 873, QUAD_FLUSH_COST = 868;
 
 int quad_form(const TermHdr& th) {
   if ((th.shape == 0 && th.n1 == 8 && th.n2 == 2) || (th.shape == 1 && th.n1 == 2 && th.n2 == 2) ||
@@ -565,8 +564,7 @@ void build_chunks(Plan& plan) {
         std::vector<double> scost;
         for (size_t r = 0; r < runs.size(); ++r) {
           const Run& run = runs[r];
-          const double sc = quad_step_cost(run.swap ? (run.form ^ 3) : run.form, run.nh1 * run.n1 + run.nh2 * run.n2,
-                                           run.swap ? run.nh1 : run.nh2);
+          const double sc = quad_step_cost(run.swap ? (run.form ^ 3) : run.form, run.nh1 * run.n1 + run.nh2 * run.n2);
           for (int k = 0; k < run.K; k += 8) {
             srun.push_back((int)r);
             sk.push_back(k);
