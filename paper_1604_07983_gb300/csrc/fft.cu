@@ -195,9 +195,22 @@ __global__ void __launch_bounds__(NT) k_fft_yz(C<T>* __restrict__ data, long lon
   const int x0 = (int)(blockIdx.x % (L / XB)) * XB;
   if (cube >= ncubes) return;
   C<T>* g = data + cube * (long long)L * L * L * IL + (long long)x0 * IL;
-  for (int e = threadIdx.x; e < NE; e += NT) {
-    const int zy = e / RUN, r = e % RUN;
-    sm[e] = g[(long long)zy * L * IL + r];
+  if constexpr ((RUN * sizeof(C<T>)) % 16 == 0 && (L * IL * sizeof(C<T>)) % 16 == 0) {
+    // rows of RUN values start on 16-byte boundaries: copy the tile 16 bytes at a
+    // time without waiting on each load, so the whole tile is in flight at once
+    constexpr int V16 = 16 / (int)sizeof(C<T>);  // values per 16-byte piece
+    for (int e = threadIdx.x * V16; e < NE; e += NT * V16) {
+      const int zy = e / RUN, r = e % RUN;
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(sm + e);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g + (long long)zy * L * IL + r)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+  } else {
+    for (int e = threadIdx.x; e < NE; e += NT) {
+      const int zy = e / RUN, r = e % RUN;
+      sm[e] = g[(long long)zy * L * IL + r];
+    }
   }
   __syncthreads();
   for (int l = threadIdx.x; l < NLINE; l += NT) {  // y lines: (z, run offset)
