@@ -109,9 +109,12 @@ cudaError_t launch_contract_chunk2(const float2* FB, int L, int nchunks, int qb,
 // segs to the per-warp runs QuadSeg[] (plan.h), max_segs = the most runs of one
 // chunk; max_cells = the largest stored type's cell count (<= 944)
 size_t qseg_smem_bytes(int max_slot, int max_tab, int max_segs);
-cudaError_t launch_contract_qseg(const float2* FB, int L, int nchunks, int qb, const void* chunks, const void* segs,
-                                 int max_segs, const int* group_ch, const unsigned short* tab, const float* codes,
-                                 int max_cells, int max_slot, int max_tab, int max_row, float2* Ft, cudaStream_t st);
+// ncells: the stored block array's cells (the TMA tensor extent); flags: bit 1
+// set if a slab wait gave up
+cudaError_t launch_contract_qseg(const float2* FB, long long ncells, int L, int nchunks, int qb, const void* chunks,
+                                 const void* segs, int max_segs, const int* group_ch, const unsigned short* tab,
+                                 const float* codes, int max_cells, int max_slot, int max_tab, int max_row, float2* Ft,
+                                 int* flags, cudaStream_t st);
 // quad-lane tensor-core contraction (split-BF16 x 3): same arguments
 size_t tcq_smem_bytes(int max_slot, int max_tab, int max_segs);
 cudaError_t launch_contract_tcq(const float2* FB, int L, int nchunks, int qb, const void* chunks, const void* segs,

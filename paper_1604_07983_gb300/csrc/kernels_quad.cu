@@ -16,6 +16,11 @@
 // when a warp moves to another channel it sums its partial products over the
 // eight shared-index lanes and adds them to the channel's slot in shared
 // memory; the slots of all warps are added in a fixed order.
+#include <cuda.h>  // CUtensorMap (the map is encoded through the runtime's driver entry point)
+
+#include <cstdint>
+#include <cstring>
+
 #include "common.cuh"
 #include "plan.h"
 
@@ -29,6 +34,43 @@ constexpr int QUAD_ST = 944;    // cells per slab side (>= the cells of any stor
 __device__ __forceinline__ void cp_async16q(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// ---- TMA staging of the slabs -------------------------------------------------
+// The stored blocks seen as a 3-D tensor of FP32: 8 values (one cell's four
+// spins at one momentum, 32 bytes), momenta (stride 32 bytes), cells (stride
+// V * 32 bytes).  One box is 236 cells of one momentum, so four boxes fill
+// a 944-cell slab side; the x coordinate is always 0 (16-byte aligned).
+constexpr int QUAD_BOX = 236;                // cells per TMA box
+constexpr int QUAD_BOX_BYTES = QUAD_BOX * 32;
+constexpr int QUAD_WAIT_LIMIT = 1 << 20;     // mbarrier polls before a wait gives up
+
+__device__ __forceinline__ void mbar_init(unsigned addr, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(addr), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned addr, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(addr), "r"(bytes) : "memory");
+}
+// bounded wait for the phase with the given parity; false if it gave up
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity) {
+  for (int i = 0; i < QUAD_WAIT_LIMIT; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            unsigned mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::
+          "r"(dst),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+      : "memory");
 }
 
 // 2 NH consecutive 16-bit entries (shared index row, pair of i) in one load
@@ -170,18 +212,24 @@ __device__ __forceinline__ void qseg_flush(float (&acc)[32], int lane, bool swap
   for (int j = 0; j < 32; ++j) acc[j] = 0.f;
 }
 
-template <int NW>
+// TMA: slabs staged by the tensor memory accelerator (one thread issues the
+// boxes, an mbarrier per buffer counts the bytes); else 16-byte cp.async by all
+// threads.  flags: bit 1 is set if a slab wait gave up (the CTA then returns).
+template <int NW, bool TMA>
 __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
-    const float2* __restrict__ FB, int L, int nchunks, int qb, const QuadChunkHdr* __restrict__ chunks,
-    const QuadSeg* __restrict__ segs, const int* __restrict__ group_ch, const unsigned short* __restrict__ tab,
-    const float* __restrict__ codes, int max_slot, int max_tab, int max_segs, float2* __restrict__ Ft) {
+    const __grid_constant__ CUtensorMap fbmap, const float2* __restrict__ FB, int L, int nchunks, int qb,
+    const QuadChunkHdr* __restrict__ chunks, const QuadSeg* __restrict__ segs, const int* __restrict__ group_ch,
+    const unsigned short* __restrict__ tab, const float* __restrict__ codes, int max_slot, int max_tab, int max_segs,
+    float2* __restrict__ Ft, int* __restrict__ flags) {
   constexpr int NT = NW * 32;
   constexpr int slab = 2 * 2 * QUAD_ST;  // uint4 per buffer: two sides x cells x 32 bytes
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned short* TAB = reinterpret_cast<unsigned short*>(smem_raw);
+  // slabs first, on a 128-byte boundary (TMA destinations), then the rest
+  const unsigned pad = (128u - ((unsigned)__cvta_generic_to_shared(smem_raw) & 127u)) & 127u;
+  uint4* SB = reinterpret_cast<uint4*>(smem_raw + pad);
+  unsigned short* TAB = reinterpret_cast<unsigned short*>(SB + 2 * slab);
   unsigned short* ZROW = TAB + max_tab;  // max_tab % 8 == 0
-  uint4* SB = reinterpret_cast<uint4*>(smem_raw + (size_t)(max_tab + QUAD_ZROW) * 2);
-  float2* OUT = reinterpret_cast<float2*>(SB + 2 * slab);
+  float2* OUT = reinterpret_cast<float2*>(ZROW + QUAD_ZROW);
   float* SC = reinterpret_cast<float*>(OUT + max_slot * 64);
   QuadSeg* SEG = reinterpret_cast<QuadSeg*>(SC + 64);
   // per chunk-local channel c: its partial-sum slots SL[CS[c] .. CS[c + 1]) in
@@ -189,6 +237,9 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
   int* CS = reinterpret_cast<int*>(SEG + max_segs);
   int* SL = CS + max_slot + 1;
   int* GC = SL + max_slot;
+  unsigned long long* MB = reinterpret_cast<unsigned long long*>(
+      (reinterpret_cast<uintptr_t>(GC + max_slot) + 7) & ~static_cast<uintptr_t>(7));  // one mbarrier per buffer
+  const unsigned mb0 = (unsigned)__cvta_generic_to_shared(MB);
   if (threadIdx.x < 64) {
     const float m = codes[threadIdx.x >> 1];
     SC[threadIdx.x] = (threadIdx.x & 1) ? -m : m;
@@ -226,6 +277,22 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
         ++nqz;
       }
     }
+    if constexpr (TMA) {
+      if (threadIdx.x == 0) {
+        const int b = S == SB ? 0 : 1;
+        const unsigned mb = mb0 + 8u * b;
+        const int nb1 = (n1c + QUAD_BOX - 1) / QUAD_BOX, nb2 = (n2c + QUAD_BOX - 1) / QUAD_BOX;
+        // the buffer's earlier reads (generic proxy) before the async writes
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_expect_tx(mb, (unsigned)((nb1 + nb2) * QUAD_BOX_BYTES));
+        const unsigned d = (unsigned)__cvta_generic_to_shared(S);
+        for (int k = 0; k < nb1; ++k)
+          tma_load_3d(d + k * QUAD_BOX_BYTES, &fbmap, 0, (int)q, base1 + k * QUAD_BOX, mb);
+        for (int k = 0; k < nb2; ++k)
+          tma_load_3d(d + 2 * QUAD_ST * 16 + k * QUAD_BOX_BYTES, &fbmap, 0, (int)qm, base2 + k * QUAD_BOX, mb);
+      }
+      return;
+    }
     for (int i = threadIdx.x; i < 2 * n1c; i += NT)
       cp_async16q(S + i, reinterpret_cast<const char*>(FB + ((long long)(base1 + (i >> 1)) * V + q) * 4) + 16 * (i & 1));
     uint4* S2 = S + 2 * QUAD_ST;
@@ -233,6 +300,15 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
       cp_async16q(S2 + i, reinterpret_cast<const char*>(FB + ((long long)(base2 + (i >> 1)) * V + qm) * 4) + 16 * (i & 1));
   };
 
+  if constexpr (TMA) {
+    // once a CTA of this launch has given up on a slab wait, the others leave at once
+    if (__syncthreads_or(threadIdx.x == 0 && (*reinterpret_cast<volatile int*>(flags) & 2))) return;
+    if (threadIdx.x == 0) {
+      mbar_init(mb0, 1);
+      mbar_init(mb0 + 8, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+  }
   for (int i = threadIdx.x; i < ck.tab_len / 8; i += NT) cp_async16q(TAB + 8 * i, tab + ck.tab_off + 8 * i);
   for (int i = threadIdx.x; i < 2 * nseg; i += NT)
     cp_async16q(reinterpret_cast<uint4*>(SEG) + i, reinterpret_cast<const uint4*>(segs + seg0) + i);
@@ -241,6 +317,21 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
   for (int i = threadIdx.x; i < ck.nslot * 64; i += NT) OUT[i] = make_float2(0.f, 0.f);
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
+  // a slab wait that gave up: flag it, let thread 0 wait once more (bounded) for
+  // the boxes in flight, and leave together
+  auto give_up = [&](unsigned mb, unsigned parity) {
+    if (threadIdx.x == 0) {
+      atomicOr(flags, 2);
+      mbar_wait(mb, parity);
+    }
+  };
+  if constexpr (TMA) {
+    const bool ok = q_begin >= q_end || mbar_wait(mb0, 0);
+    if (__syncthreads_or(!ok)) {
+      give_up(mb0, 0);
+      return;
+    }
+  }
 
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a = lane & 3, kq = lane >> 2;
@@ -288,33 +379,82 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
       const int spin = (m & ~3) + 2 * (m & 1) + ((m >> 1) & 1);
       Ft[((long long)GC[c] * 64 + spin) * V + q] = sum;
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
+    if constexpr (TMA) {
+      // the next momentum's slabs: buffer (u + 1) & 1, its fill number (u + 1) >> 1
+      const long long u = q + 1 - q_begin;
+      const unsigned mb = mb0 + 8u * (unsigned)(u & 1), parity = (unsigned)((u >> 1) & 1);
+      const bool ok = q + 1 >= q_end || mbar_wait(mb, parity);
+      if (__syncthreads_or(!ok)) {
+        give_up(mb, parity);
+        return;
+      }
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      __syncthreads();
+    }
   }
 }
 
 }  // namespace
 
 size_t qseg_smem_bytes(int max_slot, int max_tab, int max_segs) {
-  return (size_t)(max_tab + QUAD_ZROW) * 2 + (size_t)2 * 2 * 2 * QUAD_ST * 16 + (size_t)max_slot * 64 * sizeof(float2) +
-         64 * sizeof(float) + (size_t)max_segs * sizeof(QuadSeg) + (size_t)(3 * max_slot + 1) * sizeof(int);
+  return 128 + (size_t)2 * 2 * 2 * QUAD_ST * 16 + (size_t)(max_tab + QUAD_ZROW) * 2 +
+         (size_t)max_slot * 64 * sizeof(float2) + 64 * sizeof(float) + (size_t)max_segs * sizeof(QuadSeg) +
+         (size_t)(3 * max_slot + 1) * sizeof(int) + 8 + 2 * sizeof(unsigned long long);
 }
 
-cudaError_t launch_contract_qseg(const float2* FB, int L, int nchunks, int qb, const void* chunks, const void* segs,
-                                 int max_segs, const int* group_ch, const unsigned short* tab, const float* codes,
-                                 int max_cells, int max_slot, int max_tab, int max_row, float2* Ft, cudaStream_t st) {
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+// the stored blocks [cell][site][4 spins] as a 3-D FP32 tensor (8, V, cells)
+bool encode_fb_map(CUtensorMap* map, const float2* FB, long long V, long long ncells) {
+  const EncodeTiled fn = encode_tiled();
+  if (!fn || !FB || (reinterpret_cast<uintptr_t>(FB) & 15) || V <= 0 || ncells <= 0 || V > (1LL << 31)) return false;
+  const cuuint64_t dim[3] = {8, (cuuint64_t)V, (cuuint64_t)ncells};
+  const cuuint64_t stride[2] = {32, (cuuint64_t)V * 32};
+  const cuuint32_t box[3] = {8, 1, (cuuint32_t)QUAD_BOX};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(FB), dim, stride, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t launch_contract_qseg(const float2* FB, long long ncells, int L, int nchunks, int qb, const void* chunks,
+                                 const void* segs, int max_segs, const int* group_ch, const unsigned short* tab,
+                                 const float* codes, int max_cells, int max_slot, int max_tab, int max_row, float2* Ft,
+                                 int* flags, cudaStream_t st) {
   const long long V = (long long)L * L * L;
-  if (max_row > QUAD_ZROW || max_tab % 8 || max_cells > QUAD_ST || max_cells > 1024 || max_segs < 0)
+  if (max_row > QUAD_ZROW || max_tab % 8 || max_cells > QUAD_ST || max_cells > 1024 || max_segs < 0 || !flags)
     return cudaErrorInvalidValue;
   const size_t sm = qseg_smem_bytes(max_slot, max_tab, max_segs);
-  auto kern = k_contract_qseg<NBS_QUAD_WARPS>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
   const long long nqb = (V + qb - 1) / qb;
   if (nqb * nchunks > 2147483647LL) return cudaErrorInvalidValue;
-  kern<<<(unsigned)(nqb * nchunks), NBS_QUAD_WARPS * 32, sm, st>>>(FB, L, nchunks, qb, (const QuadChunkHdr*)chunks,
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  const bool tma = encode_fb_map(&map, FB, V, ncells);
+  auto kern = tma ? k_contract_qseg<NBS_QUAD_WARPS, true> : k_contract_qseg<NBS_QUAD_WARPS, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)(nqb * nchunks), NBS_QUAD_WARPS * 32, sm, st>>>(map, FB, L, nchunks, qb, (const QuadChunkHdr*)chunks,
                                                                    (const QuadSeg*)segs, group_ch, tab, codes,
-                                                                   max_slot, max_tab, max_segs, Ft);
+                                                                   max_slot, max_tab, max_segs, Ft, flags);
   return cudaGetLastError();
 }
 

@@ -399,11 +399,11 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
                             h->chunk_st1, h->chunk_st2, h->chunk_slot, h->chunk_tab, (float2*)h->Ft.p, h->st),
          "contraction (tensor cores)");
     } else if (use_qseg) {
-      CK(launch_contract_qseg((const float2*)h->FB.p, h->L, (int)h->plan.quad_chunks.size(), h->chunk_qb,
-                              h->d_qchunks.p, h->d_qsegs.p, h->plan.max_quad_segs, (const int*)h->d_gch.p,
-                              (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
+      CK(launch_contract_qseg((const float2*)h->FB.p, h->plan.ncells, h->L, (int)h->plan.quad_chunks.size(),
+                              h->chunk_qb, h->d_qchunks.p, h->d_qsegs.p, h->plan.max_quad_segs,
+                              (const int*)h->d_gch.p, (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
                               std::max(h->chunk_st1, h->chunk_st2), h->quad_slot, h->chunk_tab, h->chunk_row,
-                              (float2*)h->Ft.p, h->st),
+                              (float2*)h->Ft.p, h->flags, h->st),
          "contraction");
     } else if (f32_chunks && h->contract_cfg == 3) {
       CK(launch_contract_chunk2((const float2*)h->FB.p, h->L, (int)h->plan.chunks.size(), h->chunk_qb,
@@ -478,6 +478,7 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
   prof_resolve(h);
   if (*h->host_flags) {
     h->blocks_t = -1;
+    if (*h->host_flags & 2) return fail(h, NBS_ETIMEOUT, "a slab copy wait in the contraction gave up");
     return fail(h, NBS_ENAN, "non-finite value in the propagators");
   }
   h->last_nch = nch;
@@ -718,6 +719,7 @@ int nbs_graph_launch(nbs_graph* graph, int wait) {
   h->blocks_t = -1;
   if (!wait) return NBS_OK;
   CK(cudaStreamSynchronize(h->st), "sync");
+  if (*h->host_flags & 2) return fail(h, NBS_ETIMEOUT, "a slab copy wait in the contraction gave up");
   if (*h->host_flags) return fail(h, NBS_ENAN, "non-finite value in the propagators");
   return NBS_OK;
 }
