@@ -117,9 +117,10 @@ cudaError_t launch_contract_qseg(const float2* FB, long long ncells, int L, int 
                                  int* flags, cudaStream_t st);
 // quad-lane tensor-core contraction (split-BF16 x 3): same arguments
 size_t tcq_smem_bytes(int max_slot, int max_tab, int max_segs);
-cudaError_t launch_contract_tcq(const float2* FB, int L, int nchunks, int qb, const void* chunks, const void* segs,
-                                int max_segs, const int* group_ch, const unsigned short* tab, const float* codes,
-                                int max_cells, int max_slot, int max_tab, int max_row, float2* Ft, cudaStream_t st);
+cudaError_t launch_contract_tcq(const float2* FB, long long ncells, int L, int nchunks, int qb, const void* chunks,
+                                const void* segs, int max_segs, const int* group_ch, const unsigned short* tab,
+                                const float* codes, int max_cells, int max_slot, int max_tab, int max_row, float2* Ft,
+                                int* flags, cudaStream_t st);
 cudaError_t launch_contract_tc(const float2* FB, int L, int nchunks, int qb, const void* chunks, const int* group_ch,
                                const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
                                const float* codes, int st1, int st2, int max_slot, int max_tab, float2* Ft,

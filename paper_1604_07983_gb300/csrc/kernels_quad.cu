@@ -16,13 +16,11 @@
 // when a warp moves to another channel it sums its partial products over the
 // eight shared-index lanes and adds them to the channel's slot in shared
 // memory; the slots of all warps are added in a fixed order.
-#include <cuda.h>  // CUtensorMap (the map is encoded through the runtime's driver entry point)
-
-#include <cstdint>
 #include <cstring>
 
 #include "common.cuh"
 #include "plan.h"
+#include "tma.cuh"
 
 namespace nbs {
 
@@ -34,43 +32,6 @@ constexpr int QUAD_ST = 944;    // cells per slab side (>= the cells of any stor
 __device__ __forceinline__ void cp_async16q(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-
-// ---- TMA staging of the slabs -------------------------------------------------
-// The stored blocks seen as a 3-D tensor of FP32: 8 values (one cell's four
-// spins at one momentum, 32 bytes), momenta (stride 32 bytes), cells (stride
-// V * 32 bytes).  One box is 236 cells of one momentum, so four boxes fill
-// a 944-cell slab side; the x coordinate is always 0 (16-byte aligned).
-constexpr int QUAD_BOX = 236;                // cells per TMA box
-constexpr int QUAD_BOX_BYTES = QUAD_BOX * 32;
-constexpr int QUAD_WAIT_LIMIT = 1 << 20;     // mbarrier polls before a wait gives up
-
-__device__ __forceinline__ void mbar_init(unsigned addr, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(addr), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned addr, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(addr), "r"(bytes) : "memory");
-}
-// bounded wait for the phase with the given parity; false if it gave up
-__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity) {
-  for (int i = 0; i < QUAD_WAIT_LIMIT; ++i) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            unsigned mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::
-          "r"(dst),
-      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
-      : "memory");
 }
 
 // 2 NH consecutive 16-bit entries (shared index row, pair of i) in one load
@@ -278,19 +239,9 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_qseg(
       }
     }
     if constexpr (TMA) {
-      if (threadIdx.x == 0) {
-        const int b = S == SB ? 0 : 1;
-        const unsigned mb = mb0 + 8u * b;
-        const int nb1 = (n1c + QUAD_BOX - 1) / QUAD_BOX, nb2 = (n2c + QUAD_BOX - 1) / QUAD_BOX;
-        // the buffer's earlier reads (generic proxy) before the async writes
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        mbar_expect_tx(mb, (unsigned)((nb1 + nb2) * QUAD_BOX_BYTES));
-        const unsigned d = (unsigned)__cvta_generic_to_shared(S);
-        for (int k = 0; k < nb1; ++k)
-          tma_load_3d(d + k * QUAD_BOX_BYTES, &fbmap, 0, (int)q, base1 + k * QUAD_BOX, mb);
-        for (int k = 0; k < nb2; ++k)
-          tma_load_3d(d + 2 * QUAD_ST * 16 + k * QUAD_BOX_BYTES, &fbmap, 0, (int)qm, base2 + k * QUAD_BOX, mb);
-      }
+      if (threadIdx.x == 0)
+        tma_issue_slabs(&fbmap, (unsigned)__cvta_generic_to_shared(S), 2 * QUAD_ST * 16, mb0 + (S == SB ? 0u : 8u),
+                        base1, n1c, (int)q, base2, n2c, (int)qm);
       return;
     }
     for (int i = threadIdx.x; i < 2 * n1c; i += NT)
@@ -403,13 +354,11 @@ size_t qseg_smem_bytes(int max_slot, int max_tab, int max_segs) {
          (size_t)(3 * max_slot + 1) * sizeof(int) + 8 + 2 * sizeof(unsigned long long);
 }
 
-namespace {
-
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-EncodeTiled encode_tiled() {
+static EncodeTiled encode_tiled() {
   static EncodeTiled fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -421,7 +370,6 @@ EncodeTiled encode_tiled() {
   return fn;
 }
 
-// the stored blocks [cell][site][4 spins] as a 3-D FP32 tensor (8, V, cells)
 bool encode_fb_map(CUtensorMap* map, const float2* FB, long long V, long long ncells) {
   const EncodeTiled fn = encode_tiled();
   if (!fn || !FB || (reinterpret_cast<uintptr_t>(FB) & 15) || V <= 0 || ncells <= 0 || V > (1LL << 31)) return false;
@@ -433,8 +381,6 @@ bool encode_fb_map(CUtensorMap* map, const float2* FB, long long V, long long nc
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
-
-}  // namespace
 
 cudaError_t launch_contract_qseg(const float2* FB, long long ncells, int L, int nchunks, int qb, const void* chunks,
                                  const void* segs, int max_segs, const int* group_ch, const unsigned short* tab,

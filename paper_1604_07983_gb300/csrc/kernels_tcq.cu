@@ -20,8 +20,11 @@
 // run-time gather lengths keeps the loop inside the instruction cache.
 #include <cuda_bf16.h>
 
+#include <cstring>
+
 #include "common.cuh"
 #include "plan.h"
+#include "tma.cuh"
 
 namespace nbs {
 
@@ -175,18 +178,23 @@ __device__ __forceinline__ void tcq_flush_all(float (&D)[4][2][4], unsigned used
   if (used & 8) tcq_flush<3>(D[3], lane, slot);
 }
 
-template <int NW>
+// TMA: slabs staged by the tensor memory accelerator (tma.cuh); else 16-byte
+// cp.async by all threads.  flags: bit 1 is set if a slab wait gave up.
+template <int NW, bool TMA>
 __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
-    const float2* __restrict__ FB, int L, int nchunks, int qb, const QuadChunkHdr* __restrict__ chunks,
-    const QuadSeg* __restrict__ segs, const int* __restrict__ group_ch, const unsigned short* __restrict__ tab,
-    const float* __restrict__ codes, int max_slot, int max_tab, int max_segs, float2* __restrict__ Ft) {
+    const __grid_constant__ CUtensorMap fbmap, const float2* __restrict__ FB, int L, int nchunks, int qb,
+    const QuadChunkHdr* __restrict__ chunks, const QuadSeg* __restrict__ segs, const int* __restrict__ group_ch,
+    const unsigned short* __restrict__ tab, const float* __restrict__ codes, int max_slot, int max_tab, int max_segs,
+    float2* __restrict__ Ft, int* __restrict__ flags) {
   constexpr int NT = NW * 32;
   constexpr int slab = 2 * 2 * TCQ_ST;  // uint4 per buffer: two sides x cells x 32 bytes
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned short* TAB = reinterpret_cast<unsigned short*>(smem_raw);
+  // slabs first, on a 128-byte boundary (TMA destinations), then the rest
+  const unsigned pad = (128u - ((unsigned)__cvta_generic_to_shared(smem_raw) & 127u)) & 127u;
+  uint4* SB = reinterpret_cast<uint4*>(smem_raw + pad);
+  unsigned short* TAB = reinterpret_cast<unsigned short*>(SB + 2 * slab);
   unsigned short* ZROW = TAB + max_tab;  // max_tab % 8 == 0
-  uint4* SB = reinterpret_cast<uint4*>(smem_raw + (size_t)(max_tab + TCQ_ZROW) * 2);
-  float2* OUT = reinterpret_cast<float2*>(SB + 2 * slab);
+  float2* OUT = reinterpret_cast<float2*>(ZROW + TCQ_ZROW);
   float* SC = reinterpret_cast<float*>(OUT + max_slot * 64);
   QuadSeg* SEG = reinterpret_cast<QuadSeg*>(SC + 64);
   // per chunk-local channel c: its partial-sum slots SL[CS[c] .. CS[c + 1]) in
@@ -194,6 +202,9 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
   int* CS = reinterpret_cast<int*>(SEG + max_segs);
   int* SL = CS + max_slot + 1;
   int* GC = SL + max_slot;
+  unsigned long long* MB = reinterpret_cast<unsigned long long*>(
+      (reinterpret_cast<uintptr_t>(GC + max_slot) + 7) & ~static_cast<uintptr_t>(7));  // one mbarrier per buffer
+  const unsigned mb0 = (unsigned)__cvta_generic_to_shared(MB);
   if (threadIdx.x < 64) {
     const float m = codes[threadIdx.x >> 1];
     SC[threadIdx.x] = (threadIdx.x & 1) ? -m : m;
@@ -232,6 +243,12 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
         ++nqz;
       }
     }
+    if constexpr (TMA) {
+      if (threadIdx.x == 0)
+        tma_issue_slabs(&fbmap, (unsigned)__cvta_generic_to_shared(S), 2 * TCQ_ST * 16, mb0 + (S == SB ? 0u : 8u),
+                        base1, n1c, (int)q, base2, n2c, (int)qm);
+      return;
+    }
     for (int i = threadIdx.x; i < 2 * n1c; i += NT)
       cp_async16t(S + i, reinterpret_cast<const char*>(FB + ((long long)(base1 + (i >> 1)) * V + q) * 4) + 16 * (i & 1));
     uint4* S2 = S + 2 * TCQ_ST;
@@ -239,6 +256,15 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
       cp_async16t(S2 + i, reinterpret_cast<const char*>(FB + ((long long)(base2 + (i >> 1)) * V + qm) * 4) + 16 * (i & 1));
   };
 
+  if constexpr (TMA) {
+    // once a CTA of this launch has given up on a slab wait, the others leave at once
+    if (__syncthreads_or(threadIdx.x == 0 && (*reinterpret_cast<volatile int*>(flags) & 2))) return;
+    if (threadIdx.x == 0) {
+      mbar_init(mb0, 1);
+      mbar_init(mb0 + 8, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+  }
   for (int i = threadIdx.x; i < ck.tab_len / 8; i += NT) cp_async16t(TAB + 8 * i, tab + ck.tab_off + 8 * i);
   for (int i = threadIdx.x; i < 2 * nseg; i += NT)
     cp_async16t(reinterpret_cast<uint4*>(SEG) + i, reinterpret_cast<const uint4*>(segs + seg0) + i);
@@ -247,6 +273,21 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
   for (int i = threadIdx.x; i < ck.nslot * 64; i += NT) OUT[i] = make_float2(0.f, 0.f);
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
+  // a slab wait that gave up: flag it, let thread 0 wait once more (bounded) for
+  // the boxes in flight, and leave together
+  auto give_up = [&](unsigned mb, unsigned parity) {
+    if (threadIdx.x == 0) {
+      atomicOr(flags, 2);
+      mbar_wait(mb, parity);
+    }
+  };
+  if constexpr (TMA) {
+    const bool ok = q_begin >= q_end || mbar_wait(mb0, 0);
+    if (__syncthreads_or(!ok)) {
+      give_up(mb0, 0);
+      return;
+    }
+  }
 
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a = lane & 3, kq = lane >> 2;
@@ -311,33 +352,49 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
       const int spin = (m & ~3) + 2 * (m & 1) + ((m >> 1) & 1);
       Ft[((long long)GC[c] * 64 + spin) * V + q] = sum;
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
+    if constexpr (TMA) {
+      // the next momentum's slabs: buffer (u + 1) & 1, its fill number (u + 1) >> 1
+      const long long u = q + 1 - q_begin;
+      const unsigned mb = mb0 + 8u * (unsigned)(u & 1), parity = (unsigned)((u >> 1) & 1);
+      const bool ok = q + 1 >= q_end || mbar_wait(mb, parity);
+      if (__syncthreads_or(!ok)) {
+        give_up(mb, parity);
+        return;
+      }
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      __syncthreads();
+    }
   }
 }
 
 }  // namespace
 
 size_t tcq_smem_bytes(int max_slot, int max_tab, int max_segs) {
-  return (size_t)(max_tab + TCQ_ZROW) * 2 + (size_t)2 * 2 * 2 * TCQ_ST * 16 + (size_t)max_slot * 64 * sizeof(float2) +
-         64 * sizeof(float) + (size_t)max_segs * sizeof(QuadSeg) + (size_t)(3 * max_slot + 1) * sizeof(int);
+  return 128 + (size_t)2 * 2 * 2 * TCQ_ST * 16 + (size_t)(max_tab + TCQ_ZROW) * 2 +
+         (size_t)max_slot * 64 * sizeof(float2) + 64 * sizeof(float) + (size_t)max_segs * sizeof(QuadSeg) +
+         (size_t)(3 * max_slot + 1) * sizeof(int) + 8 + 2 * sizeof(unsigned long long);
 }
 
-cudaError_t launch_contract_tcq(const float2* FB, int L, int nchunks, int qb, const void* chunks, const void* segs,
-                                int max_segs, const int* group_ch, const unsigned short* tab, const float* codes,
-                                int max_cells, int max_slot, int max_tab, int max_row, float2* Ft, cudaStream_t st) {
+cudaError_t launch_contract_tcq(const float2* FB, long long ncells, int L, int nchunks, int qb, const void* chunks,
+                                const void* segs, int max_segs, const int* group_ch, const unsigned short* tab,
+                                const float* codes, int max_cells, int max_slot, int max_tab, int max_row, float2* Ft,
+                                int* flags, cudaStream_t st) {
   const long long V = (long long)L * L * L;
-  if (max_row > TCQ_ZROW || max_tab % 8 || max_cells > TCQ_ST || max_cells > 1024 || max_segs < 0)
+  if (max_row > TCQ_ZROW || max_tab % 8 || max_cells > TCQ_ST || max_cells > 1024 || max_segs < 0 || !flags)
     return cudaErrorInvalidValue;
   const size_t sm = tcq_smem_bytes(max_slot, max_tab, max_segs);
-  auto kern = k_contract_tcq<NBS_QUAD_WARPS>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
   const long long nqb = (V + qb - 1) / qb;
   if (nqb * nchunks > 2147483647LL) return cudaErrorInvalidValue;
-  kern<<<(unsigned)(nqb * nchunks), NBS_QUAD_WARPS * 32, sm, st>>>(FB, L, nchunks, qb, (const QuadChunkHdr*)chunks,
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  const bool tma = encode_fb_map(&map, FB, V, ncells);
+  auto kern = tma ? k_contract_tcq<NBS_QUAD_WARPS, true> : k_contract_tcq<NBS_QUAD_WARPS, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)(nqb * nchunks), NBS_QUAD_WARPS * 32, sm, st>>>(map, FB, L, nchunks, qb, (const QuadChunkHdr*)chunks,
                                                                   (const QuadSeg*)segs, group_ch, tab, codes, max_slot,
-                                                                  max_tab, max_segs, Ft);
+                                                                  max_tab, max_segs, Ft, flags);
   return cudaGetLastError();
 }
 

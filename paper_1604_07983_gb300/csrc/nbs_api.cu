@@ -385,11 +385,11 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
     const bool f32_chunks = sizeof(T) == 4 && h->plan.chunks_ok;
     const bool use_qseg = f32_chunks && h->contract_cfg == 0;
     if (h->mode == NBS_BF16X3 && h->plan.chunks_ok && h->contract_cfg != 2) {
-      CK(launch_contract_tcq((const float2*)h->FB.p, h->L, (int)h->plan.quad_chunks.size(), h->chunk_qb,
-                             h->d_qchunks.p, h->d_qsegs.p, h->plan.max_quad_segs, (const int*)h->d_gch.p,
-                             (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
+      CK(launch_contract_tcq((const float2*)h->FB.p, h->plan.ncells, h->L, (int)h->plan.quad_chunks.size(),
+                             h->chunk_qb, h->d_qchunks.p, h->d_qsegs.p, h->plan.max_quad_segs,
+                             (const int*)h->d_gch.p, (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
                              std::max(h->chunk_st1, h->chunk_st2), h->quad_slot, h->chunk_tab, h->chunk_row,
-                             (float2*)h->Ft.p, h->st),
+                             (float2*)h->Ft.p, h->flags, h->st),
          "contraction (tensor cores)");
     } else if (h->mode == NBS_BF16X3) {
       if (!h->plan.chunks_ok) return fail(h, NBS_EINVAL, "BF16X3 needs channel tables that fit the chunk kernel");
