@@ -36,7 +36,7 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes per momentum of the FP32 contraction kernels, from one ncu capture of
 # `python bench.py --L 16 --T 2 --steps 1 --warmup 1 --e2e-steps 1 --no-cpu-baseline`
 # (dram__bytes_read.sum + dram__bytes_write.sum / 4096 momenta; profiles/k_contract_16cube_fp32.md)
-DRAM_BYTES_PER_Q = {}
+DRAM_BYTES_PER_Q = {"k_contract_qseg": 1.255847e9 / 4096}
 
 
 def parse():
