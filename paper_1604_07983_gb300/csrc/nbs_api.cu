@@ -97,6 +97,7 @@ struct nbs_ctx {
   int blocks_t = -1, blocks_mode = -1, blocks_gen = -1;
   int last_nch = 0;
   int contract_cfg = 0;  // NBS_PARAM_CONTRACT_CFG, 0 = default
+  int smem_optin = 0;    // the device's shared memory per block (opt-in)
 
   // profiling: CUDA events around each stage, resolved after the final sync
   bool prof = false;
@@ -383,8 +384,12 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
     cudaEvent_t e3 = stage_begin(h);
     // default in FP32: the quad-lane chunk kernel when the tables fit; FP64: the thread-per-momentum kernel
     const bool f32_chunks = sizeof(T) == 4 && h->plan.chunks_ok;
-    const bool use_qseg = f32_chunks && h->contract_cfg == 0;
-    if (h->mode == NBS_BF16X3 && h->plan.chunks_ok && h->contract_cfg != 2) {
+    // the quad-lane kernels: where their shared memory (table, slabs, slots, runs) fits the device
+    const bool quad_fits = h->plan.chunks_ok &&
+                           qseg_smem_bytes(h->quad_slot, h->chunk_tab, h->plan.max_quad_segs) <= (size_t)h->smem_optin &&
+                           tcq_smem_bytes(h->quad_slot, h->chunk_tab, h->plan.max_quad_segs) <= (size_t)h->smem_optin;
+    const bool use_qseg = f32_chunks && h->contract_cfg == 0 && quad_fits;
+    if (h->mode == NBS_BF16X3 && quad_fits && h->contract_cfg != 2) {
       CK(launch_contract_tcq((const float2*)h->FB.p, h->plan.ncells, h->L, (int)h->plan.quad_chunks.size(),
                              h->chunk_qb, h->d_qchunks.p, h->d_qsegs.p, h->plan.max_quad_segs,
                              (const int*)h->d_gch.p, (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
@@ -405,7 +410,7 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
                               std::max(h->chunk_st1, h->chunk_st2), h->quad_slot, h->chunk_tab, h->chunk_row,
                               (float2*)h->Ft.p, h->flags, h->st),
          "contraction");
-    } else if (f32_chunks && h->contract_cfg == 3) {
+    } else if (f32_chunks && (h->contract_cfg == 3 || h->contract_cfg == 0)) {
       CK(launch_contract_chunk2((const float2*)h->FB.p, h->L, (int)h->plan.chunks.size(), h->chunk_qb,
                                 h->d_chunks.p, (const int*)h->d_gch.p, (const int*)h->d_citems.p,
                                 (const DevTerm*)h->d_terms.p, (const int*)h->d_ctoff.p,
@@ -517,6 +522,10 @@ int nbs_create(nbs_ctx** out, int L, int T, int flavours) {
   h->have.assign(T, -1);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "cudaGetDevice"); }
+  if ((e = cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device)) != cudaSuccess) {
+    delete h;
+    return cuda_fail(nullptr, e, "shared memory limit");
+  }
   if ((e = fft_init()) != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "FFT twiddles"); }
   if ((e = cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking)) != cudaSuccess) {
     delete h;

@@ -306,3 +306,18 @@ def test_quad_runs_cover_every_step_once(lib):
             # a warp's runs visit each (channel, side order) once: one flush each
             assert len(set(keys)) == len([k for i, k in enumerate(keys) if i == 0 or keys[i - 1] != k])
         assert all((v == 1).all() for v in seen.values())
+
+
+@pytest.mark.parametrize("ids", [list(range(52)), list(range(208)), [0], [24, 25, 51], list(range(0, 208, 5))])
+def test_quad_kernels_fit_one_block_of_shared_memory(lib, ids):
+    """The quad-lane kernels hold a chunk's table and runs, two double-buffered slabs of 2 x 944 cells, the
+    partial-sum slots and the per-channel slot lists in one block's shared memory; for the channel sets used
+    here that fits a GB300 block (227 KB), so they run instead of the pair-lane fallback."""
+    tb = nbs.plan_tables(ids)
+    qc = tb["quad_chunks"]
+    assert len(qc) > 0
+    max_tab, max_slot = int(qc[:, 7].max()), int(qc[:, 8].max())
+    max_segs = max(int(q[43 + 16] - q[43]) for q in qc)
+    smem = 128 + 2 * 2 * 2 * 944 * 16 + (max_tab + 128) * 2 + max_slot * 64 * 8 + 64 * 4 + max_segs * 32 + \
+        (3 * max_slot + 1) * 4 + 8 + 16
+    assert smem <= 227 * 1024, smem
