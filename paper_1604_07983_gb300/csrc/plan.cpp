@@ -362,12 +362,12 @@ void order_for_banks(int K, int n1, int nh1, int n2, int nh2, std::vector<unsign
 // of starting a run, and of a channel flush.
 double quad_step_cost(int form, int ent) {
   switch (form) {
-    case 5: return 781;
-    case 7: return 1082;
-    default: return 846 + 47.5 * ent;  // run-time lengths
+    case 5: return 799;
+    case 7: return 1035;
+    default: return 926 + 43.0 * ent;  // run-time lengths
   }
 }
-constexpr double QUAD_RUN_COST = 667, QUAD_FLUSH_COST = 975;
+constexpr double QUAD_RUN_COST = 671, QUAD_FLUSH_COST = 893;
 
 int quad_form(const TermHdr& th) {
   if ((th.shape == 0 && th.n1 == 8 && th.n2 == 2) || (th.shape == 1 && th.n1 == 2 && th.n2 == 2) ||
