@@ -228,13 +228,17 @@ __global__ void __launch_bounds__(256) k_blocks_tiled(const C<T>* __restrict__ P
     const int st = it % TS, g = it / TS;
     const int code = cells[g];
     const int key = code & 2047;
-    const int y[3] = {key % 12, (key / 12) % 12, key / 144};
+    const int y0 = key % 12, y1 = (key / 12) % 12, y2 = key / 144;
     const TypeRecipe& R = rs.t[code >> 11];
     C<T> out[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
     for (int t = 0; t < R.nterms; ++t) {
       const int pat = R.pat[t], arg = R.arg[t];
       const T coef = (T)R.coef[t];
-      const int j1 = y[arg & 3], j2 = y[(arg >> 2) & 3], j3 = y[(arg >> 4) & 3];
+      // positions a0, a1, a2 of the normal block's arguments among (y0, y1, y2), by selects
+      const int a0 = arg & 3, a1 = (arg >> 2) & 3, a2 = (arg >> 4) & 3;
+      const int j1 = a0 == 0 ? y0 : (a0 == 1 ? y1 : y2);
+      const int j2 = a1 == 0 ? y0 : (a1 == 1 ? y1 : y2);
+      const int j3 = a2 == 0 ? y0 : (a2 == 1 ? y1 : y2);
       const int d = pat / NF, f3 = pat % NF;
       const C<T>* S3 = Ps + f3 * 144 * TS + st;
       const C<T>* q = Qs + ((d * 3) * 144 + j1 * 12 + j2) * TS + st;
