@@ -155,17 +155,32 @@ __global__ void __launch_bounds__(256) k_fft_strided(C<T>* __restrict__ data, lo
 // lines along x: IL interleaved lines per row of L*IL contiguous elements
 // (IL = 4 for blocks stored [cell][site][alpha]); NT lines per block staged
 // through shared memory, line t of a block = (row t / IL, offset t % IL).
+// FP32 with four interleaved values: rows padded by 4 (16-byte aligned rows, and
+// the lines of a warp fall on distinct bank pairs); otherwise by 1
+template <typename T, int IL>
+constexpr int contig_pad() { return (sizeof(C<T>) == 8 && IL == 4) ? 4 : 1; }
+
 template <typename T, int L, int DIR, int NT, int IL>
 __global__ void __launch_bounds__(NT) k_fft_contig(C<T>* __restrict__ data, long long nlines) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
-  constexpr int RL = L * IL;      // row length
-  constexpr int RP = RL + 1;      // padded row
+  constexpr int RL = L * IL;                        // row length
+  constexpr int RP = RL + contig_pad<T, IL>();      // padded row
   const long long l0 = (long long)blockIdx.x * NT;  // NT is a multiple of IL
   const int nl = (int)min((long long)NT, nlines - l0);
   const int nrow = nl / IL;
   C<T>* g = data + (l0 / IL) * RL;
-  for (int e = threadIdx.x; e < nrow * RL; e += NT) sm[(e / RL) * RP + (e % RL)] = g[e];
+  if constexpr ((RP * sizeof(C<T>)) % 16 == 0 && (RL * sizeof(C<T>)) % 16 == 0) {
+    // whole 16-byte pieces on both sides: copy without waiting on each load
+    constexpr int V16 = 16 / (int)sizeof(C<T>);
+    for (int e = threadIdx.x * V16; e < nrow * RL; e += NT * V16) {
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(sm + (e / RL) * RP + (e % RL));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g + e) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+  } else {
+    for (int e = threadIdx.x; e < nrow * RL; e += NT) sm[(e / RL) * RP + (e % RL)] = g[e];
+  }
   __syncthreads();
   if (threadIdx.x < nl) {
     C<T>* row = sm + (threadIdx.x / IL) * RP + (threadIdx.x % IL);
@@ -254,7 +269,7 @@ cudaError_t run3d(C<T>* data, long long nbatch, int sb, cudaStream_t st) {
   if (nlines == 0 || L == 1) return cudaSuccess;
   {
     constexpr int NT = 64;
-    size_t sm = (size_t)(NT / IL) * (L * IL + 1) * sizeof(C<T>);
+    size_t sm = (size_t)(NT / IL) * (L * IL + contig_pad<T, IL>()) * sizeof(C<T>);
     auto kern = k_fft_contig<T, L, DIR, NT, IL>;
     if (sm > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
