@@ -321,3 +321,120 @@ def test_quad_kernels_fit_one_block_of_shared_memory(lib, ids):
     smem = 128 + 2 * 2 * 2 * 944 * 16 + (max_tab + 128) * 2 + max_slot * 64 * 8 + 64 * 4 + max_segs * 32 + \
         (3 * max_slot + 1) * 4 + 8 + 16
     assert smem <= 227 * 1024, smem
+
+
+def _halfwarp_passes(tb):
+    """Shared-memory passes of the quad kernels' gathers under the bank model the compiler orders for: per
+    entry slot, the four consecutive shared indices of a half-warp read 32-byte cell rows that take one pass
+    per cell of the most frequent (cell mod 4), identical cells counting once.  Returns (passes, ideal)."""
+    tab, T, toff, qc, items = tb["chunk_tab"], tb["terms"], tb["term_tab_off"], tb["chunks"], tb["chunk_items"]
+    passes = ideal = 0
+    seen = set()
+    for ck in qc:
+        tab_off, item_off, nit = ck[6], ck[8], ck[10 + 8]
+        for t in sorted(set(int(x) for x in items[item_off:item_off + nit, 0])):
+            ch, K, shape, n1, n2 = T[t][:5]
+            nh1 = 1 << ((shape & 1) + ((shape >> 1) & 1))
+            for side, (nn, nh) in enumerate(((n1, nh1), (n2, 4 // nh1))):
+                o = tab_off + toff[t][side]
+                if (o, side) in seen:
+                    continue
+                seen.add((o, side))
+                e = tab[o:o + K * nn * nh].astype(np.int64).reshape(K, nn * nh)
+                for g in range(0, K, 4):
+                    for j in range(nn * nh):
+                        cells = set(int(c) & 1023 for c in e[g:g + 4, j])
+                        passes += max(sum(1 for c in cells if c % 4 == r) for r in range(4))
+                        ideal += 1
+    return passes, ideal
+
+
+def test_gather_tables_are_ordered_for_the_banks(lib):
+    """The compiler groups each table run's shared indices four at a time so that a half-warp's gathers hit
+    distinct bank groups where it can: the 52-channel tables need at most 1.3x the conflict-free number of
+    shared-memory passes (the unordered tables needed about 2.6x)."""
+    passes, ideal = _halfwarp_passes(nbs.plan_tables(list(range(52))))
+    assert passes <= 1.3 * ideal, (passes, ideal)
+
+
+def test_quad_warp_split_is_balanced_under_its_cost_model(lib):
+    """Each chunk's steps are cut into 16 warp ranges whose largest cost (per-form step costs plus a cost per
+    run start and per flush, the compiler's model) is within 10 % of the mean over the chunks' warps."""
+    tb = nbs.plan_tables(list(range(52)))
+    qc, segs = tb["quad_chunks"], tb["quad_segs"]
+    worst = mean = 0.0
+    for q in qc:
+        costs = []
+        for w in range(16):
+            x, cur = 0.0, None
+            for form, t1, t2, kb, ke, local, n1, n2 in segs[q[43 + w]:q[43 + w + 1]]:
+                sh = form & 3
+                nh1 = 1 << ((sh & 1) + ((sh >> 1) & 1))
+                ent = nh1 * n1 + (4 // nh1) * n2
+                step = {5: 799.0, 7: 1035.0}.get(form & 7, 926.0 + 43.0 * ent)
+                x += ((ke - kb + 7) // 8) * step + 671.0
+                if (local, form >> 3) != cur:
+                    x += 893.0
+                    cur = (local, form >> 3)
+            costs.append(x)
+        worst += max(costs)
+        mean += sum(costs) / 16
+    assert worst <= 1.10 * mean, worst / mean
+
+
+def _held(shape):
+    nh1 = 1 << ((shape & 1) + ((shape >> 1) & 1))
+    return nh1, 4 // nh1
+
+
+def _s_index(shape, h1, h2):  # alpha3 + 2 alpha4 of a product, by the term's shape
+    return {0: h2, 3: h1, 1: h1 + 2 * h2, 2: h2 + 2 * h1}[shape]
+
+
+@pytest.mark.parametrize("ids", [list(range(52)), [0, 17, 47]])
+def test_quad_runs_reproduce_the_term_products(lib, ids):
+    """The quad-lane kernels' walk of the compiled runs, emulated in FP64 on random slab values (one momentum):
+    lane spin a gathers its own list, the exchanged list's rows are taken for every alpha, runs with exchanged
+    sides (shapes 0 and 2 as 3 and 1) read B2's list first and flush transposed in (alpha1, alpha2), and the s
+    index follows the run's shape.  Every channel equals the plain sum over its terms of E1 E2 built from the
+    uncompressed gather lists."""
+    tb = nbs.plan_tables(ids)
+    T, codes, tab = tb["terms"], tb["codes"], tb["chunk_tab"]
+    rng = np.random.default_rng(7)
+    ncells = int(tb["cells"].shape[0])
+    A = rng.standard_normal((ncells, 4)) + 1j * rng.standard_normal((ncells, 4))  # B1's blocks at q
+    B = rng.standard_normal((ncells, 4)) + 1j * rng.standard_normal((ncells, 4))  # B2's blocks at -q
+    nch = len(ids)
+    want = np.zeros((nch, 4, 4, 4), complex)
+    for t in range(len(T)):
+        ch, K, shape, n1, n2, off1, off2 = (int(x) for x in T[t][:7])
+        nh1, nh2 = _held(shape)
+        c1 = tb["ent1_cell"][off1:off1 + K * n1 * nh1].reshape(K, n1, nh1)
+        f1 = tb["ent1_coef"][off1:off1 + K * n1 * nh1].reshape(K, n1, nh1)
+        c2 = tb["ent2_cell"][off2:off2 + K * n2 * nh2].reshape(K, n2, nh2)
+        f2 = tb["ent2_coef"][off2:off2 + K * n2 * nh2].reshape(K, n2, nh2)
+        E1 = np.einsum("kih,kiha->kha", f1, A[c1])  # [xi][h1][alpha1]
+        E2 = np.einsum("kih,kiha->kha", f2, B[c2])
+        for h1 in range(nh1):
+            for h2 in range(nh2):
+                want[ch, :, :, _s_index(shape, h1, h2)] += np.einsum("ka,kb->ab", E1[:, h1], E2[:, h2])
+    got = np.zeros_like(want)
+    for ck, q in zip(tb["chunks"], tb["quad_chunks"]):
+        base1, base2, ch_off, tab_off = ck[0], ck[2], ck[4], ck[6]
+        for w in range(16):
+            for form, t1, t2, kb, ke, local, n1, n2 in tb["quad_segs"][q[43 + w]:q[43 + w + 1]]:
+                swapped, shape = bool(form & 8), int(form & 3)
+                nh1, nh2 = _held(shape)
+                Sa, ba, Sb, bb = (B, base2, A, base1) if swapped else (A, base1, B, base2)
+                def gather(off, n, nh, S, base):
+                    e = tab[tab_off + off + kb * n * nh: tab_off + off + ke * n * nh].astype(np.int64)
+                    e = e.reshape(ke - kb, n, nh)
+                    c = codes[e >> 11] * np.where(e & 1024, -1.0, 1.0)
+                    return np.einsum("kih,kiha->kha", c, S[base + (e & 1023)])
+                Eo, Ex = gather(t1, n1, nh1, Sa, ba), gather(t2, n2, nh2, Sb, bb)
+                ch = tb["group_ch"][ch_off + local]
+                for h1 in range(nh1):
+                    for h2 in range(nh2):
+                        P = np.einsum("ka,kb->ab", Eo[:, h1], Ex[:, h2])  # [own spin][exchanged spin]
+                        got[ch, :, :, _s_index(shape, h1, h2)] += P.T if swapped else P
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
