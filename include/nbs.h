@@ -113,7 +113,10 @@ int nbs_blocks(nbs_ctx* h, int t);
  *   [n_channels][t_end - t_begin][a1][a2][a3][a4][z][y][x]
  * (a3, a4 in {0, 1} relative to the id's source spin pair)
  * on the device (out_on_device = 1) or on the host (0; pinned memory is
- * copied asynchronously per timeslice).  Returns when `out` is complete. */
+ * copied asynchronously per timeslice).  Returns when `out` is complete.
+ * NBS_ENAN if a propagator held a non-finite value; NBS_ETIMEOUT if a
+ * bounded wait of the contraction on its TMA slab copies gave up (the
+ * output is then incomplete; the context stays usable). */
 int nbs_correlate(nbs_ctx* h, const int* channel_ids, int n_channels,
                   int t_begin, int t_end, void* out, int out_on_device);
 
@@ -133,7 +136,8 @@ int nbs_correlate(nbs_ctx* h, const int* channel_ids, int n_channels,
  * nbs_graph_launch returns NBS_ESTATE if the context's buffers were
  * reallocated (a later call with more channels or another precision) or a
  * timeslice's storage type changed since the capture, NBS_ENAN after a
- * waited replay whose propagators held a non-finite value.  wait = 0 returns
+ * waited replay whose propagators held a non-finite value, NBS_ETIMEOUT
+ * after a waited replay in which a contraction's slab wait gave up.  wait = 0 returns
  * after the launch; synchronise the context's stream before reading `out`. */
 int nbs_graph_capture(nbs_ctx* h, const int* channel_ids, int n_channels, int t_begin, int t_end,
                       void* out, nbs_graph** graph);
