@@ -3,8 +3,9 @@
 //
 // A CTA of 16 warps keeps one chunk of channels' compressed gather tables in
 // shared memory and sweeps a block of momenta, staging the two momentum slabs
-// of each q (B1's stored type at q, B2's at -q) with cp.async into a double
-// buffer.  Inside a warp, lane 4 kq + a owns shared index k0 + kq of the
+// of each q (B1's stored type at q, B2's at -q) into a double buffer with TMA
+// boxes issued by one thread (tma.cuh; 16-byte cp.async by all threads where
+// the tensor map cannot be encoded).  Inside a warp, lane 4 kq + a owns shared index k0 + kq of the
 // current 8-index step and spin a: it builds E1[alpha1 = a][h1] and
 // E2[alpha2 = a][h2] (one 8-byte load and two FMAs per gather entry), takes
 // the other three alpha2 rows of E2 from the lanes of its quad by warp
