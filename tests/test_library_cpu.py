@@ -391,7 +391,7 @@ def _s_index(shape, h1, h2):  # alpha3 + 2 alpha4 of a product, by the term's sh
     return {0: h2, 3: h1, 1: h1 + 2 * h2, 2: h2 + 2 * h1}[shape]
 
 
-@pytest.mark.parametrize("ids", [list(range(52)), [0, 17, 47]])
+@pytest.mark.parametrize("ids", [list(range(52)), [0, 17, 47], [5, 60, 130, 199, 207], [51, 3, 29, 104, 8]])
 def test_quad_runs_reproduce_the_term_products(lib, ids):
     """The quad-lane kernels' walk of the compiled runs, emulated in FP64 on random slab values (one momentum):
     lane spin a gathers its own list, the exchanged list's rows are taken for every alpha, runs with exchanged
