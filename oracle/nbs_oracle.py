@@ -357,6 +357,102 @@ def zero_momentum(channel, props: dict, L: int, block=(0, 0)) -> np.ndarray:
     return F
 
 
+class PhaseSums:
+    """Phase-weighted site sums of the normal blocks, sum_x e^{i sign 2 pi n.x / L} N^m(x), per monomial.
+
+    For a momentum q = 2 pi n / L the correlation theorem of Eq. (2.6) gives
+        sum_r e^{-i q.r} F(r) = sum_terms (sum_Y e^{-i q.Y} E1(Y)) (sum_X e^{+i q.X} E2(X)),
+    and an effective block is linear in the normal block of each site (the source tensor of Eq. (2.4)
+    acts site by site, Eq. (2.7)), so sum_x w(x) E(x) is the effective block built from
+    sum_x w(x) N(x).  The sums are accumulated over chunks of sites, so no full-volume normal block is
+    held; each one is returned as a one-site block [1, 4, 4, 3, 4, 3, 4, 3] that effective_block()
+    takes in place of the per-site blocks.
+    """
+
+    def __init__(self, props: dict, L: int, n_list, chunk: int = 1024):
+        self.props, self.L, self.chunk = props, L, chunk
+        self.n_list = [tuple(int(v) for v in n) for n in n_list]
+        self.cache: dict[str, dict] = {}
+
+    def _fill(self, mono: str) -> dict:
+        L, V = self.L, self.L ** 3
+        s = np.arange(V)
+        x, y, z = s % L, (s // L) % L, s // (L * L)
+        keys = [(n, sign) for n in self.n_list for sign in (-1, 1)]
+        acc = None
+        for c0 in range(0, V, self.chunk):
+            sl = slice(c0, min(V, c0 + self.chunk))
+            N = normal_block(self.props[mono[0]][sl], self.props[mono[1]][sl], self.props[mono[2]][sl])
+            # one row of weights e^{i sign q.x} per (n, sign) over this chunk's sites
+            W = np.stack([np.exp(1j * sign * 2.0 * math.pi * (n[0] * x[sl] + n[1] * y[sl] + n[2] * z[sl]) / L)
+                          for n, sign in keys])
+            part = W @ N.reshape(N.shape[0], -1)
+            acc = part if acc is None else acc + part
+        shape = (1,) + N.shape[1:]
+        return {k: acc[i].reshape(shape) for i, k in enumerate(keys)}
+
+    def blocks(self, n, sign: int):
+        """A blocks callable (monomial -> one-site block) for the weight e^{i sign 2 pi n.x / L}."""
+        n = tuple(int(v) for v in n)
+
+        def get(mono: str) -> np.ndarray:
+            if mono not in self.cache:
+                self.cache[mono] = self._fill(mono)
+            return self.cache[mono][(n, sign)]
+        return get
+
+
+def momentum_projection(channel, sums: PhaseSums, n_list, block=(0, 0)) -> np.ndarray:
+    """F~(q) = sum_r e^{-i q.r} F(r) at q = 2 pi n / L for each n of n_list, by the correlation theorem of
+    Eq. (2.6): sum over terms of (sum_Y e^{-i q.Y} E1(Y)) (sum_X e^{+i q.X} E2(X)).
+    complex128 [len(n_list), 4, 4, 2, 2]; n = (0, 0, 0) is the zero-momentum sum of zero_momentum()."""
+    B1, B2, B3, B4 = channel
+    F = np.zeros((len(n_list), 4, 4, 2, 2), dtype=np.complex128)
+    for t in topologies(B1, B2, B3, B4, block):
+        for k, n in enumerate(n_list):
+            s1 = effective_block(t, 1, sums.blocks(n, -1))[0]
+            s2 = effective_block(t, 2, sums.blocks(n, +1))[0]
+            F[k] += t.sign0 * t.c34 * _place((s1 @ s2.T)[None], t)[0]
+    return F
+
+
+#: strangeness sectors S = 0 .. -4 and their particle-basis pairs of smallest |I3|
+SECTORS = [
+    [("p", "n")],
+    [("p", "Lambda"), ("p", "Sigma0"), ("n", "Sigma+")],
+    [("p", "Xi-"), ("n", "Xi0"), ("Lambda", "Lambda"), ("Lambda", "Sigma0"), ("Sigma+", "Sigma-"),
+     ("Sigma0", "Sigma0")],
+    [("Lambda", "Xi0"), ("Sigma+", "Xi-"), ("Sigma0", "Xi0")],
+    [("Xi0", "Xi-")],
+]
+
+
+def channel_table_56() -> list[tuple[str, str, str, str]]:
+    """Every (sink pair, source pair) of one sector, in sector order, sink-major: 1 + 9 + 36 + 9 + 1 = 56."""
+    return [sink + src for sector in SECTORS for sink in sector for src in sector]
+
+
+def vanishes_for_equal_light(channel) -> bool:
+    """True for a channel that is identically zero when u and d share a propagator.
+
+    Lambda and Sigma0 are the only fields of the list that the exchange u <-> d maps to themselves
+    (Lambda to -Lambda, Sigma0 to +Sigma0, Eq. (2.3)), so a channel made of them alone with an odd
+    number of Lambdas equals minus itself.
+    """
+    return all(f in ("Lambda", "Sigma0") for f in channel) and sum(f == "Lambda" for f in channel) % 2 == 1
+
+
+def channel_table() -> list[tuple[str, str, str, str]]:
+    """The 52 octet-octet channels "from NN to Xi Xi" (Sec. 1; Sec. 4 (iii)), reconstructed.
+
+    The paper takes its list from tables of another paper that are not available here, so the list is
+    rebuilt from its description: in each strangeness sector the particle-basis sink pairs of smallest
+    |I3| (SECTORS), each with every pair of its sector as the source (channel_table_56), without the
+    four that vanish identically for u = d (vanishes_for_equal_light): 52 remain.
+    """
+    return [ch for ch in channel_table_56() if not vanishes_for_equal_light(ch)]
+
+
 def flavour_content(channel) -> tuple[int, int]:
     """(number of light quarks, number of strange quarks) of the sink pair."""
     m = FIELDS[channel[0]][0][1] + FIELDS[channel[1]][0][1]

@@ -300,6 +300,61 @@ def test_zero_momentum_is_sum_over_r():
     assert rel(O.zero_momentum(ch, props, L), O.correlator(ch, props, L).sum(-1)) < 1e-13
 
 
+def test_momentum_projection_is_dft_of_direct_sum():
+    """The momentum projection (correlation theorem of Eq. (2.6) on phase-weighted site sums of the normal
+    blocks, accumulated in chunks with a ragged last chunk) against the explicit DFT of the direct O(V^2)
+    sum, for distinct u, d, s propagators and several momenta; n = 0 is the zero-momentum sum."""
+    L = 3
+    props = props3(61, L)
+    ns = [(0, 0, 0), (1, 0, 0), (0, 2, 1), (1, 2, 2)]
+    sums = O.PhaseSums(props, L, ns, chunk=10)
+    s = np.arange(L ** 3)
+    x, y, z = s % L, (s // L) % L, s // (L * L)
+    for ch in [("p", "n", "p", "n"), ("Lambda", "Sigma0", "Sigma+", "Sigma-"), ("Xi0", "Xi-", "Sigma0", "Xi0")]:
+        F = O.correlator(ch, props, L)
+        got = O.momentum_projection(ch, sums, ns)
+        for k, n in enumerate(ns):
+            want = F @ np.exp(-2j * np.pi * (n[0] * x + n[1] * y + n[2] * z) / L)
+            assert rel(got[k], want) < 1e-13, (ch, n)
+        assert rel(got[0], O.zero_momentum(ch, props, L)) < 1e-13
+
+
+def test_momentum_projection_other_source_spins():
+    L = 2
+    props = props3(62, L)
+    sums = O.PhaseSums(props, L, [(1, 0, 1)], chunk=3)
+    s = np.arange(L ** 3)
+    ph = np.exp(-2j * np.pi * ((s % L) + (s // (L * L))) / L)
+    ch = ("p", "Sigma0", "n", "Sigma+")
+    for block in [(1, 0), (1, 1)]:
+        want = O.correlator(ch, props, L, block=block) @ ph
+        assert rel(O.momentum_projection(ch, sums, [(1, 0, 1)], block=block)[0], want) < 1e-13
+
+
+def test_channel_table_and_the_four_that_vanish():
+    """52 of the 56 sector pairs; the four left out are identically zero when u = d (the oracle computes
+    them directly, never identifying u with d), the 52 kept are not, and with u != d none vanishes."""
+    table, all56 = O.channel_table(), O.channel_table_56()
+    assert len(all56) == 56 and len(set(all56)) == 56
+    assert len(table) == 52 and table[0] == ("p", "n", "p", "n") and table[-1] == ("Xi0", "Xi-", "Xi0", "Xi-")
+    dropped = [ch for ch in all56 if ch not in table]
+    assert sorted(dropped) == sorted([("Lambda", "Lambda", "Lambda", "Sigma0"), ("Lambda", "Sigma0", "Lambda", "Lambda"),
+                                      ("Lambda", "Sigma0", "Sigma0", "Sigma0"), ("Sigma0", "Sigma0", "Lambda", "Sigma0")])
+    Sl, Ss = I.propagator(63, "l", 1, 0), I.propagator(63, "s", 1, 0)
+    equal = {"u": Sl, "d": Sl.copy(), "s": Ss}
+    unequal = props3(64, 1)
+    for ch in all56:
+        if "Lambda" not in ch and "Sigma0" not in ch:
+            continue
+        F = O.correlator(ch, equal, 1)
+        scale = np.linalg.norm(O.correlator(("Lambda", "Lambda", "Lambda", "Lambda"), equal, 1))
+        if ch in dropped:
+            assert np.linalg.norm(F) < 1e-13 * scale, ch
+            assert np.linalg.norm(O.correlator(ch, unequal, 1)) > 1e-3 * scale, ch
+        else:
+            assert np.linalg.norm(F) > 1e-3 * scale, ch
+
+
 def test_direct_sum_paths_agree():
     rng = np.random.default_rng(0)
     L, m, n, K = 3, 4, 8, 5
