@@ -32,10 +32,11 @@ sys.path.insert(0, ROOT)
 L_DEFAULT, T_DEFAULT, DECAY, SEED = 32, 32, 0.5, 1607
 METRIC = "52-channel NBS correlators/sec/timeslice at 32^3"
 UNIT = "correlators/s"
-SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_LANES, SM_MAX_MHZ = 128, 2070.0   # FP32 lanes per SM; the clock used when no sample is available
 # DRAM bytes per momentum of the FP32 contraction kernels, from one ncu capture of
 # `python bench.py --L 16 --T 2 --steps 1 --warmup 1 --e2e-steps 1 --no-cpu-baseline`
-# (dram__bytes_read.sum + dram__bytes_write.sum / 4096 momenta; profiles/k_contract_16cube_fp32.md)
+# (dram__bytes_read.sum + dram__bytes_write.sum over 4096 momenta); an entry is dropped
+# whenever its kernel changes, until it is captured again
 DRAM_BYTES_PER_Q = {"k_contract_qseg": 1.255847e9 / 4096}
 
 
@@ -50,6 +51,8 @@ def parse():
     ap.add_argument("--T", type=int, default=T_DEFAULT)
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision-legs", action="store_true",
+                    help="skip the FP64 / split-BF16x3 timing and error legs of the FP32 line")
     ap.add_argument("--contract-cfg", type=int, default=0, help="NBS_PARAM_CONTRACT_CFG (kernel / launch shape)")
     ap.add_argument("--qblock", type=int, default=0, help="NBS_PARAM_CHUNK_QBLOCK (0 = library default)")
     ap.add_argument("--c64", action="store_true", help="store the propagators as complex64 (the 48^3 x 64 config)")
@@ -146,10 +149,10 @@ def oracle_sample_setup(L, seed=SEED, t=3):
 
 
 def oracle_cmac_per_correlator(L):
-    """Complex multiply-adds of the oracle's direct sum for one correlator, averaged over the 52 channels."""
+    """Complex multiply-adds of the oracle's direct sum for one correlator, averaged over the 52 channels
+    (the oracle's own channel table: this arm never loads the library)."""
     from oracle import nbs_oracle as O
-    from paper_1604_07983_gb300 import channel_names
-    names = channel_names()
+    names = O.channel_table()
     V = L ** 3
     tot = sum(sum(O.xi_size(t) for t in O.topologies(*ch)) for ch in names)
     return 64.0 * tot / len(names) * V * V
@@ -260,6 +263,42 @@ def contraction_flops(ids):
     return 8.0 * 64.0 * float(tb["terms"][:, 1].sum()), tb
 
 
+def precision_legs(P, ctx, ids, T, out, t_err=12, steps64=3, steps16=8):
+    """The second half of the metric on the same context and workload: per-channel normwise error of
+    the FP32 and split-BF16x3 paths against the plain FP64 GPU path on one timeslice, and the device
+    throughput of the FP64 and BF16x3 paths (each step one timeslice, all channels)."""
+    import torch
+    nch, V = len(ids), ctx.V
+    t_err = t_err % T
+    res = {}
+    for name, mode in (("fp64", P.NBS_FP64), ("fp32", P.NBS_FP32), ("bf16x3", P.NBS_BF16X3)):
+        ctx.set_precision(mode)
+        o = torch.empty((nch, 1, 4, 4, 2, 2, V), dtype=torch.complex128, device="cuda")
+        ctx.correlate(ids, t_err, t_err + 1, o)
+        res[name] = o.reshape(nch, -1)
+    torch.cuda.synchronize()
+    ref = res.pop("fp64")
+    norm = torch.linalg.vector_norm(ref, dim=1)
+    err = {k: (torch.linalg.vector_norm(v - ref, dim=1) / norm).cpu().tolist() for k, v in res.items()}
+    del res, ref
+    rates = {}
+    for name, mode, steps, warm in (("fp64", P.NBS_FP64, steps64, 1), ("bf16x3", P.NBS_BF16X3, steps16, 2)):
+        ctx.set_precision(mode)
+        for k in range(warm):
+            ctx.correlate(ids, k % T, k % T + 1, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(steps):
+            t = (warm + k) % T
+            ctx.correlate(ids, t, t + 1, out)
+        e1.record()
+        torch.cuda.synchronize()
+        rates[name] = (nch * steps / (e0.elapsed_time(e1) / 1e3), steps)
+    ctx.set_precision(P.NBS_FP32)
+    return err, rates, t_err
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -353,6 +392,10 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = job_rate(nch * e2e_steps, world, e2e_s)
     h2d = 2 * V * 144 * (8 if args.c64 else 16)
     d2h = nch * 64 * V * 16
+    legs = None
+    if world == 1 and prec == P.NBS_FP32 and not args.no_precision_legs:
+        legs = precision_legs(P, ctx, ids, T, out)
+    n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
     ctx.close()
 
     if rank != 0:
@@ -379,14 +422,16 @@ def run_ours(args, rank, world, local_rank):
                                    % int(tb["terms"][:, 1].sum())}
     elif dominant == "contract":
         if prec == P.NBS_FP32:
-            peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-            peak_src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+            mhz = clocks.summary().get("sm_mhz") or SM_MAX_MHZ
+            peak = n_sm * FP32_LANES * 2 * mhz * 1e6 / 1e12
+            peak_src = ("derived, not measured: %d SMs (device) x %d FP32 lanes x 2 flop x %.0f MHz (median "
+                        "sampled SM clock)" % (n_sm, FP32_LANES, mhz))
         else:
             peak = 1.25
             peak_src = "nominal GB300 FP64 1.25 TFLOP/s"
         ach = flops_per_launch / (per_launch_ms["contract"] / 1e3) / 1e12
         cfg = tuned["cfg"] if tuned else args.contract_cfg
-        kname = {0: "k_contract_qseg", 2: "k_contract_chunk", 3: "k_contract_chunk2",
+        kname = {0: "k_contract_rows", 4: "k_contract_qseg", 2: "k_contract_chunk", 3: "k_contract_chunk2",
                  1: "k_contract_slab"}.get(cfg, "k_contract") if prec == P.NBS_FP32 else \
             ("k_contract_slab" if cfg == 1 else "k_contract")
         traffic = None
@@ -435,6 +480,20 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
     }
+    if legs:
+        err, rates, t_err = legs
+        v64, v16 = rates["fp64"][0], rates["bf16x3"][0]
+        line["fp64_value"] = v64
+        line["mixed_over_fp64"] = value / v64
+        line["bf16x3_value"] = v16
+        line["bf16x3_over_fp64"] = v16 / v64
+        line["error_vs_fp64"] = {
+            "what": "normwise ||F - F_fp64|| / ||F_fp64|| per channel over all r and 64 spins, timeslice %d, "
+                    "against the plain FP64 GPU path in this run" % t_err,
+            "tolerance": 2e-5, "fp32_max": max(err["fp32"]), "bf16x3_max": max(err["bf16x3"]),
+            "fp32_per_channel": [float("%.3g" % e) for e in err["fp32"]],
+            "bf16x3_per_channel": [float("%.3g" % e) for e in err["bf16x3"]],
+            "steps": {"fp64": rates["fp64"][1], "bf16x3": rates["bf16x3"][1]}}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(L)
     print(json.dumps(line), flush=True)
