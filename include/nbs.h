@@ -165,11 +165,13 @@ int nbs_zero_momentum(nbs_ctx* h, double* out);
 
 /* Launch-shape parameters (for tuning; results agree to rounding).
  * NBS_PARAM_CONTRACT_CFG selects the contraction kernel:
- *   0 = default: in FP32, when the channel tables fit its shared memory, the
- *       quad-lane chunk kernel (persistent blocks of 16 warps, four lanes per
- *       shared index, one sink spin each; each warp walks its share of the
- *       steps as runs of one table run); in BF16X3 its tensor-core form; in
- *       FP64 the thread-per-momentum kernel (A = 2, W = 1);
+ *   0 = default: in FP32, when its tables fit shared memory, the two-phase
+ *       row kernel (persistent blocks of 16 warps; per momentum every distinct
+ *       effective-block row of a chunk of channels is built once for all four
+ *       sink spins, Eq. (4.2), then each lane forms the 4 x 4 sink-spin outer
+ *       products of one shared index and one source-spin pair, Eq. (4.3)),
+ *       else config 4; in BF16X3 the quad-lane tensor-core form; in FP64 the
+ *       thread-per-momentum kernel (A = 2, W = 1);
  *   1 = the momentum-slab kernel (one block per momentum and channel group,
  *       stored blocks staged in shared memory);
  *   2 = the chunk kernel (FP32; persistent blocks that keep a chunk of
@@ -178,6 +180,10 @@ int nbs_zero_momentum(nbs_ctx* h, double* out);
  *       else the default;
  *   3 = the chunk kernel's second form (FP32; same work split, cheaper inner
  *       loops: signed coefficient table, no divergence), else the default;
+ *   4 = the quad-lane chunk kernel (FP32; persistent blocks of 16 warps,
+ *       four lanes per shared index, one sink spin each, gathers straight
+ *       from the staged slabs; each warp walks its share of the steps as runs
+ *       of one table run), else the default;
  *   A*10 + W = the thread-per-momentum kernel with A sink spins alpha1 per
  *       thread (1, 2 or 4) and W warps per block (1, 2 or 4).
  * In NBS_BF16X3 mode the tensor-core kernels run: the quad-lane form
@@ -190,6 +196,13 @@ int nbs_zero_momentum(nbs_ctx* h, double* out);
 /* NBS_PARAM_FFT_BLOCK: threads per block of the strided (y, z) passes of the
  * 3-D FFTs: 64, 128 (default) or 256. */
 #define NBS_PARAM_FFT_BLOCK 2
+/* NBS_PARAM_TEST_SKIP_SLAB (test switch, 0 by default): 1 makes the FP32
+ * two-phase contraction arm its first slab wait in every block without
+ * issuing the copy, so that the bounded wait runs out with no copy in
+ * flight and nbs_correlate (or a waited nbs_graph_launch of a graph captured
+ * meanwhile) returns NBS_ETIMEOUT; it exercises the failure path without a
+ * device fault.  Each block waits about one second before it gives up. */
+#define NBS_PARAM_TEST_SKIP_SLAB 3
 int nbs_set_param(nbs_ctx* h, int param, int value);
 
 /* Profiling (stage timing with CUDA events on the context's stream).
@@ -295,7 +308,30 @@ int nbs_plan_sizes(const nbs_plan* p, long long* sizes);
                                  back to back, or one term): form (0..3 shape, 4..7 the fixed
                                  forms), side-1 and side-2 table offsets, first and end shared
                                  index, chunk-local channel, n1, n2                            */
+#define NBS_PX_ROWCHUNKS 20   /* int32 [nchunks][80]: the two-phase kernel's chunks: base1, ncell1, base2,
+                                 ncell2, nrow1, nrow2, aent_off, naent, adesc_off, rec_off, nstep, ch_off,
+                                 nch, nslot, seg_off, smem, seg_base[17], out_base[17], cfirst[16], padding */
+#define NBS_PX_ROWAENT   21   /* uint16: row entries, slab cell (bits 0..10; B2's cells from 944) | code
+                                 (bits 11..12: +1, -1, +2, -2)                                           */
+#define NBS_PX_ROWADESC  22   /* uint32 per row: entry offset in its chunk (bits 0..19) | count << 20      */
+#define NBS_PX_ROWREC    23   /* uint32 [step][8 xi~][4 s]: scale code (bits 0..4) | B1 row << 5 |
+                                 B2 row << 21                                                            */
+#define NBS_PX_ROWCH     24   /* int32: request-order channel of each chunk channel                       */
+#define NBS_PX_ROWSEGS   25   /* int32 [nsegs][4]: first step, end step, chunk-local channel, 0           */
+#define NBS_PX_ROWSCALES 26   /* double [32]: the scale of each code (code 31 = 0)                          */
 int nbs_plan_export(const nbs_plan* p, int what, void* dst);
+/* Sizes of the two-phase contraction's tables (rows of the effective blocks
+ * per chunk of channels, Eqs. (4.2)-(4.3)): sizes[0..NBS_PRS_N-1]. */
+#define NBS_PRS_OK       0   /* 1 if every chunk fits a block's shared memory     */
+#define NBS_PRS_NCHUNKS  1
+#define NBS_PRS_NAENT    2
+#define NBS_PRS_NADESC   3
+#define NBS_PRS_NREC     4
+#define NBS_PRS_NCH      5
+#define NBS_PRS_NSEGS    6
+#define NBS_PRS_SMEM     7   /* the largest chunk's shared memory (bytes)        */
+#define NBS_PRS_N        8
+int nbs_plan_row_sizes(const nbs_plan* p, long long* sizes);
 
 #ifdef __cplusplus
 }

@@ -125,6 +125,14 @@ cudaError_t launch_contract_tc(const float2* FB, int L, int nchunks, int qb, con
                                const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
                                const float* codes, int st1, int st2, int max_slot, int max_tab, float2* Ft,
                                cudaStream_t st);
+// two-phase contraction over distinct effective-block rows (kernels_rows.cu, FP32):
+// chunks points to RowChunkHdr[nchunks], segs to RowSeg[] (plan.h); scales: 32
+// floats; smem: the largest chunk's shared memory; skip_first (test switch):
+// arm the first slab wait without issuing its copy, so that it runs out
+cudaError_t launch_contract_rows(const float2* FB, long long ncells, int L, int nchunks, int qb, const void* chunks,
+                                 const unsigned short* aent, const unsigned* adesc, const unsigned* rec,
+                                 const void* segs, const int* row_ch, const float* scales, int smem, float2* Ft,
+                                 int* flags, int skip_first, cudaStream_t st);
 // ch_fl: per channel the quarks of each propagator (3 ints); exps: per propagator
 template <typename T>
 cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_fl, const int* exps, int nflav,

@@ -90,6 +90,8 @@ struct nbs_ctx {
   DevBuf d_chunks, d_qchunks, d_qsegs, d_ctab, d_citems, d_ctoff, d_codes;
   int chunk_st1 = 0, chunk_st2 = 0, chunk_slot = 0, chunk_tab = 0, chunk_row = 0, quad_slot = 0;
   int chunk_qb = 32;
+  DevBuf d_rchunks, d_raent, d_radesc, d_rrec, d_rsegs, d_rch, d_rscales;  // two-phase contraction tables
+  int test_skip_slab = 0;  // NBS_PARAM_TEST_SKIP_SLAB (test switch)
   int fft_block = 128;  // NBS_PARAM_FFT_BLOCK
   int tables_mode = -1;
   TypeRecipeSet recipes;
@@ -241,6 +243,31 @@ int upload_tables(nbs_ctx* h) {
     CK(cudaMemcpyAsync(h->d_codes.p, codes, sizeof(codes), cudaMemcpyHostToDevice, h->st), "upload codes");
     CK(cudaStreamSynchronize(h->st), "upload sync");
   }
+  if (P.rows_ok) {
+    float sc[NBS_ROW_SCALES];
+    for (int i = 0; i < NBS_ROW_SCALES; ++i) sc[i] = (float)P.row_scales[i];
+    if ((rc = ensure(h, h->d_rchunks, P.row_chunks.size() * sizeof(RowChunkHdr), "row chunks"))) return rc;
+    if ((rc = ensure(h, h->d_raent, std::max<size_t>(P.row_aent.size(), 8) * 2, "row entries"))) return rc;
+    if ((rc = ensure(h, h->d_radesc, std::max<size_t>(P.row_adesc.size(), 4) * 4, "row descriptors"))) return rc;
+    if ((rc = ensure(h, h->d_rrec, std::max<size_t>(P.row_rec.size(), 32) * 4, "row records"))) return rc;
+    if ((rc = ensure(h, h->d_rsegs, std::max<size_t>(P.row_segs.size(), 1) * sizeof(RowSeg), "row segments"))) return rc;
+    if ((rc = ensure(h, h->d_rch, std::max<size_t>(P.row_ch.size(), 1) * sizeof(int), "row channels"))) return rc;
+    if ((rc = ensure(h, h->d_rscales, sizeof(sc), "row scales"))) return rc;
+    CK(cudaMemcpyAsync(h->d_rchunks.p, P.row_chunks.data(), P.row_chunks.size() * sizeof(RowChunkHdr),
+                       cudaMemcpyHostToDevice, h->st), "upload row chunks");
+    CK(cudaMemcpyAsync(h->d_raent.p, P.row_aent.data(), P.row_aent.size() * 2, cudaMemcpyHostToDevice, h->st),
+       "upload row entries");
+    CK(cudaMemcpyAsync(h->d_radesc.p, P.row_adesc.data(), P.row_adesc.size() * 4, cudaMemcpyHostToDevice, h->st),
+       "upload row descriptors");
+    CK(cudaMemcpyAsync(h->d_rrec.p, P.row_rec.data(), P.row_rec.size() * 4, cudaMemcpyHostToDevice, h->st),
+       "upload row records");
+    CK(cudaMemcpyAsync(h->d_rsegs.p, P.row_segs.data(), P.row_segs.size() * sizeof(RowSeg), cudaMemcpyHostToDevice,
+                       h->st), "upload row segments");
+    CK(cudaMemcpyAsync(h->d_rch.p, P.row_ch.data(), P.row_ch.size() * sizeof(int), cudaMemcpyHostToDevice, h->st),
+       "upload row channels");
+    CK(cudaMemcpyAsync(h->d_rscales.p, sc, sizeof(sc), cudaMemcpyHostToDevice, h->st), "upload row scales");
+    CK(cudaStreamSynchronize(h->st), "upload sync");
+  }
   CK(cudaMemcpyAsync(h->d_groups.p, P.groups.data(), P.groups.size() * sizeof(GroupHdr), cudaMemcpyHostToDevice, h->st), "upload groups");
   CK(cudaMemcpyAsync(h->d_gch.p, P.group_ch.data(), P.group_ch.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload group channels");
   CK(cudaMemcpyAsync(h->d_items.p, P.items.data(), P.items.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload items");
@@ -388,8 +415,18 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
     const bool quad_fits = h->plan.chunks_ok &&
                            qseg_smem_bytes(h->quad_slot, h->chunk_tab, h->plan.max_quad_segs) <= (size_t)h->smem_optin &&
                            tcq_smem_bytes(h->quad_slot, h->chunk_tab, h->plan.max_quad_segs) <= (size_t)h->smem_optin;
-    const bool use_qseg = f32_chunks && h->contract_cfg == 0 && quad_fits;
-    if (h->mode == NBS_BF16X3 && quad_fits && h->contract_cfg != 2) {
+    // the two-phase row kernel: FP32 default where its tables fit the device's shared memory
+    const bool rows_fit = sizeof(T) == 4 && h->plan.rows_ok && h->plan.row_smem <= h->smem_optin;
+    const bool use_rows = rows_fit && h->mode == NBS_FP32 && h->contract_cfg == 0;
+    const bool use_qseg = f32_chunks && quad_fits && (h->contract_cfg == 4 || (h->contract_cfg == 0 && !rows_fit));
+    if (use_rows) {
+      CK(launch_contract_rows((const float2*)h->FB.p, h->plan.ncells, h->L, (int)h->plan.row_chunks.size(),
+                              h->chunk_qb, h->d_rchunks.p, (const unsigned short*)h->d_raent.p,
+                              (const unsigned*)h->d_radesc.p, (const unsigned*)h->d_rrec.p, h->d_rsegs.p,
+                              (const int*)h->d_rch.p, (const float*)h->d_rscales.p, h->plan.row_smem,
+                              (float2*)h->Ft.p, h->flags, h->test_skip_slab, h->st),
+         "contraction (rows)");
+    } else if (h->mode == NBS_BF16X3 && quad_fits && h->contract_cfg != 2) {
       CK(launch_contract_tcq((const float2*)h->FB.p, h->plan.ncells, h->L, (int)h->plan.quad_chunks.size(),
                              h->chunk_qb, h->d_qchunks.p, h->d_qsegs.p, h->plan.max_quad_segs,
                              (const int*)h->d_gch.p, (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
@@ -759,8 +796,8 @@ int nbs_set_param(nbs_ctx* h, int param, int value) {
   switch (param) {
     case NBS_PARAM_CONTRACT_CFG: {
       const int a = value / 10, w = value % 10;
-      if (!(value >= 0 && value <= 3) && !((a == 1 || a == 2 || a == 4) && (w == 1 || w == 2 || w == 4)))
-        return fail(h, NBS_EINVAL, "contraction config must be 0, 1, 2, 3 or A*10+W with A, W in {1, 2, 4}");
+      if (!(value >= 0 && value <= 4) && !((a == 1 || a == 2 || a == 4) && (w == 1 || w == 2 || w == 4)))
+        return fail(h, NBS_EINVAL, "contraction config must be 0, 1, 2, 3, 4 or A*10+W with A, W in {1, 2, 4}");
       h->contract_cfg = value;
       return NBS_OK;
     }
@@ -771,6 +808,10 @@ int nbs_set_param(nbs_ctx* h, int param, int value) {
     case NBS_PARAM_FFT_BLOCK:
       if (value != 64 && value != 128 && value != 256) return fail(h, NBS_EINVAL, "FFT block must be 64, 128 or 256");
       h->fft_block = value;
+      return NBS_OK;
+    case NBS_PARAM_TEST_SKIP_SLAB:
+      if (value != 0 && value != 1) return fail(h, NBS_EINVAL, "the slab-skip test switch is 0 or 1");
+      h->test_skip_slab = value;
       return NBS_OK;
     default: return fail(h, NBS_EINVAL, "unknown parameter");
   }
@@ -877,6 +918,20 @@ int nbs_plan_sizes(const nbs_plan* p, long long* s) {
   return NBS_OK;
 }
 
+int nbs_plan_row_sizes(const nbs_plan* p, long long* s) {
+  if (!p || !s) return fail(nullptr, NBS_EINVAL, "bad arguments");
+  const Plan& P = p->plan;
+  s[NBS_PRS_OK] = P.rows_ok ? 1 : 0;
+  s[NBS_PRS_NCHUNKS] = (long long)P.row_chunks.size();
+  s[NBS_PRS_NAENT] = (long long)P.row_aent.size();
+  s[NBS_PRS_NADESC] = (long long)P.row_adesc.size();
+  s[NBS_PRS_NREC] = (long long)P.row_rec.size();
+  s[NBS_PRS_NCH] = (long long)P.row_ch.size();
+  s[NBS_PRS_NSEGS] = (long long)P.row_segs.size();
+  s[NBS_PRS_SMEM] = P.row_smem;
+  return NBS_OK;
+}
+
 int nbs_plan_export(const nbs_plan* p, int what, void* dst) {
   if (!p || !dst) return fail(nullptr, NBS_EINVAL, "bad arguments");
   const Plan& P = p->plan;
@@ -940,6 +995,21 @@ int nbs_plan_export(const nbs_plan* p, int what, void* dst) {
     case NBS_PX_QUADSEGS:
       static_assert(sizeof(QuadSeg) == 8 * sizeof(int), "quad segment layout");
       if (P.chunks_ok) std::memcpy(I, P.quad_segs.data(), P.quad_segs.size() * sizeof(QuadSeg));
+      return NBS_OK;
+    case NBS_PX_ROWCHUNKS:
+      static_assert(sizeof(RowChunkHdr) == 80 * sizeof(int), "row chunk header layout");
+      std::memcpy(I, P.row_chunks.data(), P.row_chunks.size() * sizeof(RowChunkHdr));
+      return NBS_OK;
+    case NBS_PX_ROWAENT: std::memcpy(dst, P.row_aent.data(), P.row_aent.size() * 2); return NBS_OK;
+    case NBS_PX_ROWADESC: std::memcpy(dst, P.row_adesc.data(), P.row_adesc.size() * 4); return NBS_OK;
+    case NBS_PX_ROWREC: std::memcpy(dst, P.row_rec.data(), P.row_rec.size() * 4); return NBS_OK;
+    case NBS_PX_ROWCH: std::memcpy(I, P.row_ch.data(), P.row_ch.size() * sizeof(int)); return NBS_OK;
+    case NBS_PX_ROWSEGS:
+      static_assert(sizeof(RowSeg) == 4 * sizeof(int), "row segment layout");
+      std::memcpy(I, P.row_segs.data(), P.row_segs.size() * sizeof(RowSeg));
+      return NBS_OK;
+    case NBS_PX_ROWSCALES:
+      for (int i = 0; i < NBS_ROW_SCALES; ++i) D[i] = i < (int)P.row_scales.size() ? P.row_scales[i] : 0.0;
       return NBS_OK;
     default: return fail(nullptr, NBS_EINVAL, "unknown export");
   }

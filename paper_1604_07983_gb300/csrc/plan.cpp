@@ -983,6 +983,7 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan, int nflav) {
     }
   }
   build_chunks(plan);
+  build_row_chunks(plan, NBS_ROW_SMEM_LIMIT);
   return "";
 }
 

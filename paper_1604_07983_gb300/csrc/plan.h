@@ -114,6 +114,38 @@ struct QuadChunkHdr {
 // Only shapes 1 and 3 (forms 1, 3, 5, 7) occur.
 struct QuadSeg { int form, t1, t2, kbeg, kend, local, n1, n2; };
 
+// Two-phase contraction over distinct effective-block rows (kernels_rows.cu).
+// Within a chunk (whole channels of one slab group) every row of an effective
+// block -- one shared index xi~ and one held source spin of one side, i.e. a
+// sum of stored cells with coefficients -- is built once per momentum for all
+// four sink spins (phase A, Eq. (4.2)); a row is kept up to a scale: its
+// coefficients divided by the magnitude m of its term side are +-1 or +-2,
+// and its sign is fixed by its first entry.  Phase B forms the product of
+// Eq. (4.3) from the rows: record (xi~, s) names the row of B1 and of B2 for
+// output source-spin pair s and the scale m1 m2 sign1 sign2 (a code into
+// Plan::row_scales).  Lane 4 kq + s of a warp takes record (8 step + kq, s),
+// so a warp step covers eight shared indices of all four s.
+#define NBS_ROW_WARPS 16
+#define NBS_ROW_SLAB 944            // cells per slab side in shared memory
+#define NBS_ROW_MAX_ROWS 2047       // rows per side (11-bit row index)
+#define NBS_ROW_SCALES 32           // scale codes (code 31 = 0)
+#define NBS_ROW_SMEM_LIMIT 232448   // shared memory per block the tables are cut for (GB300 opt-in)
+struct RowChunkHdr {
+  int base1, ncell1, base2, ncell2;  // the group's two stored types
+  int nrow1, nrow2;                  // distinct rows of B1 (at q) and of B2 (at -q)
+  int aent_off, naent;               // phase-A entries (uint16) into Plan::row_aent
+  int adesc_off;                     // nrow1 + nrow2 row descriptors into Plan::row_adesc
+  int rec_off, nstep;                // 32 records (uint32) per step into Plan::row_rec
+  int ch_off, nch;                   // chunk channels into Plan::row_ch (request-order indices)
+  int nslot, seg_off, smem;          // per-warp partial-sum slots; segments into Plan::row_segs; bytes
+  int seg_base[NBS_ROW_WARPS + 1];   // warp w walks segments seg_base[w] .. seg_base[w + 1] (relative)
+  int out_base[NBS_ROW_WARPS + 1];   // its slots start at out_base[w] (chunk-local channel - cfirst[w])
+  int cfirst[NBS_ROW_WARPS];
+  int pad[14];                       // 80 ints
+};
+// Steps [sbeg, send) of chunk-local channel `local` (one flush at the end).
+struct RowSeg { int sbeg, send, local, pad; };
+
 struct Plan {
   std::vector<int> channels;                  // built-in ids, in request order
   std::vector<BlockType> types;
@@ -137,6 +169,16 @@ struct Plan {
   std::vector<QuadChunkHdr> quad_chunks;      // one per chunk (valid when chunks_ok)
   std::vector<QuadSeg> quad_segs;             // per-warp term runs of every quad chunk
   int max_quad_segs = 0;                      // most segments of one chunk
+  bool rows_ok = false;                       // every chunk of the two-phase tables fits shared memory
+  std::vector<RowChunkHdr> row_chunks;
+  std::vector<unsigned short> row_aent;       // slab cell (bits 0..10) | coefficient code (bits 11..12: +1 -1 +2 -2)
+  std::vector<unsigned> row_adesc;            // entry offset within the chunk (bits 0..19) | count << 20
+  std::vector<unsigned> row_rec;              // code (bits 0..4) | B1 row << 5 | B2 row << 21
+  std::vector<int> row_ch;
+  std::vector<RowSeg> row_segs;
+  std::vector<double> row_scales;             // NBS_ROW_SCALES signed scales, code 31 = 0
+  int row_smem = 0;                           // the largest chunk's shared memory (bytes)
+  std::string row_why;                        // why rows_ok is false
   // flops of the contraction per q (complex multiply-adds), for rooflines
   double cmac_per_q = 0, gathers_per_q = 0;
 };
@@ -148,6 +190,11 @@ struct Plan {
 
 // Compile the tables for the given channel ids.  Returns "" or an error text.
 std::string compile_plan(const std::vector<int>& channel_ids, Plan& out, int nflav = 2);
+
+// Two-phase contraction tables (plan_rows.cpp); smem_limit: bytes per block.
+void build_row_chunks(Plan& plan, int smem_limit);
+// Shared memory of one chunk of the two-phase contraction (kernels_rows.cu layout).
+size_t row_chunk_smem(int nrow, int naent, int nstep, int nslot, int nseg, int nch);
 
 // Set the text that nbs_last_error(NULL) returns on this thread.
 void set_global_error(const std::string& msg);

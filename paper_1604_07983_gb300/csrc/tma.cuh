@@ -38,6 +38,30 @@ __device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity) {
   }
   return false;
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// wait bounded in time (limit_ns of the global timer) and in polls; false if it gave up
+__device__ __forceinline__ bool mbar_wait_timed(unsigned addr, unsigned parity, unsigned long long limit_ns) {
+  unsigned long long t0 = 0;
+  for (int i = 0; i < (1 << 28); ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((i & 255) == 255) {
+      const unsigned long long t = global_ns();
+      if (!t0) t0 = t;
+      else if (t - t0 > limit_ns) return false;
+    }
+  }
+  return false;
+}
 __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2,
                                             unsigned mbar) {
   asm volatile(

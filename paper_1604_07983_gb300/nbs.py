@@ -27,7 +27,7 @@ EXPORTS = ["nbs_set_allocator", "nbs_create", "nbs_destroy", "nbs_set_precision"
            "nbs_profile", "nbs_channel_count",
            "nbs_channel_info", "nbs_last_error", "nbs_plan_create", "nbs_plan_destroy", "nbs_plan_sizes",
            "nbs_plan_export", "nbs_correlate_static", "nbs_graph_capture", "nbs_graph_launch", "nbs_graph_destroy",
-           "nbs_load_props3", "nbs_plan_create_flavours", "nbs_potential"]
+           "nbs_load_props3", "nbs_plan_create_flavours", "nbs_potential", "nbs_plan_row_sizes"]
 
 
 class NBSError(RuntimeError):
@@ -69,6 +69,7 @@ def lib():
         "nbs_plan_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(i), i]),
         "nbs_plan_destroy": (i, [vp]),
         "nbs_plan_sizes": (i, [vp, ctypes.POINTER(ll)]),
+        "nbs_plan_row_sizes": (i, [vp, ctypes.POINTER(ll)]),
         "nbs_plan_export": (i, [vp, i, vp]),
         "nbs_correlate_static": (i, [vp, vp, i, i, i, vp, vp]),
         "nbs_graph_capture": (i, [vp, ctypes.POINTER(i), i, i, i, vp, ctypes.POINTER(vp)]),
@@ -116,7 +117,8 @@ def channel_names():
 
 PX = dict(TYPES=0, TYPETERMS=1, TYPECOEF=2, CELLS=3, TERMS=4, ENT1_CELL=5, ENT1_COEF=6, ENT2_CELL=7,
           ENT2_COEF=8, CHANNELS=9, GROUPS=10, GROUPCH=11, ITEMS=12, CHUNKS=13, CHUNKTAB=14, CHUNKITEMS=15,
-          QUADCHUNKS=18, QUADSEGS=19,
+          QUADCHUNKS=18, QUADSEGS=19, ROWCHUNKS=20, ROWAENT=21, ROWADESC=22, ROWREC=23, ROWCH=24, ROWSEGS=25,
+          ROWSCALES=26,
           TERMTABOFF=16, CODES=17)
 
 
@@ -148,9 +150,24 @@ def plan_tables(channel_ids, flavours: int = 2):
             quad_chunks=(qc := get("QUADCHUNKS", (nck, 64), np.int32)),
             quad_segs=get("QUADSEGS", (int(qc[-1, 43 + 16]) if nck else 0, 8), np.int32),
             chunk_tab=get("CHUNKTAB", (max(nctab, 1),), np.uint16), chunk_items=get("CHUNKITEMS", (ncit, 2), np.int32),
-            term_tab_off=get("TERMTABOFF", (nterm, 2), np.int32), codes=get("CODES", (32,), np.float64))
+            term_tab_off=get("TERMTABOFF", (nterm, 2), np.int32), codes=get("CODES", (32,), np.float64),
+            rows=row_tables(L, p, get))
     finally:
         L.nbs_plan_destroy(p)
+
+
+def row_tables(L, p, get):
+    """The two-phase contraction's tables (None where they do not fit shared memory)."""
+    import numpy as np
+    rs = (ctypes.c_longlong * 8)()
+    _check(L.nbs_plan_row_sizes(p, rs))
+    ok, nck, naent, nadesc, nrec, nch, nseg, smem = list(rs)
+    if not ok:
+        return None
+    return dict(chunks=get("ROWCHUNKS", (nck, 80), np.int32), aent=get("ROWAENT", (max(naent, 1),), np.uint16),
+                adesc=get("ROWADESC", (max(nadesc, 1),), np.uint32), rec=get("ROWREC", (max(nrec, 1),), np.uint32),
+                ch=get("ROWCH", (max(nch, 1),), np.int32), segs=get("ROWSEGS", (max(nseg, 1), 4), np.int32),
+                scales=get("ROWSCALES", (32,), np.float64), smem=smem)
 
 
 # ---- torch-backed device allocator -------------------------------------------

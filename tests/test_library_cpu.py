@@ -438,3 +438,74 @@ def test_quad_runs_reproduce_the_term_products(lib, ids):
                         P = np.einsum("ka,kb->ab", Eo[:, h1], Ex[:, h2])  # [own spin][exchanged spin]
                         got[ch, :, :, _s_index(shape, h1, h2)] += P.T if swapped else P
     assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("ids", [list(range(52)), [0], [24, 25, 51], list(range(0, 208, 5)), list(range(208))])
+def test_row_tables_reproduce_the_term_products(lib, ids):
+    """The two-phase contraction's tables, executed in FP64 on random slab values (one momentum) the way the
+    kernel does: phase A builds every listed row of a chunk (sum of +-1 / +-2 times slab cells, B2's cells
+    from 944 on), phase B walks each warp's segments, lane (kq, s) of step st takes record (8 st + kq, s):
+    scale times the outer product of its B1 row and B2 row into output pair s.  Every channel equals the plain
+    sum over its terms of E1 E2 built from the uncompressed gather lists; every step is walked by exactly one
+    warp, inside one channel, and each warp's channels fit its slots."""
+    tb = nbs.plan_tables(ids)
+    rt = tb["rows"]
+    assert rt is not None
+    T = tb["terms"]
+    rng = np.random.default_rng(8)
+    ncells = int(tb["cells"].shape[0])
+    A = rng.standard_normal((ncells, 4)) + 1j * rng.standard_normal((ncells, 4))  # B1's blocks at q
+    B = rng.standard_normal((ncells, 4)) + 1j * rng.standard_normal((ncells, 4))  # B2's blocks at -q
+    nch = len(ids)
+    want = np.zeros((nch, 4, 4, 4), complex)
+    for t in range(len(T)):
+        ch, K, shape, n1, n2, off1, off2 = (int(x) for x in T[t][:7])
+        nh1, nh2 = _held(shape)
+        c1 = tb["ent1_cell"][off1:off1 + K * n1 * nh1].reshape(K, n1, nh1)
+        f1 = tb["ent1_coef"][off1:off1 + K * n1 * nh1].reshape(K, n1, nh1)
+        c2 = tb["ent2_cell"][off2:off2 + K * n2 * nh2].reshape(K, n2, nh2)
+        f2 = tb["ent2_coef"][off2:off2 + K * n2 * nh2].reshape(K, n2, nh2)
+        E1 = np.einsum("kih,kiha->kha", f1, A[c1])
+        E2 = np.einsum("kih,kiha->kha", f2, B[c2])
+        for h1 in range(nh1):
+            for h2 in range(nh2):
+                want[ch, :, :, _s_index(shape, h1, h2)] += np.einsum("ka,kb->ab", E1[:, h1], E2[:, h2])
+    coef = np.array([1.0, -1.0, 2.0, -2.0])
+    got = np.zeros_like(want)
+    assert np.count_nonzero(rt["scales"][:31]) <= 31 and rt["scales"][31] == 0
+    for ck in rt["chunks"]:
+        base1, ncell1, base2, ncell2, nrow1, nrow2, aent_off, naent, adesc_off, rec_off, nstep, ch_off, nch_c, \
+            nslot = (int(x) for x in ck[:14])
+        seg_off, smem = int(ck[14]), int(ck[15])
+        seg_base, out_base, cfirst = ck[16:33], ck[33:50], ck[50:66]
+        assert smem <= rt["smem"] <= 232448 and nrow1 <= 2047 and nrow2 <= 2047
+        slab = np.zeros((2 * 944, 4), complex)
+        slab[:ncell1] = A[base1:base1 + ncell1]
+        slab[944:944 + ncell2] = B[base2:base2 + ncell2]
+        E = np.zeros((nrow1 + nrow2, 4), complex)
+        for r in range(nrow1 + nrow2):
+            d = int(rt["adesc"][adesc_off + r])
+            off, cnt = d & 0xFFFFF, d >> 20
+            e = rt["aent"][aent_off + off: aent_off + off + cnt].astype(np.int64)
+            if r < nrow1:
+                assert np.all((e & 0x7FF) < ncell1)
+            else:
+                assert np.all(((e & 0x7FF) >= 944) & ((e & 0x7FF) < 944 + ncell2))
+            E[r] = (coef[(e >> 11) & 3][:, None] * slab[e & 0x7FF]).sum(axis=0)
+        rec = rt["rec"][rec_off: rec_off + 32 * nstep].astype(np.int64).reshape(nstep, 8, 4)
+        seen = np.zeros(nstep, int)
+        for w in range(16):
+            segs = rt["segs"][seg_off + seg_base[w]: seg_off + seg_base[w + 1]]
+            for sb, se, local, _ in segs:
+                assert cfirst[w] <= local < cfirst[w] + out_base[w + 1] - out_base[w]
+                seen[sb:se] += 1
+                ch = rt["ch"][ch_off + local]
+                for st in range(sb, se):
+                    for kq in range(8):
+                        for s in range(4):
+                            wd = rec[st, kq, s]
+                            r1, r2, code = (wd >> 5) & 0x7FF, wd >> 21, wd & 31
+                            assert r1 < nrow1 and r2 < nrow2
+                            got[ch, :, :, s] += rt["scales"][code] * np.outer(E[r1], E[nrow1 + r2])
+        assert np.all(seen == 1)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
