@@ -166,7 +166,7 @@ int nbs_zero_momentum(nbs_ctx* h, double* out);
 /* Launch-shape parameters (for tuning; results agree to rounding).
  * NBS_PARAM_CONTRACT_CFG selects the contraction kernel:
  *   0 = default: in FP32, when its tables fit shared memory, the two-phase
- *       row kernel (persistent blocks of 16 warps; per momentum every distinct
+ *       row kernel (persistent blocks of 24 warps; per momentum every distinct
  *       effective-block row of a chunk of channels is built once for all four
  *       sink spins, Eq. (4.2), then each lane forms the 4 x 4 sink-spin outer
  *       products of one shared index and one source-spin pair, Eq. (4.3)),
@@ -308,14 +308,16 @@ int nbs_plan_sizes(const nbs_plan* p, long long* sizes);
                                  back to back, or one term): form (0..3 shape, 4..7 the fixed
                                  forms), side-1 and side-2 table offsets, first and end shared
                                  index, chunk-local channel, n1, n2                            */
-#define NBS_PX_ROWCHUNKS 20   /* int32 [nchunks][80]: the two-phase kernel's chunks: base1, ncell1, base2,
-                                 ncell2, nrow1, nrow2, aent_off, naent, adesc_off, rec_off, nstep, ch_off,
-                                 nch, nslot, seg_off, smem, seg_base[17], out_base[17], cfirst[16], padding */
-#define NBS_PX_ROWAENT   21   /* uint16: row entries, slab cell (bits 0..10; B2's cells from 944) | code
-                                 (bits 11..12: +1, -1, +2, -2)                                           */
-#define NBS_PX_ROWADESC  22   /* uint32 per row: entry offset in its chunk (bits 0..19) | count << 20      */
-#define NBS_PX_ROWREC    23   /* uint32 [step][8 xi~][4 s]: scale code (bits 0..4) | B1 row << 5 |
-                                 B2 row << 21                                                            */
+#define NBS_PX_ROWCHUNKS 20   /* int32 [nchunks][96]: the two-phase kernel's chunks: base1, ncell1, base2,
+                                 ncell2, nrow1, nrow2, aent_off, naent, adesc_off, nadesc, rec_off, nstep,
+                                 ch_off, nch, nslot, seg_off, smem, nbuf, seg_base[W + 1], out_base[W + 1],
+                                 cfirst[W], padding (W = the block's warps, NBS_PRS_WARPS)                 */
+#define NBS_PX_ROWAENT   21   /* uint16: row entries, planar slab unit (bits 0..11: side * 1888 + (cell / 236)
+                                 * 472 + cell % 236) | code (bits 12..13: +1, -1, +2, -2)                 */
+#define NBS_PX_ROWADESC  22   /* uint32 per distinct row: entry offset in its chunk (bits 0..13) |
+                                 count << 14 | row slot << 19 (B2's rows from nrow1)                     */
+#define NBS_PX_ROWREC    23   /* uint32 [step][8 xi~][4 s]: B1 row (bits 0..11) | B2 row << 12 |
+                                 scale code << 24; four padding steps follow the last chunk              */
 #define NBS_PX_ROWCH     24   /* int32: request-order channel of each chunk channel                       */
 #define NBS_PX_ROWSEGS   25   /* int32 [nsegs][4]: first step, end step, chunk-local channel, 0           */
 #define NBS_PX_ROWSCALES 26   /* double [32]: the scale of each code (code 31 = 0)                          */
@@ -330,7 +332,8 @@ int nbs_plan_export(const nbs_plan* p, int what, void* dst);
 #define NBS_PRS_NCH      5
 #define NBS_PRS_NSEGS    6
 #define NBS_PRS_SMEM     7   /* the largest chunk's shared memory (bytes)        */
-#define NBS_PRS_N        8
+#define NBS_PRS_WARPS    8   /* warps per block of the two-phase kernel          */
+#define NBS_PRS_N        9
 int nbs_plan_row_sizes(const nbs_plan* p, long long* sizes);
 
 #ifdef __cplusplus

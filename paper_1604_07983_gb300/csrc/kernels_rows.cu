@@ -1,22 +1,28 @@
 // kernels_rows.cu -- the effective blocks (Eq. (4.2)) and their product
 // (Eq. (4.3)) in two phases per momentum, FP32.
 //
-// A CTA of 16 warps keeps one chunk's tables in shared memory (plan_rows.cpp)
-// and sweeps a block of momenta.  Per momentum q:
-//   * the two slabs (B1's stored type at q, B2's at -q; 32 bytes per cell:
-//     four sink spins, complex) arrive by TMA into one buffer;
-//   * phase A: each thread builds whole effective-block rows, sum of
-//     +-1 / +-2 times slab cells, for all four spins at once (one decode per
-//     entry, two 16-byte loads, eight FMAs), into the row array;
-//   * the slab buffer is free again: one thread issues the next momentum's
-//     boxes, which land while phase B runs;
-//   * phase B: lane 4 kq + s of a warp takes record (8 step + kq, s): the B1
-//     row and B2 row of shared index xi~ for output source-spin pair s and the
+// A CTA of 24 warps keeps one chunk's row tables in shared memory
+// (plan_rows.cpp) and sweeps a block of momenta:
+//   * phase A(q): each thread builds whole effective-block rows, sums of
+//     +-1 / +-2 times cells of the two staged slabs (B1's stored type at q,
+//     B2's at -q; per cell 16 bytes of sink spins 0, 1 and 16 bytes of spins
+//     2, 3 in separate planes, staged by 4-D TMA boxes), for all four spins at
+//     once (one decode per entry, two 16-byte loads, eight FMAs).
+//     The rows live in two planes of 16-byte entries (sink spins 0, 1 and
+//     2, 3), double-buffered by the parity of q; row numbers are chosen so
+//     that the rows a quarter warp loads together differ mod 8 (no bank
+//     conflicts);
+//   * phase B(q): lane 4 kq + s of a warp takes record (8 step + kq, s) --
+//     read from global memory (L1/L2), four steps ahead -- naming the B1 row
+//     and B2 row of shared index xi~ for output source-spin pair s and a
 //     scale; it forms the 4 x 4 outer product over the sink spins alpha1,
 //     alpha2 and accumulates 16 complex values.  At the end of each channel
-//     segment a warp sums over its eight kq lanes and adds into its slot;
-//   * the slots of each channel are summed in warp order (deterministic) and
-//     written to F~[channel][spin][q].
+//     segment the warp sums over its eight kq lanes into its slot (slots
+//     double-buffered by the parity of q);
+//   * each warp runs B(q) and then its share of A(q + 1); one barrier per
+//     momentum, after which one thread issues the TMA boxes of the slabs of
+//     q + 2 (the slab buffer is single) and the slots of q are summed in warp
+//     order (deterministic) into F~[channel][spin][q].
 // Waits on the slab mbarrier are bounded (a second of the global timer); a
 // wait that gives up sets bit 1 of flags, the CTA leaves once nothing is in
 // flight, and every later CTA of the launch leaves at its start.
@@ -32,25 +38,26 @@ namespace {
 
 constexpr unsigned RSLAB_BYTES = 2u * NBS_ROW_SLAB * 32u;
 constexpr unsigned long long RWAIT_NS = 1000000000ull;  // slab wait limit (global timer)
+constexpr int RPREF = 4;                                  // records loaded ahead (steps)
 
 struct RowLayout {
-  unsigned e, rec, aent, adesc, out, seg, sc, cs, mb, total;
+  unsigned e, aent, adesc, out, seg, sc, cs, mb, total;
 };
 
-// shared-memory layout of one chunk (offsets from a 128-byte aligned base)
-__host__ __device__ inline RowLayout row_layout(int nrow, int naent, int nstep, int nslot, int nseg, int nch) {
+// shared-memory layout of one chunk (offsets from a 128-byte aligned base):
+// slab, one or two row buffers of two planes, row tables, two slot buffers, segments, scales, channel lists
+__host__ __device__ inline RowLayout row_layout(int nbuf, int nrow, int nadesc, int naent, int nslot, int nseg,
+                                                int nch) {
   RowLayout L;
   unsigned o = RSLAB_BYTES;
   L.e = o;
-  o += (unsigned)nrow * 32u;
-  L.rec = o;
-  o += (unsigned)nstep * 128u;
+  o += (unsigned)nbuf * (unsigned)nrow * 32u;
   L.aent = o;
   o += (unsigned)((naent + 7) / 8) * 16u;
   L.adesc = o;
-  o += (unsigned)((nrow + 3) / 4) * 16u;
+  o += (unsigned)((nadesc + 3) / 4) * 16u;
   L.out = o;
-  o += (unsigned)nslot * 512u;
+  o += 2u * (unsigned)nslot * 512u;
   L.seg = o;
   o += (unsigned)nseg * 16u;
   L.sc = o;
@@ -73,6 +80,31 @@ __device__ __forceinline__ void cp16(void* smem, const void* gmem) {
 __device__ __forceinline__ long long minus_q(long long q, int L) {
   const int x = (int)(q % L), y = (int)((q / L) % L), z = (int)(q / ((long long)L * L));
   return (long long)((L - x) % L) + L * ((long long)((L - y) % L) + (long long)L * ((L - z) % L));
+}
+
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            unsigned mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(dst),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+      : "memory");
+}
+
+// Stage the planar slabs of one momentum into S with mbarrier mb (one thread, after the block has finished
+// reading S): side 1 ncell1 cells from base1 at q, side 2 ncell2 cells from base2 at qm.  The tensor map
+// sees the stored blocks as [momentum][half][cell][4 floats] (half = sink spins 0, 1 or 2, 3); a box of
+// NBS_ROW_BOX cells and both halves lands as [half][cell][16 bytes], box k of side s at 16-byte unit
+// s * 2 NBS_ROW_SLAB + k * 2 NBS_ROW_BOX.  The box's x coordinate is always 0 (16-byte aligned).
+__device__ __forceinline__ void tma_issue_planar(const CUtensorMap* map, unsigned S, unsigned mb, int base1, int ncell1,
+                                                 int q, int base2, int ncell2, int qm) {
+  const int nb1 = (ncell1 + NBS_ROW_BOX - 1) / NBS_ROW_BOX, nb2 = (ncell2 + NBS_ROW_BOX - 1) / NBS_ROW_BOX;
+  constexpr unsigned box = 2u * NBS_ROW_BOX * 16u;
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // earlier generic reads of S first
+  mbar_expect_tx(mb, (unsigned)(nb1 + nb2) * box);
+  for (int k = 0; k < nb1; ++k) tma_load_4d(S + k * box, map, 0, base1 + k * NBS_ROW_BOX, 0, q, mb);
+  for (int k = 0; k < nb2; ++k)
+    tma_load_4d(S + 2u * NBS_ROW_SLAB * 16u + k * box, map, 0, base2 + k * NBS_ROW_BOX, 0, qm, mb);
 }
 
 // sum a lane's 32 floats over the eight lanes of equal s (xor 16, 8, 4),
@@ -118,15 +150,16 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_rows(
   const unsigned pad = (128u - (smem_u32(smem_raw) & 127u)) & 127u;
   unsigned char* const sb = smem_raw + pad;
   const RowChunkHdr& ck = chunks[blockIdx.x % nchunks];
-  const int nrow1 = ck.nrow1, nrow = ck.nrow1 + ck.nrow2, nstep = ck.nstep, nslot = ck.nslot, nch = ck.nch;
-  const int nseg = ck.seg_base[NW];
-  const RowLayout lay = row_layout(nrow, ck.naent, nstep, nslot, nseg, nch);
+  const int nrow1 = ck.nrow1, nrow = ck.nrow1 + ck.nrow2, nslot = ck.nslot, nch = ck.nch;
+  const int nseg = ck.seg_base[NW], nadesc = ck.nadesc, nbuf = ck.nbuf;
+  const RowLayout lay = row_layout(nbuf, nrow, nadesc, ck.naent, nslot, nseg, nch);
   float4* const SL = reinterpret_cast<float4*>(sb);  // slab: [2][NBS_ROW_SLAB] cells of two float4
-  float4* const E = reinterpret_cast<float4*>(sb + lay.e);
-  const unsigned* const REC = reinterpret_cast<const unsigned*>(sb + lay.rec);
+  // row buffer b: E0 + 2 b nrow; plane 0 [nrow] (sink spins 0, 1), plane 1 [nrow] (spins 2, 3); B2's rows
+  // from nrow1
+  float4* const E0 = reinterpret_cast<float4*>(sb + lay.e);
   const unsigned short* const AE = reinterpret_cast<const unsigned short*>(sb + lay.aent);
   const unsigned* const AD = reinterpret_cast<const unsigned*>(sb + lay.adesc);
-  float2* const OUT = reinterpret_cast<float2*>(sb + lay.out);
+  float2* const OUT0 = reinterpret_cast<float2*>(sb + lay.out);  // slot buffer b: OUT0 + b nslot 64
   const RowSeg* const SEG = reinterpret_cast<const RowSeg*>(sb + lay.seg);
   float* const SC = reinterpret_cast<float*>(sb + lay.sc);
   int* const CS = reinterpret_cast<int*>(sb + lay.cs);  // per chunk channel: its slots SLT[CS[c] .. CS[c + 1])
@@ -149,8 +182,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_rows(
         if (skip_first)  // test switch: arm the barrier, issue no box (the wait runs out, nothing in flight)
           mbar_expect_tx(mb, 32u);
         else
-          tma_issue_slabs(&fbmap, smem_u32(SL), NBS_ROW_SLAB * 32u, mb, base1, n1c, (int)q_begin, base2, n2c,
-                          (int)minus_q(q_begin, L));
+          tma_issue_planar(&fbmap, smem_u32(SL), mb, base1, n1c, (int)q_begin, base2, n2c, (int)minus_q(q_begin, L));
       }
     }
   }
@@ -168,62 +200,54 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_rows(
     CS[nch] = n;
   }
   {
-    const uint4* g = reinterpret_cast<const uint4*>(rec + ck.rec_off);
-    for (int i = threadIdx.x; i < nstep * 8; i += NT) cp16((uint4*)REC + i, g + i);
     const uint4* ga = reinterpret_cast<const uint4*>(aent + ck.aent_off);
     for (int i = threadIdx.x; i < (ck.naent + 7) / 8; i += NT) cp16((uint4*)AE + i, ga + i);
     const uint4* gd = reinterpret_cast<const uint4*>(adesc + ck.adesc_off);
-    for (int i = threadIdx.x; i < (nrow + 3) / 4; i += NT) cp16((uint4*)AD + i, gd + i);
+    for (int i = threadIdx.x; i < (nadesc + 3) / 4; i += NT) cp16((uint4*)AD + i, gd + i);
     const uint4* gs = reinterpret_cast<const uint4*>(segs + ck.seg_off);
     for (int i = threadIdx.x; i < nseg; i += NT) cp16((uint4*)SEG + i, gs + i);
   }
-  auto stage_slabs_async = [&](long long q) {  // 16-byte cp.async by all threads (no tensor map)
+  auto stage_slabs_async = [&](long long q) {  // the same planar slabs by 16-byte cp.async (no tensor map)
     const long long qm = minus_q(q, L);
-    for (int i = threadIdx.x; i < 2 * n1c; i += NT)
-      cp16(SL + i, reinterpret_cast<const char*>(FB + ((long long)(base1 + (i >> 1)) * V + q) * 4) + 16 * (i & 1));
-    for (int i = threadIdx.x; i < 2 * n2c; i += NT)
-      cp16(SL + 2 * NBS_ROW_SLAB + i,
-           reinterpret_cast<const char*>(FB + ((long long)(base2 + (i >> 1)) * V + qm) * 4) + 16 * (i & 1));
+    for (int i = threadIdx.x; i < 2 * (n1c + n2c); i += NT) {
+      const int side = i >= 2 * n1c, k = side ? i - 2 * n1c : i, c = k >> 1, h = k & 1;
+      const long long src = ((long long)((side ? base2 : base1) + c) * V + (side ? qm : q)) * 4 + 2 * h;
+      cp16(SL + side * 2 * NBS_ROW_SLAB + (c / NBS_ROW_BOX) * 2 * NBS_ROW_BOX + h * NBS_ROW_BOX + c % NBS_ROW_BOX,
+           FB + src);
+    }
+  };
+  // the slabs of momentum qn into the (free) slab buffer
+  auto stage_slabs = [&](long long qn) {
+    if constexpr (TMA) {
+      if (threadIdx.x == 0)
+        tma_issue_planar(&fbmap, smem_u32(SL), mb, base1, n1c, (int)qn, base2, n2c, (int)minus_q(qn, L));
+    } else {
+      stage_slabs_async(qn);
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
   };
   if (!TMA && q_begin < q_end) stage_slabs_async(q_begin);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
-  for (int i = threadIdx.x; i < nslot * 64; i += NT) OUT[i] = make_float2(0.f, 0.f);
+  for (int i = threadIdx.x; i < 2 * nslot * 64; i += NT) OUT0[i] = make_float2(0.f, 0.f);
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
 
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s_begin = ck.seg_base[w], s_end = ck.seg_base[w + 1];
-  float2* const out_w = OUT + (ck.out_base[w] - ck.cfirst[w]) * 64;
-  const char* const E1b = reinterpret_cast<const char*>(E);
-  const char* const E2b = E1b + (size_t)nrow1 * 32;
-  unsigned parity = 0;
-  for (long long q = q_begin; q < q_end; ++q, parity ^= 1u) {
-    if constexpr (TMA) {
-      const bool ok = mbar_wait_timed(mb, parity, RWAIT_NS);
-      if (__syncthreads_or(!ok)) {
-        // flag the launch; before leaving, wait (bounded) for the one transfer that may be in flight
-        if (threadIdx.x == 0) {
-          atomicOr(flags, 2);
-          if (!skip_first || q != q_begin)
-            for (int k = 0; k < 8 && !mbar_wait_timed(mb, parity, RWAIT_NS); ++k) {
-            }
-        }
-        __syncthreads();
-        return;
-      }
-    }
-    // ---- phase A: the distinct effective-block rows, all four sink spins ----
-    for (int r = threadIdx.x; r < nrow; r += NT) {
-      const unsigned d = AD[r];
-      const int cnt = (int)(d >> 20);
-      const unsigned short* p = AE + (d & 0xFFFFFu);
+  // phase A: this thread's share of the distinct rows from the staged slabs, into row buffer Eb
+  auto phase_a = [&](float4* Eb) {
+    // rows come longest first: deal them to the threads in snake order (reversed every other round)
+    for (int r0 = 0, k = 0; r0 < nadesc; r0 += NT, ++k) {
+      const int i = (k & 1) ? r0 + NT - 1 - (int)threadIdx.x : r0 + (int)threadIdx.x;
+      if (i >= nadesc) continue;
+      const unsigned d = AD[i];
+      const int cnt = (int)((d >> 14) & 31u), r = (int)(d >> 19);
+      const unsigned short* p = AE + (d & 0x3FFFu);
       float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-      for (int i = 0; i < cnt; ++i) {
-        const unsigned x = p[i];
-        float c = (x & 0x1000u) ? 2.f : 1.f;
-        c = (x & 0x800u) ? -c : c;
-        const float4* sp = SL + 2 * (x & 0x7FFu);
-        const float4 v0 = sp[0], v1 = sp[1];
+      for (int j = 0; j < cnt; ++j) {
+        const unsigned x = p[j];
+        float c = (x & 0x2000u) ? 2.f : 1.f;
+        c = (x & 0x1000u) ? -c : c;
+        const float4* sp = SL + (x & 0xFFFu);  // planar slab unit: spins 0, 1; spins 2, 3 one box-half on
+        const float4 v0 = sp[0], v1 = sp[NBS_ROW_BOX];
         a0.x = fmaf(c, v0.x, a0.x);
         a0.y = fmaf(c, v0.y, a0.y);
         a0.z = fmaf(c, v0.z, a0.z);
@@ -233,58 +257,116 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_rows(
         a1.z = fmaf(c, v1.z, a1.z);
         a1.w = fmaf(c, v1.w, a1.w);
       }
-      E[2 * r] = a0;
-      E[2 * r + 1] = a1;
+      Eb[r] = a0;
+      Eb[nrow + r] = a1;
+    }
+  };
+  // a slab wait gave up: flag the launch; before leaving, wait (bounded) for the transfer that may still
+  // be in flight (none when the test switch withheld the first copy)
+  auto give_up = [&](unsigned parity, bool in_flight) {
+    if (threadIdx.x == 0) {
+      atomicOr(flags, 2);
+      if (in_flight)
+        for (int k = 0; k < 8 && !mbar_wait_timed(mb, parity, RWAIT_NS); ++k) {
+        }
     }
     __syncthreads();
-    // the slab buffer is free: the next momentum's boxes land during phase B
+  };
+
+  // rows of the first momentum
+  {
+    bool ok = true;
+    if (q_begin < q_end) {
+      if constexpr (TMA) ok = mbar_wait_timed(mb, 0u, RWAIT_NS);
+      if (ok) phase_a(E0);
+    }
+    if (__syncthreads_or(!ok)) {
+      give_up(0u, !skip_first);
+      return;
+    }
+    if (q_begin + 1 < q_end) stage_slabs(q_begin + 1);
+  }
+
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s_begin = ck.seg_base[w], s_end = ck.seg_base[w + 1];
+  // the warp's records: steps [SEG[s_begin].sbeg, SEG[s_end - 1].send), the same for every momentum; the
+  // first RPREF of them stay in registers, the rest are read RPREF steps ahead (the table has RPREF
+  // padding steps after its last chunk)
+  const int st_a = s_begin < s_end ? SEG[s_begin].sbeg : 0, st_b = s_begin < s_end ? SEG[s_end - 1].send : 0;
+  const unsigned* const R0 = rec + ck.rec_off + st_a * 32 + lane;
+  unsigned first[RPREF];
+#pragma unroll
+  for (int k = 0; k < RPREF; ++k) first[k] = __ldg(R0 + 32 * k);
+  for (long long q = q_begin; q < q_end; ++q) {
+    const int b = (int)((q - q_begin) & 1), eb = nbuf == 2 ? b : 0;
+    const float4* const E1 = E0 + 2 * eb * nrow;
+    const float4* const E2 = E1 + nrow1;
+    float2* const out_w = OUT0 + b * nslot * 64 + (ck.out_base[w] - ck.cfirst[w]) * 64;
+    // ---- phase B(q): products of the rows over the records ----
+    {
+      float acc[32];  // complex 4 alpha1 + alpha2 as floats 2 c, 2 c + 1
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+      unsigned pf[RPREF];
+#pragma unroll
+      for (int k = 0; k < RPREF; ++k) pf[k] = first[k];
+      const unsigned* R = R0 + 32 * RPREF;
+      for (int si = s_begin; si < s_end; ++si) {
+        const RowSeg sg = SEG[si];
+#pragma unroll 1
+        for (int st = sg.sbeg; st < sg.send; ++st) {
+          const unsigned wd = pf[0];
+#pragma unroll
+          for (int k = 0; k < RPREF - 1; ++k) pf[k] = pf[k + 1];
+          pf[RPREF - 1] = __ldg(R);
+          R += 32;
+          const float sc = SC[wd >> 24];
+          const float4* pa = E1 + (wd & 0xFFFu);
+          const float4* pb = E2 + ((wd >> 12) & 0xFFFu);
+          const float4 a0 = pa[0], a1 = pa[nrow], b0 = pb[0], b1 = pb[nrow];
+          const float2 a[4] = {make_float2(a0.x * sc, a0.y * sc), make_float2(a0.z * sc, a0.w * sc),
+                               make_float2(a1.x * sc, a1.y * sc), make_float2(a1.z * sc, a1.w * sc)};
+          const float2 b[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
+                               make_float2(b1.z, b1.w)};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              float2 z = make_float2(acc[2 * (4 * i + j)], acc[2 * (4 * i + j) + 1]);
+              cfma<float>(z, a[i], b[j]);
+              acc[2 * (4 * i + j)] = z.x;
+              acc[2 * (4 * i + j) + 1] = z.y;
+            }
+        }
+        rows_flush(acc, lane, out_w + sg.local * 64);
+      }
+    }
+    // ---- phase A(q + 1): this thread's rows, once the slabs of q + 1 have landed ----
+    bool ok = true;
+    const unsigned parity = (unsigned)((q + 1 - q_begin) & 1);
     if (q + 1 < q_end) {
       if constexpr (TMA) {
-        if (threadIdx.x == 0)
-          tma_issue_slabs(&fbmap, smem_u32(SL), NBS_ROW_SLAB * 32u, mb, base1, n1c, (int)(q + 1), base2, n2c,
-                          (int)minus_q(q + 1, L));
+        ok = mbar_wait_timed(mb, parity, RWAIT_NS);
       } else {
-        stage_slabs_async(q + 1);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
       }
+      // one row buffer (or cp.async staging by all threads): every warp finishes B(q) first
+      if (nbuf == 1 || !TMA) __syncthreads();
+      if (ok) phase_a(E0 + 2 * (nbuf == 2 ? b ^ 1 : 0) * nrow);
     }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    // ---- phase B: products of the rows over the records ----
-    float acc[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-    for (int si = s_begin; si < s_end; ++si) {
-      const RowSeg sg = SEG[si];
-      const unsigned* R = REC + sg.sbeg * 32 + lane;
-#pragma unroll 1
-      for (int st = sg.sbeg; st < sg.send; ++st, R += 32) {
-        const unsigned wd = *R;
-        const float sc = SC[wd & 31u];
-        const float4* pa = reinterpret_cast<const float4*>(E1b + (wd & 0xFFE0u));
-        const float4* pb = reinterpret_cast<const float4*>(E2b + (wd >> 16));
-        const float4 a0 = pa[0], a1 = pa[1], b0 = pb[0], b1 = pb[1];
-        const float2 a[4] = {make_float2(a0.x * sc, a0.y * sc), make_float2(a0.z * sc, a0.w * sc),
-                             make_float2(a1.x * sc, a1.y * sc), make_float2(a1.z * sc, a1.w * sc)};
-        const float2 b[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
-                             make_float2(b1.z, b1.w)};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            float2 z = make_float2(acc[2 * (4 * i + j)], acc[2 * (4 * i + j) + 1]);
-            cfma<float>(z, a[i], b[j]);
-            acc[2 * (4 * i + j)] = z.x;
-            acc[2 * (4 * i + j) + 1] = z.y;
-          }
-      }
-      rows_flush(acc, lane, out_w + sg.local * 64);
+    if (__syncthreads_or(!ok)) {
+      give_up(parity, true);
+      return;
     }
-    __syncthreads();
-    // ---- the channels' sums, slots in warp order ----
+    // every thread is past B(q) and A(q + 1): the slab buffer is free for q + 2
+    if (q + 2 < q_end) stage_slabs(q + 2);
+    // ---- the channels' sums of q, slots in warp order ----
+    float2* const OUTb = OUT0 + b * nslot * 64;
     for (int i = threadIdx.x; i < nch * 64; i += NT) {
       const int c = i >> 6, m = i & 63;
       float2 sum = make_float2(0.f, 0.f);
       for (int k = CS[c]; k < CS[c + 1]; ++k) {
-        float2& v = OUT[SLT[k] * 64 + m];
+        float2& v = OUTb[SLT[k] * 64 + m];
         sum.x += v.x;
         sum.y += v.y;
         v = make_float2(0.f, 0.f);
@@ -292,17 +374,40 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_rows(
       const int spin = (m & ~3) | ((m & 1) << 1) | ((m >> 1) & 1);  // [a1][a2][a3 + 2 a4] -> [a1][a2][a3][a4]
       Ft[((long long)GC[c] * 64 + spin) * V + q] = sum;
     }
-    if constexpr (!TMA) {
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-      __syncthreads();
-    }
   }
 }
 
 }  // namespace
 
-size_t row_chunk_smem(int nrow, int naent, int nstep, int nslot, int nseg, int nch) {
-  return 128 + row_layout(nrow, naent, nstep, nslot, nseg, nch).total;
+size_t row_chunk_smem(int nbuf, int nrow, int nadesc, int naent, int nslot, int nseg, int nch) {
+  return 128 + row_layout(nbuf, nrow, nadesc, naent, nslot, nseg, nch).total;
+}
+
+using EncodeTiledRows = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                     const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The stored blocks [cell][momentum][8 floats] seen as a 4-D FP32 tensor (4 floats; cells, stride V * 32
+// bytes; halves, stride 16; momenta, stride 32) with boxes of 4 x NBS_ROW_BOX x 2 x 1: one box is
+// NBS_ROW_BOX cells of one momentum, both halves, landing as [half][cell][16 bytes].  false if TMA is not
+// available (the kernel then stages with cp.async).
+static bool encode_fb_map_planar(CUtensorMap* map, const float2* FB, long long V, long long ncells) {
+  static EncodeTiledRows fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+        qr != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiledRows>(p);
+  }();
+  if (!fn || !FB || (reinterpret_cast<uintptr_t>(FB) & 15) || V <= 0 || ncells <= 0 || V > (1LL << 31)) return false;
+  const cuuint64_t dim[4] = {4, (cuuint64_t)ncells, 2, (cuuint64_t)V};
+  const cuuint64_t stride[3] = {(cuuint64_t)V * 32, 16, 32};
+  const cuuint32_t box[4] = {4, (cuuint32_t)NBS_ROW_BOX, 2, 1};
+  const cuuint32_t estride[4] = {1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float2*>(FB), dim, stride, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 cudaError_t launch_contract_rows(const float2* FB, long long ncells, int L, int nchunks, int qb, const void* chunks,
@@ -315,7 +420,7 @@ cudaError_t launch_contract_rows(const float2* FB, long long ncells, int L, int 
   if (nqb * nchunks > 2147483647LL) return cudaErrorInvalidValue;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
-  const bool tma = encode_fb_map(&map, FB, V, ncells);
+  const bool tma = encode_fb_map_planar(&map, FB, V, ncells);
   auto kern = tma ? k_contract_rows<NBS_ROW_WARPS, true> : k_contract_rows<NBS_ROW_WARPS, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

@@ -929,6 +929,7 @@ int nbs_plan_row_sizes(const nbs_plan* p, long long* s) {
   s[NBS_PRS_NCH] = (long long)P.row_ch.size();
   s[NBS_PRS_NSEGS] = (long long)P.row_segs.size();
   s[NBS_PRS_SMEM] = P.row_smem;
+  s[NBS_PRS_WARPS] = NBS_ROW_WARPS;
   return NBS_OK;
 }
 
@@ -997,7 +998,7 @@ int nbs_plan_export(const nbs_plan* p, int what, void* dst) {
       if (P.chunks_ok) std::memcpy(I, P.quad_segs.data(), P.quad_segs.size() * sizeof(QuadSeg));
       return NBS_OK;
     case NBS_PX_ROWCHUNKS:
-      static_assert(sizeof(RowChunkHdr) == 80 * sizeof(int), "row chunk header layout");
+      static_assert(sizeof(RowChunkHdr) == 96 * sizeof(int), "row chunk header layout");
       std::memcpy(I, P.row_chunks.data(), P.row_chunks.size() * sizeof(RowChunkHdr));
       return NBS_OK;
     case NBS_PX_ROWAENT: std::memcpy(dst, P.row_aent.data(), P.row_aent.size() * 2); return NBS_OK;

@@ -125,23 +125,25 @@ struct QuadSeg { int form, t1, t2, kbeg, kend, local, n1, n2; };
 // output source-spin pair s and the scale m1 m2 sign1 sign2 (a code into
 // Plan::row_scales).  Lane 4 kq + s of a warp takes record (8 step + kq, s),
 // so a warp step covers eight shared indices of all four s.
-#define NBS_ROW_WARPS 16
+#define NBS_ROW_WARPS 24
 #define NBS_ROW_SLAB 944            // cells per slab side in shared memory
-#define NBS_ROW_MAX_ROWS 2047       // rows per side (11-bit row index)
+#define NBS_ROW_BOX 236             // cells per TMA box (four boxes per side)
+#define NBS_ROW_MAX_ROWS 4095       // row slots per side (12-bit row index in a record)
 #define NBS_ROW_SCALES 32           // scale codes (code 31 = 0)
 #define NBS_ROW_SMEM_LIMIT 232448   // shared memory per block the tables are cut for (GB300 opt-in)
 struct RowChunkHdr {
   int base1, ncell1, base2, ncell2;  // the group's two stored types
-  int nrow1, nrow2;                  // distinct rows of B1 (at q) and of B2 (at -q)
+  int nrow1, nrow2;                  // row slots of B1 (at q) and of B2 (at -q), multiples of 8
   int aent_off, naent;               // phase-A entries (uint16) into Plan::row_aent
-  int adesc_off;                     // nrow1 + nrow2 row descriptors into Plan::row_adesc
+  int adesc_off, nadesc;             // phase-A row descriptors (one per distinct row) into Plan::row_adesc
   int rec_off, nstep;                // 32 records (uint32) per step into Plan::row_rec
   int ch_off, nch;                   // chunk channels into Plan::row_ch (request-order indices)
   int nslot, seg_off, smem;          // per-warp partial-sum slots; segments into Plan::row_segs; bytes
+  int nbuf;                          // row buffers: 2 (phase A of q + 1 overlaps phase B of q) or 1
   int seg_base[NBS_ROW_WARPS + 1];   // warp w walks segments seg_base[w] .. seg_base[w + 1] (relative)
   int out_base[NBS_ROW_WARPS + 1];   // its slots start at out_base[w] (chunk-local channel - cfirst[w])
   int cfirst[NBS_ROW_WARPS];
-  int pad[14];                       // 80 ints
+  int pad[4];                        // 96 ints
 };
 // Steps [sbeg, send) of chunk-local channel `local` (one flush at the end).
 struct RowSeg { int sbeg, send, local, pad; };
@@ -171,9 +173,9 @@ struct Plan {
   int max_quad_segs = 0;                      // most segments of one chunk
   bool rows_ok = false;                       // every chunk of the two-phase tables fits shared memory
   std::vector<RowChunkHdr> row_chunks;
-  std::vector<unsigned short> row_aent;       // slab cell (bits 0..10) | coefficient code (bits 11..12: +1 -1 +2 -2)
-  std::vector<unsigned> row_adesc;            // entry offset within the chunk (bits 0..19) | count << 20
-  std::vector<unsigned> row_rec;              // code (bits 0..4) | B1 row << 5 | B2 row << 21
+  std::vector<unsigned short> row_aent;       // planar slab unit (bits 0..11) | coefficient code (bits 12..13: +1 -1 +2 -2)
+  std::vector<unsigned> row_adesc;            // entry offset in the chunk (bits 0..13) | count << 14 | row << 19
+  std::vector<unsigned> row_rec;              // B1 row (bits 0..11) | B2 row << 12 | scale code << 24
   std::vector<int> row_ch;
   std::vector<RowSeg> row_segs;
   std::vector<double> row_scales;             // NBS_ROW_SCALES signed scales, code 31 = 0
@@ -194,7 +196,7 @@ std::string compile_plan(const std::vector<int>& channel_ids, Plan& out, int nfl
 // Two-phase contraction tables (plan_rows.cpp); smem_limit: bytes per block.
 void build_row_chunks(Plan& plan, int smem_limit);
 // Shared memory of one chunk of the two-phase contraction (kernels_rows.cu layout).
-size_t row_chunk_smem(int nrow, int naent, int nstep, int nslot, int nseg, int nch);
+size_t row_chunk_smem(int nbuf, int nrow, int nadesc, int naent, int nslot, int nseg, int nch);
 
 // Set the text that nbs_last_error(NULL) returns on this thread.
 void set_global_error(const std::string& msg);

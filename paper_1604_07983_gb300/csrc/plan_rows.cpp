@@ -28,6 +28,13 @@ namespace {
 
 int held_count(int shape) { return 1 << ((shape & 1) + ((shape >> 1) & 1)); }
 
+// 16-byte unit of sink spins 0, 1 of cell `cell` of slab side `side` in the kernel's planar slab: each
+// side is four TMA boxes of NBS_ROW_BOX cells, a box holding spins 0, 1 of its cells, then spins 2, 3
+// (the unit of spins 2, 3 is NBS_ROW_BOX further)
+int slab_unit(int side, int cell) {
+  return side * 2 * NBS_ROW_SLAB + (cell / NBS_ROW_BOX) * 2 * NBS_ROW_BOX + cell % NBS_ROW_BOX;
+}
+
 // held source spins (h1 of B1's list, h2 of B2's) feeding output pair s = alpha3 + 2 alpha4;
 // shape bit 0: alpha3's projector on B1, bit 1: alpha4's projector on B1
 void held_of(int shape, int s, int& h1, int& h2) {
@@ -75,7 +82,7 @@ bool term_rows(const Plan& P, const TermHdr& th, int base1, int base2, TermRows&
     const int n = side ? th.n2 : th.n1, nh = side ? nh2 : nh1, off = side ? th.off2 : th.off1;
     const std::vector<int>& cells = side ? P.ent2_cell : P.ent1_cell;
     const std::vector<double>& coefs = side ? P.ent2_coef : P.ent1_coef;
-    const int base = side ? base2 : base1, shift = side ? NBS_ROW_SLAB : 0;
+    const int base = side ? base2 : base1;
     double m = 0;
     for (int i = 0; i < th.K * n * nh; ++i) {
       const double a = std::fabs(coefs[off + i]);
@@ -104,7 +111,7 @@ bool term_rows(const Plan& P, const TermHdr& th, int base1, int base2, TermRows&
             why = "stored type larger than a slab side";
             return false;
           }
-          r.key.push_back({cell + shift, iq});
+          r.key.push_back({slab_unit(side, cell), iq});
         }
         if (r.key.empty()) continue;
         r.empty = false;
@@ -184,6 +191,53 @@ std::vector<int> split_steps(const std::vector<int>& step_ch) {
   return starts;  // NBS_ROW_WARPS + 1 step offsets
 }
 
+// Greedy colouring of one side's rows (provisional ids 0..n-1) with 8 colours so that the distinct rows
+// one warp loads in a step (its 32 records) spread evenly over the 8 16-byte bank groups (row mod 8):
+// rows in order of their co-load count, each taking the colour least shared with its coloured co-loads
+// (ties: the least used colour).  idx[r] = colour + 8 * (rank within the colour); npad = 8 * largest
+// class.
+template <typename PRecT>
+void color_rows(const std::vector<PRecT>& prec, int n, int side, std::vector<int>& idx, int& npad) {
+  std::vector<std::map<int, int>> adj(n);
+  const size_t nq = prec.size() / 32;  // warp steps of 32 records
+  for (size_t qi = 0; qi < nq; ++qi) {
+    int rows[32], m = 0;
+    for (int j = 0; j < 32; ++j) {
+      const PRecT& r = prec[qi * 32 + j];
+      const int id = side ? r.r2 : r.r1;
+      if (id < 0) continue;
+      bool dup = false;
+      for (int i = 0; i < m; ++i) dup = dup || rows[i] == id;
+      if (!dup) rows[m++] = id;
+    }
+    for (int a = 0; a < m; ++a)
+      for (int b = 0; b < m; ++b)
+        if (a != b) ++adj[rows[a]][rows[b]];
+  }
+  std::vector<int> order(n), weight(n, 0), color(n, -1);
+  for (int r = 0; r < n; ++r) {
+    order[r] = r;
+    for (auto& kv : adj[r]) weight[r] += kv.second;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return weight[a] > weight[b]; });
+  int used[8] = {};
+  for (int r : order) {
+    long long cost[8] = {};
+    for (auto& kv : adj[r])
+      if (color[kv.first] >= 0) cost[color[kv.first]] += kv.second;
+    int best = 0;
+    for (int c = 1; c < 8; ++c)
+      if (cost[c] < cost[best] || (cost[c] == cost[best] && used[c] < used[best])) best = c;
+    color[r] = best;
+    ++used[best];
+  }
+  int rank[8] = {}, big = 0;
+  idx.assign(n, 0);
+  for (int r = 0; r < n; ++r) idx[r] = color[r] + 8 * rank[color[r]]++;
+  for (int c = 0; c < 8; ++c) big = std::max(big, used[c]);
+  npad = std::max(8, 8 * big);
+}
+
 }  // namespace
 
 void build_row_chunks(Plan& plan, int smem_limit) {
@@ -241,9 +295,14 @@ void build_row_chunks(Plan& plan, int smem_limit) {
         (void)ci;
         const int st = steps + ch_steps(c1);
         const int nch = c1 - c0 + 1;
-        const int nrow = (int)std::max<size_t>(t1.keys.size(), 1) + (int)std::max<size_t>(t2.keys.size(), 1);
-        const size_t sm = row_chunk_smem(nrow, (int)(t1.entries + t2.entries + 16), st, nch + NBS_ROW_WARPS,
-                                         nch + NBS_ROW_WARPS, nch);
+        // the bank colouring pads each side's rows to 8 equal colour classes: allow for it
+        const int nd = (int)(t1.keys.size() + t2.keys.size());
+        const int nrow = (int)(1.1 * (double)nd) + 32;
+        // two row buffers where they fit, else one (a channel alone may need one)
+        const int ne = (int)(t1.entries + t2.entries + 16);
+        size_t sm = row_chunk_smem(2, nrow, nd, ne, nch + NBS_ROW_WARPS, nch + NBS_ROW_WARPS, nch);
+        if (sm > (size_t)smem_limit && c1 == c0)
+          sm = row_chunk_smem(1, nrow, nd, ne, nch + NBS_ROW_WARPS, nch + NBS_ROW_WARPS, nch);
         if (c1 > c0 && (sm > (size_t)smem_limit || (int)t1.keys.size() > NBS_ROW_MAX_ROWS ||
                         (int)t2.keys.size() > NBS_ROW_MAX_ROWS))
           break;
@@ -270,48 +329,13 @@ void build_row_chunks(Plan& plan, int smem_limit) {
       h.ncell1 = g.ncell1;
       h.base2 = g.base2;
       h.ncell2 = g.ncell2;
-      // row order: longest lists first (warp-uniform trip counts in phase A); an all-zero
-      // placeholder row where a side has none
-      auto order = [](SideRows& s, std::vector<int>& idx_of) {
-        std::vector<int> ord(s.keys.size());
-        for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
-        std::stable_sort(ord.begin(), ord.end(),
-                         [&](int a, int b) { return s.keys[a]->size() > s.keys[b]->size(); });
-        idx_of.assign(ord.size(), 0);
-        for (size_t i = 0; i < ord.size(); ++i) idx_of[ord[i]] = (int)i;
-        return ord;
-      };
-      std::vector<int> idx1, idx2;
-      const std::vector<int> ord1 = order(s1, idx1), ord2 = order(s2, idx2);
-      h.nrow1 = std::max<int>((int)ord1.size(), 1);
-      h.nrow2 = std::max<int>((int)ord2.size(), 1);
-      h.adesc_off = (int)plan.row_adesc.size();
-      h.aent_off = (int)plan.row_aent.size();
-      auto emit_rows = [&](SideRows& s, const std::vector<int>& ord) {
-        if (ord.empty()) {
-          plan.row_adesc.push_back(0u);  // count 0: a zero row
-          return;
-        }
-        for (int r : ord) {
-          const RowKey& k = *s.keys[r];
-          const unsigned off = (unsigned)(plan.row_aent.size() - h.aent_off);
-          plan.row_adesc.push_back(off | (unsigned)k.size() << 20);
-          for (auto& e : k) {
-            const unsigned code = (e.second < 0 ? 1u : 0u) | (std::abs(e.second) == 2 ? 2u : 0u);
-            plan.row_aent.push_back((unsigned short)(e.first | code << 11));
-          }
-        }
-      };
-      emit_rows(s1, ord1);
-      emit_rows(s2, ord2);
-      h.naent = (int)plan.row_aent.size() - h.aent_off;
-      while ((plan.row_aent.size() - h.aent_off) % 8) plan.row_aent.push_back(0);
-      while ((plan.row_adesc.size() - h.adesc_off) % 4) plan.row_adesc.push_back(0u);
-      // records, channel by channel, each padded to whole steps
-      h.rec_off = (int)plan.row_rec.size();
+      // records with provisional row ids (insertion order of s1, s2), channel by channel, each padded
+      // to whole steps; -1 marks a record with no product
+      struct PRec { int code, r1, r2; };
+      std::vector<PRec> prec;
+      std::vector<int> step_ch;
       h.ch_off = (int)plan.row_ch.size();
       h.nch = c1 - c0;
-      std::vector<int> step_ch;
       for (int c = c0; c < c1; ++c) {
         const int local = c - c0;
         plan.row_ch.push_back(plan.group_ch[g.ch_off + c]);
@@ -327,26 +351,116 @@ void build_row_chunks(Plan& plan, int smem_limit) {
               held_of(th.shape, s, h1, h2);
               const RowOf& a = tr.r1[(size_t)k * nh1 + h1];
               const RowOf& b = tr.r2[(size_t)k * nh2 + h2];
-              unsigned w = NBS_ROW_SCALES - 1;
+              PRec r = {NBS_ROW_SCALES - 1, -1, -1};
               if (!a.empty && !b.empty) {
-                const int code = scale_code(scales, tr.m1 * tr.m2 * a.sign * b.sign, why);
-                if (code < 0) {
+                r.code = scale_code(scales, tr.m1 * tr.m2 * a.sign * b.sign, why);
+                if (r.code < 0) {
                   plan.row_why = why;
                   return;
                 }
-                w = (unsigned)code | (unsigned)idx1[s1.id.at(a.key)] << 5 | (unsigned)idx2[s2.id.at(b.key)] << 21;
+                r.r1 = s1.id.at(a.key);
+                r.r2 = s2.id.at(b.key);
               }
-              plan.row_rec.push_back(w);
+              prec.push_back(r);
             }
             ++nrec;
           }
         }
         while (nrec % 8) {
-          for (int s = 0; s < 4; ++s) plan.row_rec.push_back(NBS_ROW_SCALES - 1);
+          for (int s = 0; s < 4; ++s) prec.push_back({NBS_ROW_SCALES - 1, -1, -1});
           ++nrec;
         }
         for (long long i = 0; i < nrec / 8; ++i) step_ch.push_back(local);
       }
+      // row numbers: the eight rows a quarter warp reads in one 16-byte load (steps of eight shared
+      // indices, lanes 4 kq + s, quarter p = kq >> 1) should fall in different 16-byte bank groups,
+      // i.e. differ mod 8 (planar row halves); greedy colouring with 8 colours, then row = colour + 8 k
+      std::vector<int> idx1, idx2;
+      int nr1p = 0, nr2p = 0;
+      color_rows(prec, (int)s1.keys.size(), 0, idx1, nr1p);
+      color_rows(prec, (int)s2.keys.size(), 1, idx2, nr2p);
+      if (nr1p > NBS_ROW_MAX_ROWS || nr2p > NBS_ROW_MAX_ROWS) {
+        plan.row_why = "too many rows after bank colouring";
+        return;
+      }
+      h.nrow1 = nr1p;
+      h.nrow2 = nr2p;
+      h.rec_off = (int)plan.row_rec.size();
+      for (const PRec& r : prec) {
+        if (r.r1 < 0) plan.row_rec.push_back((unsigned)(NBS_ROW_SCALES - 1) << 24);
+        else plan.row_rec.push_back((unsigned)idx1[r.r1] | (unsigned)idx2[r.r2] << 12 | (unsigned)r.code << 24);
+      }
+      // phase-A descriptors, longest lists first (warp-uniform trip counts): entry offset | count << 14 |
+      // target row << 19 (B2's rows after B1's nrow1)
+      h.adesc_off = (int)plan.row_adesc.size();
+      h.aent_off = (int)plan.row_aent.size();
+      std::vector<std::pair<int, int>> all;  // (side, provisional id)
+      for (int i = 0; i < (int)s1.keys.size(); ++i) all.push_back({0, i});
+      for (int i = 0; i < (int)s2.keys.size(); ++i) all.push_back({1, i});
+      // longest lists first (warp-uniform trip counts); within one length, batches of 32 rows (one warp
+      // instruction) picked greedily so that their store targets (row slot mod 8) and, for each entry
+      // position, their slab units (mod 8) spread over the 16-byte bank groups
+      auto target_of = [&](const std::pair<int, int>& x) {
+        return x.first ? nr1p + idx2[x.second] : idx1[x.second];
+      };
+      auto key_of = [&](const std::pair<int, int>& x) -> const RowKey& { return *(x.first ? s2 : s1).keys[x.second]; };
+      std::stable_sort(all.begin(), all.end(), [&](const std::pair<int, int>& x, const std::pair<int, int>& y) {
+        return key_of(x).size() > key_of(y).size();
+      });
+      {
+        std::vector<std::pair<int, int>> ordered;
+        ordered.reserve(all.size());
+        for (size_t i = 0; i < all.size();) {
+          size_t j = i;
+          while (j < all.size() && key_of(all[j]).size() == key_of(all[i]).size()) ++j;
+          std::vector<char> taken(j - i, 0);
+          size_t left = j - i, first = i;
+          while (left) {
+            int tc[8] = {}, gc[32][8] = {};
+            for (int pick = 0; pick < 32 && left; ++pick) {
+              while (taken[first - i]) ++first;
+              long best = -1, bestcost = 0;
+              int scanned = 0;
+              // quadratic in the bank-group counts: a load takes as many wavefronts as its fullest group
+              for (size_t k = first; k < j && scanned < 256; ++k) {
+                if (taken[k - i]) continue;
+                ++scanned;
+                const RowKey& kk = key_of(all[k]);
+                const int t = tc[target_of(all[k]) & 7];
+                long cost = 2L * (2 * t + 1);
+                for (size_t e = 0; e < kk.size() && e < 32; ++e) cost += 2 * gc[e][kk[e].first & 7] + 1;
+                if (best < 0 || cost < bestcost) { best = (long)k; bestcost = cost; }
+              }
+              taken[best - i] = 1;
+              --left;
+              const RowKey& kk = key_of(all[best]);
+              ++tc[target_of(all[best]) & 7];
+              for (size_t e = 0; e < kk.size() && e < 32; ++e) ++gc[e][kk[e].first & 7];
+              ordered.push_back(all[best]);
+            }
+          }
+          i = j;
+        }
+        all.swap(ordered);
+      }
+      h.nadesc = (int)all.size();
+      for (auto& r : all) {
+        const RowKey& k = *(r.first ? s2 : s1).keys[r.second];
+        const unsigned off = (unsigned)(plan.row_aent.size() - h.aent_off);
+        const unsigned target = r.first ? (unsigned)(nr1p + idx2[r.second]) : (unsigned)idx1[r.second];
+        if (off >= (1u << 14) || k.size() >= 32) {
+          plan.row_why = "row entry table of a chunk beyond its descriptor fields";
+          return;
+        }
+        plan.row_adesc.push_back(off | (unsigned)k.size() << 14 | target << 19);
+        for (auto& e : k) {
+          const unsigned code = (e.second < 0 ? 1u : 0u) | (std::abs(e.second) == 2 ? 2u : 0u);
+          plan.row_aent.push_back((unsigned short)(e.first | code << 12));
+        }
+      }
+      h.naent = (int)plan.row_aent.size() - h.aent_off;
+      while ((plan.row_aent.size() - h.aent_off) % 8) plan.row_aent.push_back(0);
+      while ((plan.row_adesc.size() - h.adesc_off) % 4) plan.row_adesc.push_back(0u);
       h.nstep = (int)step_ch.size();
       // warps and their segments
       const std::vector<int> starts = split_steps(step_ch);
@@ -370,7 +484,13 @@ void build_row_chunks(Plan& plan, int smem_limit) {
       h.seg_base[NBS_ROW_WARPS] = (int)plan.row_segs.size() - h.seg_off;
       h.out_base[NBS_ROW_WARPS] = nslot;
       h.nslot = nslot;
-      h.smem = (int)row_chunk_smem(h.nrow1 + h.nrow2, h.naent, h.nstep, h.nslot, h.seg_base[NBS_ROW_WARPS], h.nch);
+      h.nbuf = 2;
+      h.smem = (int)row_chunk_smem(2, h.nrow1 + h.nrow2, h.nadesc, h.naent, h.nslot, h.seg_base[NBS_ROW_WARPS], h.nch);
+      if (h.smem > smem_limit) {
+        h.nbuf = 1;
+        h.smem =
+            (int)row_chunk_smem(1, h.nrow1 + h.nrow2, h.nadesc, h.naent, h.nslot, h.seg_base[NBS_ROW_WARPS], h.nch);
+      }
       if (h.smem > smem_limit) {
         plan.row_why = "a chunk exceeds a block's shared memory";
         return;
@@ -380,6 +500,8 @@ void build_row_chunks(Plan& plan, int smem_limit) {
       c0 = c1;
     }
   }
+  // the kernel reads each warp's records a few steps ahead of use: padding steps after the last chunk
+  plan.row_rec.insert(plan.row_rec.end(), 4 * 32, (unsigned)(NBS_ROW_SCALES - 1) << 24);
   plan.row_scales.assign(NBS_ROW_SCALES, 0.0);
   for (size_t i = 0; i < scales.size(); ++i) plan.row_scales[i] = scales[i];
   plan.rows_ok = !plan.row_chunks.empty();

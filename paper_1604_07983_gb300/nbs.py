@@ -159,12 +159,12 @@ def plan_tables(channel_ids, flavours: int = 2):
 def row_tables(L, p, get):
     """The two-phase contraction's tables (None where they do not fit shared memory)."""
     import numpy as np
-    rs = (ctypes.c_longlong * 8)()
+    rs = (ctypes.c_longlong * 9)()
     _check(L.nbs_plan_row_sizes(p, rs))
-    ok, nck, naent, nadesc, nrec, nch, nseg, smem = list(rs)
+    ok, nck, naent, nadesc, nrec, nch, nseg, smem, warps = list(rs)
     if not ok:
         return None
-    return dict(chunks=get("ROWCHUNKS", (nck, 80), np.int32), aent=get("ROWAENT", (max(naent, 1),), np.uint16),
+    return dict(warps=warps, chunks=get("ROWCHUNKS", (nck, 96), np.int32), aent=get("ROWAENT", (max(naent, 1),), np.uint16),
                 adesc=get("ROWADESC", (max(nadesc, 1),), np.uint32), rec=get("ROWREC", (max(nrec, 1),), np.uint32),
                 ch=get("ROWCH", (max(nch, 1),), np.int32), segs=get("ROWSEGS", (max(nseg, 1), 4), np.int32),
                 scales=get("ROWSCALES", (32,), np.float64), smem=smem)

@@ -474,27 +474,31 @@ def test_row_tables_reproduce_the_term_products(lib, ids):
     got = np.zeros_like(want)
     assert np.count_nonzero(rt["scales"][:31]) <= 31 and rt["scales"][31] == 0
     for ck in rt["chunks"]:
-        base1, ncell1, base2, ncell2, nrow1, nrow2, aent_off, naent, adesc_off, rec_off, nstep, ch_off, nch_c, \
-            nslot = (int(x) for x in ck[:14])
-        seg_off, smem = int(ck[14]), int(ck[15])
-        seg_base, out_base, cfirst = ck[16:33], ck[33:50], ck[50:66]
-        assert smem <= rt["smem"] <= 232448 and nrow1 <= 2047 and nrow2 <= 2047
-        slab = np.zeros((2 * 944, 4), complex)
-        slab[:ncell1] = A[base1:base1 + ncell1]
-        slab[944:944 + ncell2] = B[base2:base2 + ncell2]
-        E = np.zeros((nrow1 + nrow2, 4), complex)
-        for r in range(nrow1 + nrow2):
-            d = int(rt["adesc"][adesc_off + r])
-            off, cnt = d & 0xFFFFF, d >> 20
+        base1, ncell1, base2, ncell2, nrow1, nrow2, aent_off, naent, adesc_off, nadesc, rec_off, nstep, ch_off, \
+            nch_c, nslot, seg_off, smem, nbuf = (int(x) for x in ck[:18])
+        W = rt["warps"]
+        seg_base, out_base, cfirst = ck[18:19 + W], ck[19 + W:20 + 2 * W], ck[20 + 2 * W:20 + 3 * W]
+        assert nbuf in (1, 2)
+        assert smem <= rt["smem"] <= 232448 and nrow1 % 8 == 0 and nrow2 % 8 == 0 and max(nrow1, nrow2) <= 4095
+        # planar slab units: side s, cell c -> 16-byte unit of sink spins 0, 1 (spins 2, 3 236 units on)
+        unit = lambda side, c: side * 1888 + (c // 236) * 472 + c % 236
+        slab = np.full((4096, 4), np.nan, complex)
+        c1, c2 = np.arange(ncell1), np.arange(ncell2)
+        slab[unit(0, c1)] = A[base1 + c1]
+        slab[unit(1, c2)] = B[base2 + c2]
+        E = np.full((nrow1 + nrow2, 4), np.nan, complex)   # row slots no descriptor writes stay NaN
+        for d in rt["adesc"][adesc_off:adesc_off + nadesc].astype(np.int64):
+            off, cnt, r = d & 0x3FFF, (d >> 14) & 31, d >> 19
             e = rt["aent"][aent_off + off: aent_off + off + cnt].astype(np.int64)
-            if r < nrow1:
-                assert np.all((e & 0x7FF) < ncell1)
-            else:
-                assert np.all(((e & 0x7FF) >= 944) & ((e & 0x7FF) < 944 + ncell2))
-            E[r] = (coef[(e >> 11) & 3][:, None] * slab[e & 0x7FF]).sum(axis=0)
+            side_of = (e & 0xFFF) >= 1888
+            assert np.all(side_of == (r >= nrow1))     # B1's rows read side 1, B2's side 2
+            assert np.isnan(E[r]).all()   # each row slot written once
+            v = slab[e & 0xFFF]
+            assert np.isfinite(v).all()   # every unit names a staged cell
+            E[r] = (coef[(e >> 12) & 3][:, None] * v).sum(axis=0)
         rec = rt["rec"][rec_off: rec_off + 32 * nstep].astype(np.int64).reshape(nstep, 8, 4)
         seen = np.zeros(nstep, int)
-        for w in range(16):
+        for w in range(W):
             segs = rt["segs"][seg_off + seg_base[w]: seg_off + seg_base[w + 1]]
             for sb, se, local, _ in segs:
                 assert cfirst[w] <= local < cfirst[w] + out_base[w + 1] - out_base[w]
@@ -504,8 +508,43 @@ def test_row_tables_reproduce_the_term_products(lib, ids):
                     for kq in range(8):
                         for s in range(4):
                             wd = rec[st, kq, s]
-                            r1, r2, code = (wd >> 5) & 0x7FF, wd >> 21, wd & 31
+                            r1, r2, code = wd & 0xFFF, (wd >> 12) & 0xFFF, wd >> 24
+                            if code == 31:
+                                continue
                             assert r1 < nrow1 and r2 < nrow2
                             got[ch, :, :, s] += rt["scales"][code] * np.outer(E[r1], E[nrow1 + r2])
         assert np.all(seen == 1)
     assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_row_loads_spread_over_the_banks_warp_wide(lib):
+    """Shared-memory wavefronts of the two-phase kernel's 16-byte loads, warp-wide (a load takes as many
+    wavefronts as its fullest 16-byte bank group has distinct addresses; ideal ceil(distinct / 8)): phase B's
+    row loads (rows numbered by colouring each warp step's rows over the groups) within 1.25x of ideal,
+    phase A's slab loads (rows batched 32 per warp instruction to spread the j-th entries' slab units)
+    within 1.7x, for the 52-channel tables.  Rows numbered in first-use order give about 1.6x and 2.2x."""
+    rt = nbs.plan_tables(list(range(52)))["rows"]
+    for phase in ("A", "B"):
+        act = ideal = 0
+        for ck in rt["chunks"]:
+            nrow1, adesc_off, nadesc, aent_off, rec_off, nstep = (int(ck[i]) for i in (4, 8, 9, 6, 10, 11))
+            if phase == "B":
+                rec = rt["rec"][rec_off: rec_off + 32 * nstep].astype(np.int64).reshape(nstep, 32)
+                groups = []
+                for w in rec:
+                    w = w[(w >> 24) != 31]
+                    groups += [w & 0xFFF, nrow1 + ((w >> 12) & 0xFFF)]
+            else:
+                d = rt["adesc"][adesc_off: adesc_off + nadesc].astype(np.int64)
+                groups = []
+                for w0 in range(0, nadesc, 32):
+                    dd = d[w0:w0 + 32]
+                    for j in range(int(((dd >> 14) & 31).max())):
+                        live = dd[((dd >> 14) & 31) > j]
+                        groups.append(rt["aent"][aent_off + (live & 0x3FFF) + j].astype(np.int64) & 0xFFF)
+            for g in groups:
+                u = np.unique(g)
+                if len(u):
+                    act += np.bincount(u % 8).max()
+                    ideal += -(-len(u) // 8)
+        assert act / ideal <= {"A": 1.7, "B": 1.25}[phase], (phase, act / ideal)
