@@ -184,10 +184,34 @@ std::vector<int> split_steps(const std::vector<int>& step_ch) {
     const double mid = 0.5 * (lo + hi);
     if (fill(mid, nullptr) <= NBS_ROW_WARPS) hi = mid; else lo = mid;
   }
-  std::vector<int> starts;
-  fill(hi, &starts);
-  while ((int)starts.size() < NBS_ROW_WARPS) starts.push_back(n);
-  starts.push_back(n);
+  // spread: warp w takes steps while its cost stays within both the smallest feasible largest cost and
+  // the remaining cost divided by the remaining warps (rounded up to a whole step), so that no warp idles
+  // while another holds the largest share
+  double total = 0;
+  for (int i = n - 1; i >= 0; --i) total += 1.0 + ((i == 0 || step_ch[i] != step_ch[i - 1]) ? kFlush : 0.0);
+  std::vector<int> starts(1, 0);
+  int i = 0;
+  double left = total;
+  for (int w = 0; w < NBS_ROW_WARPS; ++w) {
+    const double target = std::min(hi, left / (NBS_ROW_WARPS - w) + 1.0);
+    double cost = 0;
+    int cur = -1;
+    while (i < n) {
+      const double add = 1.0 + (step_ch[i] != cur ? kFlush : 0.0);
+      if (cost > 0 && cost + add > target) break;
+      cost += add;
+      cur = step_ch[i];
+      ++i;
+    }
+    left = std::max(0.0, left - cost);
+    starts.push_back(i);
+  }
+  if (i < n) {  // fall back to the greedy fill at the feasible cap
+    starts.clear();
+    fill(hi, &starts);
+    while ((int)starts.size() < NBS_ROW_WARPS) starts.push_back(n);
+    starts.push_back(n);
+  }
   return starts;  // NBS_ROW_WARPS + 1 step offsets
 }
 
