@@ -166,7 +166,7 @@ int nbs_zero_momentum(nbs_ctx* h, double* out);
 /* Launch-shape parameters (for tuning; results agree to rounding).
  * NBS_PARAM_CONTRACT_CFG selects the contraction kernel:
  *   0 = default: in FP32, when its tables fit shared memory, the two-phase
- *       row kernel (persistent blocks of 24 warps; per momentum every distinct
+ *       row kernel (persistent blocks of 16 warps; per momentum every distinct
  *       effective-block row of a chunk of channels is built once for all four
  *       sink spins, Eq. (4.2), then each lane forms the 4 x 4 sink-spin outer
  *       products of one shared index and one source-spin pair, Eq. (4.3)),

@@ -1,7 +1,7 @@
 // kernels_rows.cu -- the effective blocks (Eq. (4.2)) and their product
 // (Eq. (4.3)) in two phases per momentum, FP32.
 //
-// A CTA of 24 warps keeps one chunk's row tables in shared memory
+// A CTA of 16 warps keeps one chunk's row tables in shared memory
 // (plan_rows.cpp) and sweeps a block of momenta:
 //   * phase A(q): each thread builds whole effective-block rows, sums of
 //     +-1 / +-2 times cells of the two staged slabs (B1's stored type at q,
@@ -38,7 +38,7 @@ namespace {
 
 constexpr unsigned RSLAB_BYTES = 2u * NBS_ROW_SLAB * 32u;
 constexpr unsigned long long RWAIT_NS = 1000000000ull;  // slab wait limit (global timer)
-constexpr int RPREF = 4;                                  // records loaded ahead (steps)
+constexpr int RPREF = 3;                                  // records of a warp's first steps kept in registers
 
 struct RowLayout {
   unsigned e, aent, adesc, out, seg, sc, cs, mb, total;
@@ -303,42 +303,72 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_rows(
     const float4* const E2 = E1 + nrow1;
     float2* const out_w = OUT0 + b * nslot * 64 + (ck.out_base[w] - ck.cfirst[w]) * 64;
     // ---- phase B(q): products of the rows over the records ----
+    // two steps per iteration with two operand sets: the rows of step st + 1 are loaded while step st's
+    // products run (and those of st + 2 during st + 1's); records are read two steps ahead
     {
       float acc[32];  // complex 4 alpha1 + alpha2 as floats 2 c, 2 c + 1
 #pragma unroll
       for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-      unsigned pf[RPREF];
+      const unsigned* R = R0 + 64;  // record of step st_a + 2
+      unsigned recA = first[0], recB = first[1];
+      float4 xa0, xa1, ya0, ya1, xb0, xb1, yb0, yb1;
+      float sa = 0.f, sb2 = 0.f;
+      auto rows_of = [&](unsigned wd, float4& x0, float4& x1, float4& y0, float4& y1, float& scale) {
+        scale = SC[wd >> 24];
+        const float4* pa = E1 + (wd & 0xFFFu);
+        const float4* pb = E2 + ((wd >> 12) & 0xFFFu);
+        x0 = pa[0];
+        x1 = pa[nrow];
+        y0 = pb[0];
+        y1 = pb[nrow];
+      };
+      auto product = [&](const float4& x0, const float4& x1, const float4& y0, const float4& y1, float scale) {
+        const float2 a[4] = {make_float2(x0.x * scale, x0.y * scale), make_float2(x0.z * scale, x0.w * scale),
+                             make_float2(x1.x * scale, x1.y * scale), make_float2(x1.z * scale, x1.w * scale)};
+        const float2 b[4] = {make_float2(y0.x, y0.y), make_float2(y0.z, y0.w), make_float2(y1.x, y1.y),
+                             make_float2(y1.z, y1.w)};
 #pragma unroll
-      for (int k = 0; k < RPREF; ++k) pf[k] = first[k];
-      const unsigned* R = R0 + 32 * RPREF;
-      for (int si = s_begin; si < s_end; ++si) {
-        const RowSeg sg = SEG[si];
-#pragma unroll 1
-        for (int st = sg.sbeg; st < sg.send; ++st) {
-          const unsigned wd = pf[0];
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int k = 0; k < RPREF - 1; ++k) pf[k] = pf[k + 1];
-          pf[RPREF - 1] = __ldg(R);
-          R += 32;
-          const float sc = SC[wd >> 24];
-          const float4* pa = E1 + (wd & 0xFFFu);
-          const float4* pb = E2 + ((wd >> 12) & 0xFFFu);
-          const float4 a0 = pa[0], a1 = pa[nrow], b0 = pb[0], b1 = pb[nrow];
-          const float2 a[4] = {make_float2(a0.x * sc, a0.y * sc), make_float2(a0.z * sc, a0.w * sc),
-                               make_float2(a1.x * sc, a1.y * sc), make_float2(a1.z * sc, a1.w * sc)};
-          const float2 b[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
-                               make_float2(b1.z, b1.w)};
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              float2 z = make_float2(acc[2 * (4 * i + j)], acc[2 * (4 * i + j) + 1]);
-              cfma<float>(z, a[i], b[j]);
-              acc[2 * (4 * i + j)] = z.x;
-              acc[2 * (4 * i + j) + 1] = z.y;
-            }
+          for (int j = 0; j < 4; ++j) {
+            float2 z = make_float2(acc[2 * (4 * i + j)], acc[2 * (4 * i + j) + 1]);
+            cfma<float>(z, a[i], b[j]);
+            acc[2 * (4 * i + j)] = z.x;
+            acc[2 * (4 * i + j) + 1] = z.y;
+          }
+      };
+      int si = s_begin, seg_end = si < s_end ? SEG[si].send : 0, local = si < s_end ? SEG[si].local : 0;
+      auto after_step = [&](int st) {
+        if (st + 1 == seg_end) {
+          rows_flush(acc, lane, out_w + local * 64);
+          if (++si < s_end) {
+            seg_end = SEG[si].send;
+            local = SEG[si].local;
+          }
         }
-        rows_flush(acc, lane, out_w + sg.local * 64);
+      };
+      if (st_a < st_b) {
+        rows_of(recA, xa0, xa1, ya0, ya1, sa);
+        recA = first[2];
+      }
+#pragma unroll 1
+      for (int st = st_a; st < st_b; st += 2) {
+        // step st in set a (loaded); load set b with step st + 1
+        const bool more = st + 1 < st_b;
+        if (more) {
+          rows_of(recB, xb0, xb1, yb0, yb1, sb2);
+          recB = __ldg(R + 32);  // step st + 3
+        }
+        product(xa0, xa1, ya0, ya1, sa);
+        after_step(st);
+        if (!more) break;
+        if (st + 2 < st_b) {
+          rows_of(recA, xa0, xa1, ya0, ya1, sa);
+          recA = __ldg(R + 64);  // step st + 4
+        }
+        R += 64;
+        product(xb0, xb1, yb0, yb1, sb2);
+        after_step(st + 1);
       }
     }
     // ---- phase A(q + 1): this thread's rows, once the slabs of q + 1 have landed ----

@@ -125,7 +125,7 @@ struct QuadSeg { int form, t1, t2, kbeg, kend, local, n1, n2; };
 // output source-spin pair s and the scale m1 m2 sign1 sign2 (a code into
 // Plan::row_scales).  Lane 4 kq + s of a warp takes record (8 step + kq, s),
 // so a warp step covers eight shared indices of all four s.
-#define NBS_ROW_WARPS 24
+#define NBS_ROW_WARPS 16
 #define NBS_ROW_SLAB 944            // cells per slab side in shared memory
 #define NBS_ROW_BOX 236             // cells per TMA box (four boxes per side)
 #define NBS_ROW_MAX_ROWS 4095       // row slots per side (12-bit row index in a record)
@@ -143,7 +143,7 @@ struct RowChunkHdr {
   int seg_base[NBS_ROW_WARPS + 1];   // warp w walks segments seg_base[w] .. seg_base[w + 1] (relative)
   int out_base[NBS_ROW_WARPS + 1];   // its slots start at out_base[w] (chunk-local channel - cfirst[w])
   int cfirst[NBS_ROW_WARPS];
-  int pad[4];                        // 96 ints
+  int pad[96 - 20 - 3 * NBS_ROW_WARPS];  // 96 ints
 };
 // Steps [sbeg, send) of chunk-local channel `local` (one flush at the end).
 struct RowSeg { int sbeg, send, local, pad; };
