@@ -245,7 +245,9 @@ const char* nbs_last_error(const nbs_ctx* h);
  * pointers (text in nbs_last_error(NULL)); NBS_ENAN; NBS_ECUDA.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and uploads the FFT twiddles; make that first call
- * before any stream capture.  Every call reuses the same array and leaves
+ * before any stream capture.  That set-up is kept for the life of the
+ * process: after cudaDeviceReset the entry is not usable again in the same
+ * process.  Every call reuses the same array and leaves
  * its contents behind; calls that overlap on the GPU (other streams or host
  * threads) race on it and must be serialised by the caller. */
 #define NBS_STATIC_MAX_L 4

@@ -273,12 +273,15 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_tcq(
   for (int i = threadIdx.x; i < ck.nslot * 64; i += NT) OUT[i] = make_float2(0.f, 0.f);
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
-  // a slab wait that gave up: flag it, let thread 0 wait once more (bounded) for
+  // a slab wait that gave up: flag it, let thread 0 wait (bounded) for
   // the boxes in flight, and leave together
   auto give_up = [&](unsigned mb, unsigned parity) {
     if (threadIdx.x == 0) {
       atomicOr(flags, 2);
-      mbar_wait(mb, parity);
+      // the boxes of the buffer given up on may still be in flight: wait for them (up to eight more
+      // seconds of the global timer) before the block's shared memory is released
+      for (int k = 0; k < 8 && !mbar_wait_timed(mb, parity, 1000000000ull); ++k) {
+      }
     }
   };
   if constexpr (TMA) {

@@ -16,8 +16,8 @@ Eq. (2.6) on phase-weighted site sums of the normal blocks), and the direct
 O(V^2) sum of the first equation of Sec. 2 at sampled separations r for a few
 channels.
 
-  python tests/golden/make_expected.py 32     # about 15 minutes on 8 cores
-  python tests/golden/make_expected.py 48     # about 15 minutes, 40 GB of memory
+  python tests/golden/make_expected.py 32     # about 40 minutes on 8 cores (Lambda Lambda: 33)
+  python tests/golden/make_expected.py 48     # about 12 minutes, 40 GB of memory
 """
 
 from __future__ import annotations

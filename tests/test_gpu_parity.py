@@ -4,6 +4,8 @@ Tolerances (normwise per channel and timeslice, ||F_gpu - F_ref|| / ||F_ref||):
 FP64 path 1e-12, FP32 path 2e-5.
 """
 
+import os
+
 import numpy as np
 import pytest
 
@@ -167,21 +169,63 @@ def test_bf16x3_tensor_core_path_all_channels(nbs, cfg):
             assert rel(F[c, t], oracle(names[c], *props[t], L)) < FP32_TOL, (names[c], t)
 
 
+def expected(L):
+    """The oracle's stored values for the L^3 parity case (tests/golden/make_expected.py: momentum
+    projections of every channel, direct O(V^2) sums at sampled r for a few channels) and the case's
+    propagators, regenerated from the same seeded recipe."""
+    e = np.load(os.path.join(os.path.dirname(__file__), "golden", "expected_%dcube_t%d.npz" % (L, {32: 12, 48: 5}[L])))
+    assert int(e["L"]) == L
+    seed, t, decay = int(e["seed"]), int(e["t"]), float(e["decay"])
+    Sl, Ss = I.propagator(seed, "l", L, t, decay), I.propagator(seed, "s", L, t, decay)
+    if bool(e["c64"]):
+        Sl = Sl.astype(np.complex64).astype(np.complex128)
+        Ss = Ss.astype(np.complex64).astype(np.complex128)
+    return e, Sl, Ss
+
+
+def check_against_expected(nbs, e, F, L, tol, what):
+    """F [channel, 1, 4, 4, 2, 2, V] from the GPU against the stored oracle values: for every channel and
+    stored momentum n, sum_r e^{-2 pi i n.r / L} F(r) normwise over the 64 spins; for the stored channels,
+    F at the sampled separations normwise over spins and separations."""
+    names = nbs.channel_names()
+    assert [" ".join(n) for n in names] == [str(x) for x in e["names"]]   # the oracle's own table
+    V = L ** 3
+    s = np.arange(V)
+    x, y, z = s % L, (s // L) % L, s // (L * L)
+    n_list = e["n_list"]
+    ph = np.stack([np.exp(-2j * np.pi * (n[0] * x + n[1] * y + n[2] * z) / L) for n in n_list], axis=1)
+    got = F[:, 0].reshape(len(names), 64, V) @ ph                     # [channel, 64, n]
+    want = e["proj"].reshape(len(names), len(n_list), 64)
+    for c in range(len(names)):
+        for k in range(len(n_list)):
+            assert rel(got[c, :, k], want[c, k]) < tol, (what, names[c], tuple(n_list[k]))
+    idx = [int(r[0] + L * (r[1] + L * r[2])) for r in e["r_list"]]
+    for j, c in enumerate(e["direct_ids"]):
+        assert rel(F[int(c), 0][..., idx], e["direct"][j]) < tol, (what, names[int(c)], "direct sum")
+
+
 def test_precision_table_32cube(nbs, capsys):
-    """Per-channel normwise error of FP32 and split-BF16 x 3 against the FP64 GPU path at 32^3
-    (decaying propagators, a late timeslice), each within 2e-5.  The FP64 GPU path is pinned to the
-    oracle by the other tests (all channels at small L, every r at 8^3, sampled r at 16^3)."""
-    L, t = 32, 12
-    Sl, Ss = I.propagator(1607, "l", L, t, 0.5), I.propagator(1607, "s", L, t, 0.5)
+    """The metric's configuration (32^3, seed 1607, t = 12, exp(-0.5 t)) against the oracle directly: the
+    FP64, FP32 and split-BF16x3 GPU paths, every one of the 52 channels at five momenta (including q = 0,
+    the self-mirror (16, 16, 16) and the contraction's last momentum (31, 31, 31)) and four channels in
+    different chunks at five separations (two seeded at random) by the oracle's direct O(V^2) sum; FP64
+    within 1e-12, the others within 2e-5.  Also the per-channel normwise error table of FP32 and
+    split-BF16x3 against the FP64 GPU path over all r."""
+    L = 32
+    e, Sl, Ss = expected(L)
+    t = int(e["t"])
     names = nbs.channel_names()
     ids = list(range(len(names)))
     F64 = gpu_correlate(nbs, ids, L, [(Sl, Ss)], nbs.NBS_FP64)
+    check_against_expected(nbs, e, F64, L, FP64_TOL, "FP64")
     rows = []
     for mode in (nbs.NBS_FP32, nbs.NBS_BF16X3):
         F = gpu_correlate(nbs, ids, L, [(Sl, Ss)], mode)
+        check_against_expected(nbs, e, F, L, FP32_TOL, mode)
         errs = [rel(F[c, 0], F64[c, 0]) for c in ids]
         rows.append(errs)
         assert max(errs) < FP32_TOL, (mode, names[int(np.argmax(errs))], max(errs))
+        del F
     with capsys.disabled():
         print("\nprecision table 32^3 t=%d: channel, FP32 err, BF16x3 err" % t)
         for c in ids:
@@ -363,18 +407,22 @@ def test_three_flavours_u_ne_d(nbs):
 
 
 def test_48cube_complex64_storage(nbs):
-    """The 48^3 configuration (complex64 propagator storage, e^{-0.4 t} decay): FP32 and split-BF16x3
-    against the FP64 GPU path on the same complex64 inputs, every channel within 2e-5, and the FP32
-    result unchanged by a site-local SU(3) rotation of the sink colour (the blocks are colour singlets)."""
-    L, t = 48, 5
-    Sl = I.propagator(1614, "l", L, t, 0.4).astype(np.complex64)
-    Ss = I.propagator(1614, "s", L, t, 0.4).astype(np.complex64)
+    """The 48^3 configuration (complex64 propagator storage, e^{-0.4 t} decay) against the oracle: every
+    channel at five momenta and pn at two separations by the direct O(V^2) sum, for the FP64 GPU path
+    (1e-12) and the FP32 and split-BF16x3 paths on complex64 storage (2e-5); FP32 and split-BF16x3 against
+    the FP64 GPU path over all r within 2e-5; and the FP32 result unchanged by a site-local SU(3) rotation
+    of the sink colour (the blocks are colour singlets)."""
+    L = 48
+    e, Sl128, Ss128 = expected(L)
     names = nbs.channel_names()
     ids = list(range(len(names)))
-    props = [(Sl.astype(np.complex128), Ss.astype(np.complex128))]
+    props = [(Sl128, Ss128)]
     F64 = gpu_correlate(nbs, ids, L, props, nbs.NBS_FP64)
+    check_against_expected(nbs, e, F64, L, FP64_TOL, "FP64")
     F32 = gpu_correlate(nbs, ids, L, props, nbs.NBS_FP32, c64=True)
+    check_against_expected(nbs, e, F32, L, FP32_TOL, "FP32")
     F16 = gpu_correlate(nbs, ids, L, props, nbs.NBS_BF16X3, c64=True)
+    check_against_expected(nbs, e, F16, L, FP32_TOL, "BF16X3")
     for c in ids:
         assert rel(F32[c, 0], F64[c, 0]) < FP32_TOL, names[c]
         assert rel(F16[c, 0], F64[c, 0]) < FP32_TOL, names[c]
@@ -418,3 +466,34 @@ def test_24cube_sampled_r(nbs):
     ref = O.correlator(("p", "n", "p", "n"), {"u": Sl, "d": Sl, "s": Ss}, L, rs)
     assert rel(F64[0, 0][..., idx], ref) < FP64_TOL
     assert rel(F32[0, 0][..., idx], ref) < FP32_TOL
+
+
+def test_slab_wait_timeout_is_reported_and_recoverable(nbs):
+    """The failure path of the contraction's bounded slab wait, without a device fault: the test switch
+    NBS_PARAM_TEST_SKIP_SLAB makes the FP32 row kernel arm each block's first slab wait and issue no copy,
+    so nothing is in flight when the wait runs out (about a second).  nbs_correlate returns NBS_ETIMEOUT, a
+    waited replay of a graph captured with the switch on returns NBS_ETIMEOUT, and with the switch off the
+    same context gives the oracle's correlators again."""
+    L = 8
+    props = seeded(1771, L, 1, decay=0.5)
+    names = nbs.channel_names()
+    ids = [0, 9, 24, 51]
+    with nbs.Context(L, 1, precision=nbs.NBS_FP32) as ctx:
+        ctx.load_props(torch.from_numpy(props[0][0]).cuda(), torch.from_numpy(props[0][1]).cuda(), 0)
+        out = torch.empty((len(ids), 1, 4, 4, 2, 2, L ** 3), dtype=torch.complex128, device="cuda")
+        ctx.correlate(ids, 0, 1, out)   # allocates every buffer before the capture below
+        ctx.set_param(3, 1)             # NBS_PARAM_TEST_SKIP_SLAB
+        with pytest.raises(nbs.NBSError) as ei:
+            ctx.correlate(ids, 0, 1, out)
+        assert ei.value.code == -5      # NBS_ETIMEOUT
+        g = ctx.capture(ids, 0, 1, out)
+        with pytest.raises(nbs.NBSError) as ei:
+            g.launch()
+        assert ei.value.code == -5
+        g.close()
+        ctx.set_param(3, 0)
+        ctx.correlate(ids, 0, 1, out)
+        torch.cuda.synchronize()
+        F = out.cpu().numpy()
+    for k, c in enumerate(ids):
+        assert rel(F[k, 0], oracle(names[c], *props[0], L)) < FP32_TOL, names[c]
