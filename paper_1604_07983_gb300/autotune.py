@@ -19,24 +19,30 @@ from .nbs import NBS_BF16X3, NBS_FP32, NBS_FP64, Context
 
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "nbs_gb300", "autotune.json")
 
-#: (contraction config, momentum block) candidates per precision mode
+#: (contraction config, momentum block) candidates per precision mode: FP32 the two-phase row kernel
+#: (config 0) at three momentum blocks and the quad-lane kernel (config 4); BF16X3 its quad-lane
+#: tensor-core kernel; FP64 the thread-per-momentum shapes
 CANDIDATES = {
-    NBS_FP32: [(0, 32), (0, 64), (2, 32), (3, 32), (0, 16), (42, 0), (22, 0), (1, 0)],
-    NBS_BF16X3: [(0, 16), (0, 32), (0, 64), (2, 32)],
-    NBS_FP64: [(21, 0), (12, 0), (22, 0), (11, 0), (1, 0)],
+    NBS_FP32: [(0, 32), (0, 64), (0, 16), (4, 32)],
+    NBS_BF16X3: [(0, 16), (0, 32), (0, 64)],
+    NBS_FP64: [(21, 0), (12, 0), (22, 0), (11, 0)],
 }
+
+
+def cache_key(device_name: str, L: int, precision: int, ids) -> str:
+    """Cache key of a tuning: GPU name, lattice size, precision mode and a hash of the channel list."""
+    h = hashlib.sha1(",".join(map(str, ids)).encode()).hexdigest()[:12]
+    return "%s|L=%d|prec=%d|ch=%s" % (device_name, L, precision, h)
 
 
 def _key(ctx: Context, ids, precision: int) -> str:
     import torch
-    name = torch.cuda.get_device_name()
-    h = hashlib.sha1(",".join(map(str, ids)).encode()).hexdigest()[:12]
-    return "%s|L=%d|prec=%d|ch=%s" % (name, ctx.L, precision, h)
+    return cache_key(torch.cuda.get_device_name(), ctx.L, precision, ids)
 
 
-def _load():
+def _load(path=None):
     try:
-        with open(CACHE) as fh:
+        with open(path or CACHE) as fh:
             return json.load(fh)
     except (OSError, ValueError):
         return {}
@@ -53,20 +59,24 @@ def _apply(ctx: Context, cfg: int, qb: int, fft_block: int = 0):
         ctx.set_param(Context.PARAM_FFT_BLOCK, fft_block)
 
 
-def tune(ctx: Context, ids, precision: int, t: int = 0, reps: int = 2, use_cache: bool = True) -> dict:
+def tune(ctx: Context, ids, precision: int, t: int = 0, reps: int = 2, use_cache: bool = True, out=None,
+         key: str = None, cache_path: str = None) -> dict:
     """Pick the fastest contraction shape and FFT block for (ctx.L, precision, ids) and apply them to ctx.
 
-    Propagators for timeslice t must be loaded.  Returns {"cfg", "qb", "ms", "timings", "fft_block",
-    "fft_ms", "fft_timings"}.
+    Propagators for timeslice t must be loaded.  out: a device tensor [len(ids), 1, 4, 4, 2, 2, V] to
+    correlate into (allocated when None); key, cache_path: the cache key and file (defaults: cache_key()
+    of this GPU, CACHE).  Returns {"cfg", "qb", "ms", "timings", "fft_block", "fft_ms", "fft_timings"}.
     """
-    import torch
-    key = _key(ctx, ids, precision)
-    cache = _load() if use_cache else {}
+    key = key or _key(ctx, ids, precision)
+    cache_path = cache_path or CACHE
+    cache = _load(cache_path) if use_cache else {}
     if key in cache and "fft_block" in cache[key]:
         best = cache[key]
         _apply(ctx, best["cfg"], best["qb"], best["fft_block"])
         return best
-    out = torch.empty((len(ids), 1, 4, 4, 2, 2, ctx.V), dtype=torch.complex128, device="cuda")
+    if out is None:
+        import torch
+        out = torch.empty((len(ids), 1, 4, 4, 2, 2, ctx.V), dtype=torch.complex128, device="cuda")
     timings = []
     for cfg, qb in CANDIDATES[precision]:
         _apply(ctx, cfg, qb)
@@ -96,9 +106,9 @@ def tune(ctx: Context, ids, precision: int, t: int = 0, reps: int = 2, use_cache
     _apply(ctx, best["cfg"], best["qb"], best["fft_block"])
     if use_cache:
         cache[key] = best
-        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
-        tmp = CACHE + ".tmp"
+        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+        tmp = cache_path + ".tmp"
         with open(tmp, "w") as fh:
             json.dump(cache, fh, indent=1)
-        os.replace(tmp, CACHE)
+        os.replace(tmp, cache_path)
     return best
