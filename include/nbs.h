@@ -254,6 +254,51 @@ const char* nbs_last_error(const nbs_ctx* h);
 #define NBS_STATIC_SCRATCH_BYTES 12582912
 int nbs_correlate_static(const void* u, const void* s, int L, int dtype, int channel_id, void* out, void* stream);
 
+/* ---- L-parallel path: the lattice split over ranks ------------------------
+ * The paper's second parallelisation (Sec. 4 (i): the FFTs need an all-to-all
+ * between the nodes that hold parts of the lattice; Sec. 5 compares it with
+ * the T-parallel mode).  nranks ranks share one L^3 timeslice: rank r holds
+ * the z-planes [z_begin, z_end) of the propagators (z0[p] = floor(p L /
+ * nranks)) and, in momentum space, every z and x of a set of y values closed
+ * under y -> -y (mod L), so that q and -q of each momentum it owns are local
+ * and the contraction of Eq. (4.3) needs no exchange.  Per timeslice:
+ *   1. nbs_slab_begin: max|S| of the rank's propagators -> maxbits[2] (bit
+ *      patterns of the two maxima: the caller reduces them over the ranks with
+ *      MAX, as 64-bit integers);
+ *   2. nbs_slab_blocks(maxbits of all ranks): common power-of-two rescale,
+ *      blocks of Eq. (4.1) on the rank's sites, FFT along x and y, packed into
+ *      `send` for the forward exchange;
+ *   3. the caller's all-to-all (send counts / receive counts per peer from
+ *      nbs_slab_sizes, complex64 values, blocks of peer order);
+ *   4. nbs_slab_contract(recv, send): FFT along z, the two-phase contraction on
+ *      the rank's momenta, inverse FFT along z, packed for the inverse exchange;
+ *   5. the caller's all-to-all (the correlator counts);
+ *   6. nbs_slab_finish(recv, out): inverse FFT along y and x, FP64 restore:
+ *      out = complex128 [n_channels][a1][a2][a3][a4][z_begin..z_end)[y][x],
+ *      the rank's z-planes of F(r) (device pointer).
+ * FP32 arithmetic (the two-phase contraction), two propagators (u = d, s).
+ * All pointers are device pointers the caller owns; the propagators passed to
+ * nbs_slab_begin must stay valid until nbs_slab_blocks returns.  Every call
+ * returns after its device work; NBS_ENAN (begin) and NBS_ETIMEOUT (contract)
+ * as for nbs_correlate. */
+/* The layout of rank `rank` of nranks on an L^3 lattice: its z range and its
+ * y values (ys must hold L ints).  Host only. */
+int nbs_slab_layout(int L, int nranks, int rank, int* z_begin, int* z_end, int* ys, int* n_ys);
+/* A context for rank `rank` of nranks for the given channels (ids as in
+ * nbs_correlate); destroyed with nbs_destroy.  NBS_EINVAL where no layout
+ * exists (each rank needs a z-plane and a y pair) or the two-phase tables do
+ * not fit shared memory. */
+int nbs_slab_create(nbs_ctx** out, int L, int nranks, int rank, const int* channel_ids, int n_channels);
+/* Per-peer element counts (complex64 values) of the four exchange buffers:
+ * forward send / receive (blocks), inverse send / receive (correlators); each
+ * array has nranks entries (NULL to skip). */
+int nbs_slab_sizes(const nbs_ctx* h, long long* send_blocks, long long* recv_blocks, long long* send_corr,
+                   long long* recv_corr);
+int nbs_slab_begin(nbs_ctx* h, const void* u, const void* s, int dtype, unsigned long long* maxbits);
+int nbs_slab_blocks(nbs_ctx* h, const unsigned long long* maxbits, void* send);
+int nbs_slab_contract(nbs_ctx* h, const void* recv, void* send);
+int nbs_slab_finish(nbs_ctx* h, const void* recv, void* out);
+
 /* ---- host-only introspection of the compiled channel tables ------------
  * nbs_plan_create runs the host "channel compiler" (Sec. 4 (ii)-(iii): the
  * diagrammatic classification done on the CPU and packed as structures of

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace nbs {
 
 template <typename T> struct cplx_t;
@@ -129,14 +131,60 @@ cudaError_t launch_contract_tc(const float2* FB, int L, int nchunks, int qb, con
 // chunks points to RowChunkHdr[nchunks], segs to RowSeg[] (plan.h); scales: 32
 // floats; smem: the largest chunk's shared memory; skip_first (test switch):
 // arm the first slab wait without issuing its copy, so that it runs out
-cudaError_t launch_contract_rows(const float2* FB, long long ncells, int L, int nchunks, int qb, const void* chunks,
+// Momenta of a contraction launch: q = x + L (y + Ly z), x and z over [0, L), y over Ly values of a set
+// that contains -y (mod L) with every y; the index of -y is ymir[y].  The full cube: Ly = L,
+// ymir[y] = (L - y) mod L.
+struct MomGeom {
+  int L, Ly;
+  int ymir[64];
+};
+inline MomGeom full_geom(int L) {
+  MomGeom g;
+  g.L = L;
+  g.Ly = L;
+  for (int y = 0; y < 64; ++y) g.ymir[y] = y < L ? (L - y) % L : 0;
+  return g;
+}
+cudaError_t launch_contract_rows(const float2* FB, long long ncells, const MomGeom& geom, int nchunks, int qb,
+                                 const void* chunks,
                                  const unsigned short* aent, const unsigned* adesc, const unsigned* rec,
                                  const void* segs, const int* row_ch, const float* scales, int smem, float2* Ft,
                                  int* flags, int skip_first, cudaStream_t st);
+// ---- L-parallel path (slab.cu) -------------------------------------------------------
+#define NBS_SLAB_MAX_RANKS 64
+// ranks' z-planes [z0[p], z0[p+1]); y-sets: owner rank and local index of each y, set sizes
+struct SlabGeom {
+  int L = 0, P = 0;
+  int z0[NBS_SLAB_MAX_RANKS + 1] = {};
+  int zowner[64] = {};
+  int ny[NBS_SLAB_MAX_RANKS] = {};
+  int yowner[64] = {}, yloc[64] = {};
+};
+// this rank and the element offset of each peer's block in an exchange buffer
+struct SlabOff {
+  int rank = 0;
+  long long off[NBS_SLAB_MAX_RANKS + 1] = {};
+};
+bool slab_layout(int L, int nranks, SlabGeom& g);
+std::vector<int> slab_yset(const SlabGeom& g, int p);
+enum SlabMove { SLAB_PACK_BLOCKS = 0, SLAB_UNPACK_BLOCKS = 1, SLAB_PACK_CORR = 2, SLAB_UNPACK_CORR = 3 };
+// the four moves around the exchanges: blocks [c][zl][y][x] (32-byte cells) -> by y-owner, by z-owner ->
+// [c][z][yl][x]; correlators [c][z][yl][x] (complex FP32) -> by z-owner, by y-owner -> [c][zl][y][x]
+cudaError_t launch_slab_move(int kind, const void* src, void* dst, long long ncomp, const SlabGeom& g,
+                             const SlabOff& o, cudaStream_t st);
+// one pass of the FFT over arbitrary lines: line l starts at (l / inner) * group + l % inner, its L points
+// `stride` apart (fft.cu)
+template <typename T>
+cudaError_t fft_lines(C<T>* data, long long nlines, int inner, long long group, long long stride, int L, int dir,
+                      int sb, cudaStream_t st);
+// the x pass: nrows contiguous rows of L * IL values, IL interleaved lines each (IL = 1 or 4)
+template <typename T>
+cudaError_t fft_rows(C<T>* data, long long nrows, int L, int IL, int dir, cudaStream_t st);
 // ch_fl: per channel the quarks of each propagator (3 ints); exps: per propagator
+// norm: the volume of the inverse transform's 1/V (0: V, the values per channel and spin)
 template <typename T>
 cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_fl, const int* exps, int nflav,
-                           double2* out, long long ch_stride, cudaStream_t st);
+                           double2* out, long long ch_stride, cudaStream_t st, long long norm = 0);
 
 // kernels_potential.cu: K = a d_t^2 R + b d_t R + c lap R, P = K / R (P may be null)
 cudaError_t launch_potential(const double2* Rm, const double2* R0, const double2* Rp, int L, long long ncomp, double a,

@@ -326,7 +326,79 @@ cudaError_t dispatch(C<T>* data, long long nbatch, int L, int sb, cudaStream_t s
   }
 }
 
+template <typename T, int DIR>
+cudaError_t lines_L(C<T>* data, long long nlines, int inner, long long group, long long stride, int L, int sb,
+                    cudaStream_t st) {
+  const long long blocks = (nlines + sb - 1) / sb;
+  if (blocks > 2147483647LL || stride > 2147483647LL) return cudaErrorInvalidValue;
+  switch (L) {
+#define NBS_LINES(n) \
+  case n: k_fft_strided<T, n, DIR><<<(unsigned)blocks, sb, 0, st>>>(data, nlines, inner, group, (int)stride); break;
+    NBS_LINES(2) NBS_LINES(3) NBS_LINES(4) NBS_LINES(6) NBS_LINES(8) NBS_LINES(12) NBS_LINES(16) NBS_LINES(24)
+    NBS_LINES(32) NBS_LINES(48)
+#undef NBS_LINES
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int L, int DIR, int IL>
+cudaError_t rows_L(C<T>* data, long long nrows, cudaStream_t st) {
+  constexpr int NT = 64;
+  const long long nlines = nrows * IL;
+  const size_t sm = (size_t)(NT / IL) * (L * IL + contig_pad<T, IL>()) * sizeof(C<T>);
+  auto kern = k_fft_contig<T, L, DIR, NT, IL>;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  const long long blocks = (nlines + NT - 1) / NT;
+  if (blocks > 2147483647LL) return cudaErrorInvalidValue;
+  kern<<<(unsigned)blocks, NT, sm, st>>>(data, nlines);
+  return cudaGetLastError();
+}
+
+template <typename T, int DIR, int IL>
+cudaError_t rows_dispatch(C<T>* data, long long nrows, int L, cudaStream_t st) {
+  switch (L) {
+    case 1: return cudaSuccess;
+    case 2: return rows_L<T, 2, DIR, IL>(data, nrows, st);
+    case 3: return rows_L<T, 3, DIR, IL>(data, nrows, st);
+    case 4: return rows_L<T, 4, DIR, IL>(data, nrows, st);
+    case 6: return rows_L<T, 6, DIR, IL>(data, nrows, st);
+    case 8: return rows_L<T, 8, DIR, IL>(data, nrows, st);
+    case 12: return rows_L<T, 12, DIR, IL>(data, nrows, st);
+    case 16: return rows_L<T, 16, DIR, IL>(data, nrows, st);
+    case 24: return rows_L<T, 24, DIR, IL>(data, nrows, st);
+    case 32: return rows_L<T, 32, DIR, IL>(data, nrows, st);
+    case 48: return rows_L<T, 48, DIR, IL>(data, nrows, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t fft_lines(C<T>* data, long long nlines, int inner, long long group, long long stride, int L, int dir,
+                      int sb, cudaStream_t st) {
+  if (nlines == 0 || L == 1) return cudaSuccess;
+  if (sb != 64 && sb != 128 && sb != 256) return cudaErrorInvalidValue;
+  return dir < 0 ? lines_L<T, -1>(data, nlines, inner, group, stride, L, sb, st)
+                 : lines_L<T, 1>(data, nlines, inner, group, stride, L, sb, st);
+}
+
+template <typename T>
+cudaError_t fft_rows(C<T>* data, long long nrows, int L, int IL, int dir, cudaStream_t st) {
+  if (nrows == 0 || L == 1) return cudaSuccess;
+  if (IL == 4) return dir < 0 ? rows_dispatch<T, -1, 4>(data, nrows, L, st) : rows_dispatch<T, 1, 4>(data, nrows, L, st);
+  if (IL == 1) return dir < 0 ? rows_dispatch<T, -1, 1>(data, nrows, L, st) : rows_dispatch<T, 1, 1>(data, nrows, L, st);
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t fft_lines<float>(float2*, long long, int, long long, long long, int, int, int, cudaStream_t);
+template cudaError_t fft_lines<double>(double2*, long long, int, long long, long long, int, int, int, cudaStream_t);
+template cudaError_t fft_rows<float>(float2*, long long, int, int, int, cudaStream_t);
+template cudaError_t fft_rows<double>(double2*, long long, int, int, int, cudaStream_t);
 
 bool fft_supported(int L) { return tw_offset(L) >= 0; }
 

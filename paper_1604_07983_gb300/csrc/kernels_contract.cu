@@ -872,7 +872,7 @@ __device__ __forceinline__ double scaled_double(float f, int ex) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_restore(const C<T>* __restrict__ Ft, long long V, const int* __restrict__ ch_fl,
                                                  const int* __restrict__ exps, int nflav, double2* __restrict__ out,
-                                                 long long ch_stride) {
+                                                 long long ch_stride, long long norm) {
   const int ch = blockIdx.y;
   int ex = 0;  // sum over the propagators of (their exponent) x (their quarks in the sink pair)
   for (int f = 0; f < nflav; ++f) ex += exps[f] * ch_fl[3 * ch + f];
@@ -882,7 +882,7 @@ __global__ void __launch_bounds__(256) k_restore(const C<T>* __restrict__ Ft, lo
   const long long stride = (long long)gridDim.x * blockDim.x;
   if constexpr (sizeof(T) == 4) {
     constexpr int RS = 4;
-    const float inv = 1.0f / (float)V;
+    const float inv = 1.0f / (float)norm;
     const float4* s4 = reinterpret_cast<const float4*>(src);  // n is even, Ft 16-byte aligned
     const long long n2 = n / 2;
     for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n2; i0 += RS * stride) {
@@ -902,7 +902,7 @@ __global__ void __launch_bounds__(256) k_restore(const C<T>* __restrict__ Ft, lo
       }
     }
   } else {
-    const double scale = ldexp(1.0, ex) / (double)V;
+    const double scale = ldexp(1.0, ex) / (double)norm;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
       const C<T> z = src[i];
       dst[i] = make_double2((double)z.x * scale, (double)z.y * scale);
@@ -1007,12 +1007,12 @@ cudaError_t launch_contract_chunk2(const float2* FB, int L, int nchunks, int qb,
 
 template <typename T>
 cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_fl, const int* exps, int nflav, double2* out,
-                           long long ch_stride, cudaStream_t st) {
+                           long long ch_stride, cudaStream_t st, long long norm) {
   long long n = 64LL * V;
   if (sizeof(T) == 4) n /= 8;  // 16-byte loads, four per thread per pass
   int bx = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096));
   dim3 grid(bx, nch);
-  k_restore<T><<<grid, 256, 0, st>>>(Ft, (long long)V, ch_fl, exps, nflav, out, ch_stride);
+  k_restore<T><<<grid, 256, 0, st>>>(Ft, (long long)V, ch_fl, exps, nflav, out, ch_stride, norm ? norm : (long long)V);
   return cudaGetLastError();
 }
 
@@ -1029,8 +1029,8 @@ template cudaError_t launch_contract_slab<double>(const double2*, int, int, cons
 template size_t slab_smem_bytes<float>(int, int, int);
 template size_t slab_smem_bytes<double>(int, int, int);
 template cudaError_t launch_restore<float>(const float2*, int, int, const int*, const int*, int, double2*, long long,
-                                           cudaStream_t);
+                                           cudaStream_t, long long);
 template cudaError_t launch_restore<double>(const double2*, int, int, const int*, const int*, int, double2*, long long,
-                                            cudaStream_t);
+                                            cudaStream_t, long long);
 
 }  // namespace nbs

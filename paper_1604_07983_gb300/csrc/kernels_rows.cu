@@ -76,10 +76,11 @@ __device__ __forceinline__ void cp16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
 
-// the site index of -q (componentwise (L - n) mod L)
-__device__ __forceinline__ long long minus_q(long long q, int L) {
-  const int x = (int)(q % L), y = (int)((q / L) % L), z = (int)(q / ((long long)L * L));
-  return (long long)((L - x) % L) + L * ((long long)((L - y) % L) + (long long)L * ((L - z) % L));
+// the index of -q in the momentum geometry (componentwise (L - n) mod L; y through the mirror table)
+__device__ __forceinline__ long long minus_q(long long q, const MomGeom& g) {
+  const int L = g.L, Ly = g.Ly;
+  const int x = (int)(q % L), y = (int)((q / L) % Ly), z = (int)(q / ((long long)L * Ly));
+  return (long long)((L - x) % L) + L * ((long long)g.ymir[y] + (long long)Ly * ((L - z) % L));
 }
 
 __device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
@@ -140,7 +141,8 @@ __device__ __forceinline__ void rows_flush(float (&acc)[32], int lane, float2* s
 
 template <int NW, bool TMA>
 __global__ void __launch_bounds__(NW * 32, 1) k_contract_rows(
-    const __grid_constant__ CUtensorMap fbmap, const float2* __restrict__ FB, int L, int nchunks, int qb,
+    const __grid_constant__ CUtensorMap fbmap, const __grid_constant__ MomGeom geom, const float2* __restrict__ FB,
+    int nchunks, int qb,
     const RowChunkHdr* __restrict__ chunks, const unsigned short* __restrict__ aent,
     const unsigned* __restrict__ adesc, const unsigned* __restrict__ rec, const RowSeg* __restrict__ segs,
     const int* __restrict__ row_ch, const float* __restrict__ scales, float2* __restrict__ Ft,
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_rows(
   int* const GC = SLT + nslot;                          // its request-order channel
   const unsigned mb = smem_u32(sb + lay.mb);
 
-  const long long V = (long long)L * L * L;
+  const long long V = (long long)geom.L * geom.Ly * geom.L;  // momenta of this launch
   const long long q_begin = (long long)(blockIdx.x / nchunks) * qb;
   const long long q_end = min(V, q_begin + qb);
   const int base1 = ck.base1, n1c = ck.ncell1, base2 = ck.base2, n2c = ck.ncell2;
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_rows(
         if (skip_first)  // test switch: arm the barrier, issue no box (the wait runs out, nothing in flight)
           mbar_expect_tx(mb, 32u);
         else
-          tma_issue_planar(&fbmap, smem_u32(SL), mb, base1, n1c, (int)q_begin, base2, n2c, (int)minus_q(q_begin, L));
+          tma_issue_planar(&fbmap, smem_u32(SL), mb, base1, n1c, (int)q_begin, base2, n2c, (int)minus_q(q_begin, geom));
       }
     }
   }
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_rows(
     for (int i = threadIdx.x; i < nseg; i += NT) cp16((uint4*)SEG + i, gs + i);
   }
   auto stage_slabs_async = [&](long long q) {  // the same planar slabs by 16-byte cp.async (no tensor map)
-    const long long qm = minus_q(q, L);
+    const long long qm = minus_q(q, geom);
     for (int i = threadIdx.x; i < 2 * (n1c + n2c); i += NT) {
       const int side = i >= 2 * n1c, k = side ? i - 2 * n1c : i, c = k >> 1, h = k & 1;
       const long long src = ((long long)((side ? base2 : base1) + c) * V + (side ? qm : q)) * 4 + 2 * h;
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_rows(
   auto stage_slabs = [&](long long qn) {
     if constexpr (TMA) {
       if (threadIdx.x == 0)
-        tma_issue_planar(&fbmap, smem_u32(SL), mb, base1, n1c, (int)qn, base2, n2c, (int)minus_q(qn, L));
+        tma_issue_planar(&fbmap, smem_u32(SL), mb, base1, n1c, (int)qn, base2, n2c, (int)minus_q(qn, geom));
     } else {
       stage_slabs_async(qn);
       asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -440,12 +442,16 @@ static bool encode_fb_map_planar(CUtensorMap* map, const float2* FB, long long V
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-cudaError_t launch_contract_rows(const float2* FB, long long ncells, int L, int nchunks, int qb, const void* chunks,
+cudaError_t launch_contract_rows(const float2* FB, long long ncells, const MomGeom& geom, int nchunks, int qb,
+                                 const void* chunks,
                                  const unsigned short* aent, const unsigned* adesc, const unsigned* rec,
                                  const void* segs, const int* row_ch, const float* scales, int smem, float2* Ft,
                                  int* flags, int skip_first, cudaStream_t st) {
-  const long long V = (long long)L * L * L;
-  if (nchunks <= 0 || qb <= 0 || smem <= 0 || !flags) return cudaErrorInvalidValue;
+  const long long V = (long long)geom.L * geom.Ly * geom.L;
+  if (nchunks <= 0 || qb <= 0 || smem <= 0 || !flags || geom.L < 1 || geom.L > 64 || geom.Ly < 1 || geom.Ly > geom.L)
+    return cudaErrorInvalidValue;
+  for (int y = 0; y < geom.Ly; ++y)
+    if (geom.ymir[y] < 0 || geom.ymir[y] >= geom.Ly) return cudaErrorInvalidValue;
   const long long nqb = (V + qb - 1) / qb;
   if (nqb * nchunks > 2147483647LL) return cudaErrorInvalidValue;
   CUtensorMap map;
@@ -455,7 +461,7 @@ cudaError_t launch_contract_rows(const float2* FB, long long ncells, int L, int 
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)(nqb * nchunks), NBS_ROW_WARPS * 32, smem, st>>>(
-      map, FB, L, nchunks, qb, (const RowChunkHdr*)chunks, aent, adesc, rec, (const RowSeg*)segs, row_ch, scales, Ft,
+      map, geom, FB, nchunks, qb, (const RowChunkHdr*)chunks, aent, adesc, rec, (const RowSeg*)segs, row_ch, scales, Ft,
       flags, tma ? skip_first : 0);
   return cudaGetLastError();
 }

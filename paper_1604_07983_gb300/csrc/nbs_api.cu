@@ -92,6 +92,17 @@ struct nbs_ctx {
   int chunk_qb = 32;
   DevBuf d_rchunks, d_raent, d_radesc, d_rrec, d_rsegs, d_rch, d_rscales;  // two-phase contraction tables
   int test_skip_slab = 0;  // NBS_PARAM_TEST_SKIP_SLAB (test switch)
+  // one rank of the L-parallel path (nbs_slab_create): its z-planes, its mirror-closed y-set
+  bool slab = false;
+  SlabGeom sg;
+  int srank = 0, slz = 0, sny = 0, snch = 0;
+  long long svs = 0, svm = 0;       // sites of its z-planes, momenta of its y-set
+  MomGeom smg;
+  SlabOff soff[4];                  // send / receive offsets of the forward and the inverse exchange
+  DevBuf s_FB, s_FBm, s_Ft, s_F;    // blocks [c][zl][y][x], [c][z][yl][x]; correlators [n][z][yl][x], [n][zl][y][x]
+  const void* s_u = nullptr;        // the rank's propagators of the current timeslice (caller's)
+  const void* s_s = nullptr;
+  int s_c64 = 0;
   int fft_block = 128;  // NBS_PARAM_FFT_BLOCK
   int tables_mode = -1;
   TypeRecipeSet recipes;
@@ -420,7 +431,7 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
     const bool use_rows = rows_fit && h->mode == NBS_FP32 && h->contract_cfg == 0;
     const bool use_qseg = f32_chunks && quad_fits && (h->contract_cfg == 4 || (h->contract_cfg == 0 && !rows_fit));
     if (use_rows) {
-      CK(launch_contract_rows((const float2*)h->FB.p, h->plan.ncells, h->L, (int)h->plan.row_chunks.size(),
+      CK(launch_contract_rows((const float2*)h->FB.p, h->plan.ncells, full_geom(h->L), (int)h->plan.row_chunks.size(),
                               h->chunk_qb, h->d_rchunks.p, (const unsigned short*)h->d_raent.p,
                               (const unsigned*)h->d_radesc.p, (const unsigned*)h->d_rrec.p, h->d_rsegs.p,
                               (const int*)h->d_rch.p, (const float*)h->d_rscales.p, h->plan.row_smem,
@@ -541,7 +552,15 @@ int nbs_set_allocator(nbs_alloc_fn alloc, nbs_free_fn free_fn, void* user) {
   return NBS_OK;
 }
 
-int nbs_create(nbs_ctx** out, int L, int T, int flavours) {
+namespace {
+int create_ctx(nbs_ctx** out, int L, int T, int flavours, bool store);
+}
+
+int nbs_create(nbs_ctx** out, int L, int T, int flavours) { return create_ctx(out, L, T, flavours, true); }
+
+namespace {
+// store: allocate the propagator store of T timeslices (the L-parallel ranks take the caller's)
+int create_ctx(nbs_ctx** out, int L, int T, int flavours, bool store) {
   if (!out) return fail(nullptr, NBS_EINVAL, "null output pointer");
   *out = nullptr;
   if (flavours != 2 && flavours != 3)
@@ -578,7 +597,7 @@ int nbs_create(nbs_ctx** out, int L, int T, int flavours) {
     return fail(nullptr, NBS_ENOMEM, "pinned flag");
   }
   *h->host_flags = 0;
-  int rc = ensure(h, h->props, (size_t)T * flavours * h->V * 144 * sizeof(double2), "propagator store");
+  int rc = store ? ensure(h, h->props, (size_t)T * flavours * h->V * 144 * sizeof(double2), "propagator store") : 0;
   if (!rc) rc = ensure(h, h->small, 256, "scale scratch");
   if (rc) {
     std::string m = h->err;
@@ -591,6 +610,7 @@ int nbs_create(nbs_ctx** out, int L, int T, int flavours) {
   *out = h;
   return NBS_OK;
 }
+}  // namespace
 
 int nbs_destroy(nbs_ctx* h) {
   if (!h) return NBS_OK;
@@ -599,7 +619,8 @@ int nbs_destroy(nbs_ctx* h) {
   DevBuf* bufs[] = {&h->props, &h->propsT, &h->FB, &h->Ft, &h->zm, &h->small, &h->stage[0], &h->stage[1],
                     &h->d_terms, &h->d_chtb, &h->d_chnl, &h->d_e1, &h->d_e2, &h->d_cells, &h->d_groups,
                     &h->d_gch, &h->d_items, &h->d_chunks, &h->d_qchunks, &h->d_qsegs, &h->d_ctab, &h->d_citems, &h->d_ctoff,
-                    &h->d_codes};
+                    &h->d_codes, &h->d_rchunks, &h->d_raent, &h->d_radesc, &h->d_rrec, &h->d_rsegs, &h->d_rch,
+                    &h->d_rscales, &h->s_FB, &h->s_FBm, &h->s_Ft, &h->s_F};
   for (DevBuf* b : bufs) dev_free(b->p, h->free_fn, h->free_user);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   for (int b = 0; b < 2; ++b) {
@@ -1014,6 +1035,177 @@ int nbs_plan_export(const nbs_plan* p, int what, void* dst) {
       return NBS_OK;
     default: return fail(nullptr, NBS_EINVAL, "unknown export");
   }
+}
+
+// ---- L-parallel path ------------------------------------------------------------------------
+
+int nbs_slab_layout(int L, int nranks, int rank, int* z_begin, int* z_end, int* ys, int* n_ys) {
+  SlabGeom g;
+  if (!z_begin || !z_end || !ys || !n_ys) return fail(nullptr, NBS_EINVAL, "null output");
+  if (!fft_supported(L) || !slab_layout(L, nranks, g) || rank < 0 || rank >= nranks)
+    return fail(nullptr, NBS_EINVAL, "no layout of this many ranks on this lattice (L must be a supported FFT "
+                                     "size; each rank needs a z-plane and a y pair)");
+  *z_begin = g.z0[rank];
+  *z_end = g.z0[rank + 1];
+  const std::vector<int> y = slab_yset(g, rank);
+  *n_ys = (int)y.size();
+  std::copy(y.begin(), y.end(), ys);
+  return NBS_OK;
+}
+
+int nbs_slab_create(nbs_ctx** out, int L, int nranks, int rank, const int* channel_ids, int n_channels) {
+  if (!out || !channel_ids || n_channels < 1) return fail(nullptr, NBS_EINVAL, "null argument or no channels");
+  *out = nullptr;
+  SlabGeom g;
+  if (!fft_supported(L) || !slab_layout(L, nranks, g) || rank < 0 || rank >= nranks)
+    return fail(nullptr, NBS_EINVAL, "no layout of this many ranks on this lattice");
+  nbs_ctx* h = nullptr;
+  int rc = create_ctx(&h, L, 1, 2, false);
+  if (rc) return rc;
+  h->mode = NBS_FP32;
+  h->slab = true;
+  h->sg = g;
+  h->srank = rank;
+  h->slz = g.z0[rank + 1] - g.z0[rank];
+  h->sny = g.ny[rank];
+  h->svs = (long long)h->slz * L * L;
+  h->svm = (long long)L * h->sny * L;
+  h->smg.L = L;
+  h->smg.Ly = h->sny;
+  const std::vector<int> ys = slab_yset(g, rank);
+  for (int i = 0; i < 64; ++i) h->smg.ymir[i] = 0;
+  for (int i = 0; i < h->sny; ++i) h->smg.ymir[i] = g.yloc[(L - ys[i]) % L];
+  std::vector<int> ids(channel_ids, channel_ids + n_channels);
+  if ((rc = ensure_plan(h, ids))) {
+    std::string m = h->err;
+    nbs_destroy(h);
+    return fail(nullptr, rc, m);
+  }
+  if (!h->plan.rows_ok || h->plan.row_smem > h->smem_optin) {
+    nbs_destroy(h);
+    return fail(nullptr, NBS_EINVAL, "the L-parallel path needs the two-phase contraction tables");
+  }
+  h->snch = n_channels;
+  const long long nc = h->plan.ncells, n64 = 64LL * n_channels;
+  // exchange offsets in elements of the moved data (32-byte cells, complex FP32 correlators)
+  for (int p = 0; p < 4; ++p) {
+    h->soff[p].rank = rank;
+    h->soff[p].off[0] = 0;
+  }
+  for (int p = 0; p < nranks; ++p) {
+    const int lz = g.z0[p + 1] - g.z0[p];
+    h->soff[0].off[p + 1] = h->soff[0].off[p] + nc * h->slz * g.ny[p] * L;     // forward send: y-set of p
+    h->soff[1].off[p + 1] = h->soff[1].off[p] + nc * lz * h->sny * L;          // forward receive: z-planes of p
+    h->soff[2].off[p + 1] = h->soff[2].off[p] + n64 * lz * h->sny * L;         // inverse send: z-planes of p
+    h->soff[3].off[p + 1] = h->soff[3].off[p] + n64 * h->slz * g.ny[p] * L;    // inverse receive: y-set of p
+  }
+  if ((rc = ensure(h, h->propsT, 2ull * 144 * h->svs * sizeof(float2), "scaled propagators")) ||
+      (rc = ensure(h, h->s_FB, 4ull * nc * h->svs * sizeof(float2), "slab blocks")) ||
+      (rc = ensure(h, h->s_FBm, 4ull * nc * h->svm * sizeof(float2), "momentum-set blocks")) ||
+      (rc = ensure(h, h->s_Ft, (size_t)n64 * h->svm * sizeof(float2), "momentum-set correlators")) ||
+      (rc = ensure(h, h->s_F, (size_t)n64 * h->svs * sizeof(float2), "slab correlators"))) {
+    std::string m = h->err;
+    nbs_destroy(h);
+    return fail(nullptr, rc, m);
+  }
+  *out = h;
+  return NBS_OK;
+}
+
+int nbs_slab_sizes(const nbs_ctx* h, long long* send_blocks, long long* recv_blocks, long long* send_corr,
+                   long long* recv_corr) {
+  if (!h || !h->slab) return fail(nullptr, NBS_EINVAL, "not an L-parallel context");
+  long long* outs[4] = {send_blocks, recv_blocks, send_corr, recv_corr};
+  for (int k = 0; k < 4; ++k) {
+    if (!outs[k]) continue;
+    const long long per = k < 2 ? 4 : 1;  // complex values per moved element
+    for (int p = 0; p < h->sg.P; ++p) outs[k][p] = (h->soff[k].off[p + 1] - h->soff[k].off[p]) * per;
+  }
+  return NBS_OK;
+}
+
+int nbs_slab_begin(nbs_ctx* h, const void* u, const void* s, int dtype, unsigned long long* maxbits) {
+  if (!h || !h->slab) return fail(h, NBS_EINVAL, "not an L-parallel context");
+  if (!u || !s || !maxbits) return fail(h, NBS_EINVAL, "null pointer");
+  if (dtype != NBS_C128 && dtype != NBS_C64) return fail(h, NBS_EINVAL, "dtype must be NBS_C128 or NBS_C64");
+  h->s_u = u;
+  h->s_s = s;
+  h->s_c64 = dtype == NBS_C64;
+  const PropPtrs pp = {{u, s, nullptr}};
+  CK(cudaMemsetAsync(h->small.p, 0, 64, h->st), "clear max|S|");
+  CK(launch_props_maxabs(pp, 2, h->s_c64, (int)h->svs, h->maxbits, h->flags, h->st), "max|S|");
+  unsigned long long mb[2];
+  CK(cudaMemcpyAsync(mb, h->maxbits, sizeof(mb), cudaMemcpyDeviceToHost, h->st), "max|S| to host");
+  CK(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->st), "NaN flag");
+  CK(cudaStreamSynchronize(h->st), "sync");
+  if (*h->host_flags) return fail(h, NBS_ENAN, "non-finite value in the propagators");
+  maxbits[0] = mb[0];
+  maxbits[1] = mb[1];
+  return NBS_OK;
+}
+
+int nbs_slab_blocks(nbs_ctx* h, const unsigned long long* maxbits, void* send) {
+  if (!h || !h->slab || !h->s_u) return fail(h, NBS_EINVAL, "not an L-parallel context, or no nbs_slab_begin");
+  if (!maxbits || !send) return fail(h, NBS_EINVAL, "null pointer");
+  const Plan& P = h->plan;
+  const int L = h->L;
+  const long long nc = P.ncells;
+  const PropPtrs pp = {{h->s_u, h->s_s, nullptr}};
+  CK(cudaMemcpyAsync(h->maxbits, maxbits, 2 * sizeof(unsigned long long), cudaMemcpyHostToDevice, h->st),
+     "max|S| of all ranks");
+  CK(launch_props_scale<float>(pp, 2, h->s_c64, (int)h->svs, h->maxbits, h->exps, (float2*)h->propsT.p, h->st),
+     "rescale");
+  CK(launch_blocks_tiled<float>((const float2*)h->propsT.p, (const int*)h->d_cells.p, P.ncells, h->recipes,
+                                (int)h->svs, 2, (float2*)h->s_FB.p, h->st),
+     "diquarks and field blocks");
+  float2* fb = (float2*)h->s_FB.p;
+  CK(fft_rows<float>(fb, nc * h->slz * L, L, 4, -1, h->st), "x pass");
+  CK(fft_lines<float>(fb, nc * h->slz * 4LL * L, 4 * L, 4LL * L * L, 4LL * L, L, -1, h->fft_block, h->st), "y pass");
+  CK(launch_slab_move(SLAB_PACK_BLOCKS, fb, send, nc, h->sg, h->soff[0], h->st), "pack for the forward exchange");
+  CK(cudaStreamSynchronize(h->st), "sync");
+  return NBS_OK;
+}
+
+int nbs_slab_contract(nbs_ctx* h, const void* recv, void* send) {
+  if (!h || !h->slab) return fail(h, NBS_EINVAL, "not an L-parallel context");
+  if (!recv || !send) return fail(h, NBS_EINVAL, "null pointer");
+  const Plan& P = h->plan;
+  const int L = h->L, ny = h->sny;
+  const long long nc = P.ncells, n64 = 64LL * h->snch;
+  float2* fbm = (float2*)h->s_FBm.p;
+  float2* ft = (float2*)h->s_Ft.p;
+  CK(launch_slab_move(SLAB_UNPACK_BLOCKS, recv, fbm, nc, h->sg, h->soff[1], h->st), "unpack the forward exchange");
+  CK(fft_lines<float>(fbm, nc * ny * 4LL * L, 4 * L * ny, 4LL * L * ny * L, 4LL * L * ny, L, -1, h->fft_block, h->st),
+     "z pass");
+  CK(cudaMemsetAsync(h->flags, 0, sizeof(int), h->st), "clear flags");
+  CK(launch_contract_rows(fbm, nc, h->smg, (int)P.row_chunks.size(), h->chunk_qb, h->d_rchunks.p,
+                          (const unsigned short*)h->d_raent.p, (const unsigned*)h->d_radesc.p,
+                          (const unsigned*)h->d_rrec.p, h->d_rsegs.p, (const int*)h->d_rch.p,
+                          (const float*)h->d_rscales.p, P.row_smem, ft, h->flags, h->test_skip_slab, h->st),
+     "contraction on the momentum set");
+  CK(fft_lines<float>(ft, n64 * ny * L, L * ny, (long long)L * ny * L, (long long)L * ny, L, 1, h->fft_block, h->st),
+     "inverse z pass");
+  CK(launch_slab_move(SLAB_PACK_CORR, ft, send, n64, h->sg, h->soff[2], h->st), "pack for the inverse exchange");
+  CK(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->st), "flags");
+  CK(cudaStreamSynchronize(h->st), "sync");
+  if (*h->host_flags & 2) return fail(h, NBS_ETIMEOUT, "a slab copy wait in the contraction gave up");
+  return NBS_OK;
+}
+
+int nbs_slab_finish(nbs_ctx* h, const void* recv, void* out) {
+  if (!h || !h->slab) return fail(h, NBS_EINVAL, "not an L-parallel context");
+  if (!recv || !out) return fail(h, NBS_EINVAL, "null pointer");
+  const int L = h->L;
+  const long long n64 = 64LL * h->snch;
+  float2* f = (float2*)h->s_F.p;
+  CK(launch_slab_move(SLAB_UNPACK_CORR, recv, f, n64, h->sg, h->soff[3], h->st), "unpack the inverse exchange");
+  CK(fft_lines<float>(f, n64 * h->slz * L, L, (long long)L * L, L, L, 1, h->fft_block, h->st), "inverse y pass");
+  CK(fft_rows<float>(f, n64 * h->slz * L, L, 1, 1, h->st), "inverse x pass");
+  CK(launch_restore<float>(f, (int)h->svs, h->snch, (const int*)h->d_chnl.p, h->exps, 2, (double2*)out, 64LL * h->svs,
+                           h->st, (long long)L * L * L),
+     "restore");
+  CK(cudaStreamSynchronize(h->st), "sync");
+  return NBS_OK;
 }
 
 }  // extern "C"

@@ -27,7 +27,9 @@ EXPORTS = ["nbs_set_allocator", "nbs_create", "nbs_destroy", "nbs_set_precision"
            "nbs_profile", "nbs_channel_count",
            "nbs_channel_info", "nbs_last_error", "nbs_plan_create", "nbs_plan_destroy", "nbs_plan_sizes",
            "nbs_plan_export", "nbs_correlate_static", "nbs_graph_capture", "nbs_graph_launch", "nbs_graph_destroy",
-           "nbs_load_props3", "nbs_plan_create_flavours", "nbs_potential", "nbs_plan_row_sizes"]
+           "nbs_load_props3", "nbs_plan_create_flavours", "nbs_potential", "nbs_plan_row_sizes",
+           "nbs_slab_layout", "nbs_slab_create", "nbs_slab_sizes", "nbs_slab_begin", "nbs_slab_blocks",
+           "nbs_slab_contract", "nbs_slab_finish"]
 
 
 class NBSError(RuntimeError):
@@ -78,6 +80,13 @@ def lib():
         "nbs_load_props3": (i, [vp, vp, vp, vp, i, i, i]),
         "nbs_plan_create_flavours": (i, [ctypes.POINTER(vp), ctypes.POINTER(i), i, i]),
         "nbs_potential": (i, [vp, vp, vp, i, ll, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp, vp]),
+        "nbs_slab_layout": (i, [i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "nbs_slab_create": (i, [ctypes.POINTER(vp), i, i, i, ctypes.POINTER(i), i]),
+        "nbs_slab_sizes": (i, [vp, ctypes.POINTER(ll), ctypes.POINTER(ll), ctypes.POINTER(ll), ctypes.POINTER(ll)]),
+        "nbs_slab_begin": (i, [vp, vp, vp, i, ctypes.POINTER(ctypes.c_ulonglong)]),
+        "nbs_slab_blocks": (i, [vp, ctypes.POINTER(ctypes.c_ulonglong), vp]),
+        "nbs_slab_contract": (i, [vp, vp, vp]),
+        "nbs_slab_finish": (i, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -390,3 +399,95 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+# ---- L-parallel path (nbs_slab_*) ----------------------------------------------
+
+def slab_layout(L: int, nranks: int, rank: int):
+    """(z_begin, z_end, y values) of rank `rank` of nranks on an L^3 lattice (host only)."""
+    zb, ze, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ys = (ctypes.c_int * max(L, 1))()
+    _check(lib().nbs_slab_layout(L, nranks, rank, ctypes.byref(zb), ctypes.byref(ze), ys, ctypes.byref(n)))
+    return zb.value, ze.value, list(ys[:n.value])
+
+
+class SlabContext:
+    """One rank of the L-parallel path (nbs_slab_create ... nbs_destroy): the steps of a timeslice, with the
+    exchanges left to the caller (slab_correlate does them with torch.distributed)."""
+
+    def __init__(self, L: int, nranks: int, rank: int, channel_ids):
+        self._lib = lib()
+        self.L, self.nranks, self.rank = L, nranks, rank
+        self.ids = list(channel_ids)
+        h = ctypes.c_void_p()
+        ids = (ctypes.c_int * len(self.ids))(*self.ids)
+        _check(self._lib.nbs_slab_create(ctypes.byref(h), L, nranks, rank, ids, len(self.ids)))
+        self.h = h
+        self.z_begin, self.z_end, self.ys = slab_layout(L, nranks, rank)
+        c = [(ctypes.c_longlong * nranks)() for _ in range(4)]
+        _check(self._lib.nbs_slab_sizes(self.h, *c), self.h)
+        self.send_blocks, self.recv_blocks, self.send_corr, self.recv_corr = ([int(v) for v in a] for a in c)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.nbs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def begin(self, u, s):
+        """u, s: device tensors [sites of the rank's z-planes, 12, 12], complex128 or complex64; returns the two
+        max|S| bit patterns (numpy uint64[2]) to be max-reduced over the ranks."""
+        import numpy as np
+        mb = (ctypes.c_ulonglong * 2)()
+        c64 = "complex64" in str(u.dtype)
+        _check(self._lib.nbs_slab_begin(self.h, _ptr(u), _ptr(s), NBS_C64 if c64 else NBS_C128, mb), self.h)
+        self._keep = (u, s)
+        return np.array([mb[0], mb[1]], dtype=np.uint64)
+
+    def blocks(self, maxbits, send):
+        """send: complex64 device tensor of sum(send_blocks) values."""
+        mb = (ctypes.c_ulonglong * 2)(int(maxbits[0]), int(maxbits[1]))
+        _check(self._lib.nbs_slab_blocks(self.h, mb, _ptr(send)), self.h)
+
+    def contract(self, recv, send):
+        _check(self._lib.nbs_slab_contract(self.h, _ptr(recv), _ptr(send)), self.h)
+
+    def finish(self, recv, out):
+        """out: complex128 device tensor [n_channels, 4, 4, 2, 2, z_end - z_begin, L, L]."""
+        _check(self._lib.nbs_slab_finish(self.h, _ptr(recv), _ptr(out)), self.h)
+
+
+def slab_correlate(ctx: SlabContext, u, s, out, group=None):
+    """One timeslice of the L-parallel path on this rank, the exchanges done with torch.distributed (the
+    default group, or `group`): MAX-reduce of the propagator maxima, two all-to-alls."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    mb = ctx.begin(u, s)
+    m = torch.from_numpy(mb.astype(np.int64)).to(u.device)   # positive doubles order like their bit patterns
+    dist.all_reduce(m, op=dist.ReduceOp.MAX, group=group)
+    mb = m.cpu().numpy().astype(np.uint64)
+    dev = u.device
+    send = torch.empty(sum(ctx.send_blocks), dtype=torch.complex64, device=dev)
+    recv = torch.empty(sum(ctx.recv_blocks), dtype=torch.complex64, device=dev)
+    ctx.blocks(mb, send)
+    dist.all_to_all_single(torch.view_as_real(recv), torch.view_as_real(send), ctx.recv_blocks, ctx.send_blocks,
+                           group=group)
+    send2 = torch.empty(sum(ctx.send_corr), dtype=torch.complex64, device=dev)
+    recv2 = torch.empty(sum(ctx.recv_corr), dtype=torch.complex64, device=dev)
+    ctx.contract(recv, send2)
+    dist.all_to_all_single(torch.view_as_real(recv2), torch.view_as_real(send2), ctx.recv_corr, ctx.send_corr,
+                           group=group)
+    ctx.finish(recv2, out)
+    return out
