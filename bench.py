@@ -59,9 +59,11 @@ def parse():
     ap.add_argument("--decay", type=float, default=DECAY)
     ap.add_argument("--autotune", action="store_true", help="pick the contraction shape with the autotuner first")
     ap.add_argument("--no-graphs", action="store_true", help="batched workload without CUDA graphs")
-    ap.add_argument("--workload", choices=["single", "batched", "potential"], default="single",
+    ap.add_argument("--workload", choices=["single", "batched", "potential", "stream"], default="single",
                     help="batched: six configurations 2x16^3x32, 2x24^3x48, 2x32^3x32, every timeslice; "
-                         "potential: the stencil from correlators to a local potential (nbs_potential)")
+                         "potential: the stencil from correlators to a local potential (nbs_potential); "
+                         "stream: 48^3 x 64 with complex64 propagators streamed through HBM one timeslice at a "
+                         "time and every correlator copied to pinned host memory")
     return ap.parse_args()
 
 
@@ -331,6 +333,11 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.destroy_process_group()
         return
+    if args.workload == "stream":
+        run_stream(args, rank, world, P, prec, ids, dist)
+        if dist:
+            dist.destroy_process_group()
+        return
     host_props = make_props_host(L, T, seed, args.decay, args.c64)
 
     ctx = P.Context(L, T, precision=prec)
@@ -559,6 +566,82 @@ def run_batched(args, rank, world, P, prec, ids, dist=None):
                                  "nbs_correlate per (configuration, timeslice)"},
             "gpu_launches": sum((9 if BATCH[ci][0] >= 16 and prec != P.NBS_FP64 else 11) for ci, _ in jobs),
             "clocks": clocks.summary()}), flush=True)
+
+
+STREAM_L, STREAM_T, STREAM_DECAY, STREAM_SEED, STREAM_BASE = 48, 64, 0.4, 1614, 4
+
+
+def run_stream(args, rank, world, P, prec, ids, dist=None):
+    """The 48^3 x 64 configuration streamed: timeslice t's complex64 propagators are copied from pinned host
+    memory into one of two propagator slots (nbs_load_props), its correlators for all channels computed and
+    copied to pinned host memory (nbs_correlate with a host output) -- a step is one timeslice, the whole path
+    including both copies, 64 steps in all, taken in pairs (one call over two propagator slots).  The host holds STREAM_BASE seeded timeslices (t = 0..3, decay
+    exp(-0.4 t)) and timeslice t streams base t mod 4: generating all 64 at 48^3 would take minutes of host
+    time, and every step moves and computes the same amount either way."""
+    import numpy as np
+    import torch
+    L, T = STREAM_L, STREAM_T
+    V = L ** 3
+    nch = len(ids)
+    seed = STREAM_SEED + 1000 * rank
+    base = [(torch.from_numpy(I_prop(seed, "l", L, t, STREAM_DECAY).astype(np.complex64)).pin_memory(),
+             torch.from_numpy(I_prop(seed, "s", L, t, STREAM_DECAY).astype(np.complex64)).pin_memory())
+            for t in range(STREAM_BASE)]
+    out = torch.empty((nch, 2, 4, 4, 2, 2, V), dtype=torch.complex128).pin_memory()
+    ctx = P.Context(L, 2, precision=prec)
+    ctx.set_param(ctx.PARAM_CONTRACT_CFG, args.contract_cfg)
+
+    def pair(t):
+        # timeslices t, t + 1 into the two slots, then one call over both: inside it the copy-out of the
+        # first overlaps the compute of the second
+        for k in range(2):
+            u, s = base[(t + k) % STREAM_BASE]
+            ctx.load_props(u, s, k)
+        ctx.correlate(ids, 0, 2, out)
+    for t in range(0, 2 * max(2, (args.warmup + 1) // 2), 2):
+        pair(t)
+    torch.cuda.synchronize()
+    steps = T
+    ctx.set_profiling(True)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clocks:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for t in range(0, steps, 2):
+            pair(t)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+    el = max_over_ranks(el, dist, "cuda")
+    stages, launches = ctx.profile()
+    ctx.close()
+    h2d = 2 * V * 144 * 8
+    d2h = nch * 64 * V * 16
+    value = job_rate(nch * steps, world, el)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC.replace("32^3", "48^3") + " (48^3 x 64, propagators streamed)", "value": value,
+            "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": 2 * max(2, (args.warmup + 1) // 2),
+            "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {P.NBS_FP32: "f32", P.NBS_FP64: "f64", P.NBS_BF16X3: "bf16x3"}[prec],
+            "data": "synthetic: %d seeded complex64 Gaussian timeslices with exp(-0.4 t) decay, timeslice t streams "
+                    "base t mod %d" % (STREAM_BASE, STREAM_BASE),
+            "config": {"workload": "48^3 x 64 lattice, all %d channels, one timeslice per step: H2D of its "
+                                   "complex64 propagators (%.0f MB), the path, D2H of its complex128 correlators "
+                                   "(%.2f GB) to pinned host memory" % (nch, h2d / 1e6, d2h / 1e9),
+                       "timing": "host clock around the 64 steps (every copy inside), synchronised",
+                       "l2": "inputs larger than L2"},
+            "stages_ms_per_step": {k: round(v / steps, 4) for k, v in stages.items()},
+            "gpu_launches": int(launches), "clocks": clocks.summary(),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}),
+            flush=True)
+
+
+def I_prop(seed, flavour, L, t, decay):
+    import nbs_inputs as I
+    return I.propagator(seed, flavour, L, t, decay)
 
 
 def run_potential(args, rank, world, P, dist=None):

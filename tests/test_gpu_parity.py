@@ -497,3 +497,43 @@ def test_slab_wait_timeout_is_reported_and_recoverable(nbs):
         F = out.cpu().numpy()
     for k, c in enumerate(ids):
         assert rel(F[k, 0], oracle(names[c], *props[0], L)) < FP32_TOL, names[c]
+
+
+def test_batched_graph_replay_uneven_sizes_against_the_oracle(nbs):
+    """The batched workload's form: contexts of uneven size (16^3 and 24^3, two timeslices each), one CUDA
+    graph per (context, timeslice) captured once and all replayed back to back without waiting; every replay
+    equals a direct nbs_correlate of the same timeslice bit for bit, and its zero-momentum sum sum_r F(r)
+    equals the oracle's (momentum projection at q = 0) within the FP32 tolerance."""
+    names = nbs.channel_names()
+    ids = [0, 9, 24, 33, 51]
+    ctxs, jobs = [], []
+    try:
+        for L, seed in ((16, 1791), (24, 1792)):
+            props = seeded(seed, L, 2, decay=0.5)
+            ctx = nbs.Context(L, 2, precision=nbs.NBS_FP32)
+            for t, (Sl, Ss) in enumerate(props):
+                ctx.load_props(torch.from_numpy(Sl).cuda(), torch.from_numpy(Ss).cuda(), t)
+            ref = torch.empty((len(ids), 1, 4, 4, 2, 2, L ** 3), dtype=torch.complex128, device="cuda")
+            ctx.correlate(ids, 0, 1, ref)   # allocates before the captures
+            for t in range(2):
+                out = torch.full((len(ids), 1, 4, 4, 2, 2, L ** 3), float("nan"), dtype=torch.complex128,
+                                 device="cuda")
+                jobs.append((ctx, L, t, props[t], out, ctx.capture(ids, t, t + 1, out)))
+            ctxs.append(ctx)
+        for job in jobs:
+            job[5].launch(wait=False)
+        torch.cuda.synchronize()
+        for ctx, L, t, (Sl, Ss), out, g in jobs:
+            direct = torch.empty_like(out)
+            ctx.correlate(ids, t, t + 1, direct)
+            torch.cuda.synchronize()
+            assert torch.equal(out, direct), (L, t)
+            zm = out.cpu().numpy()[:, 0].sum(axis=-1)
+            sums = O.PhaseSums({"u": Sl, "d": Sl, "s": Ss}, L, [(0, 0, 0)])
+            for k, c in enumerate(ids):
+                assert rel(zm[k], O.momentum_projection(names[c], sums, [(0, 0, 0)])[0]) < FP32_TOL, (L, t, names[c])
+    finally:
+        for job in jobs:
+            job[5].close()
+        for c in ctxs:
+            c.close()
