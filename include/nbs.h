@@ -76,16 +76,25 @@ int nbs_set_allocator(nbs_alloc_fn alloc, nbs_free_fn free_fn, void* user);
  * 1 <= L <= 64, 1 <= T <= 4096.  Allocates the propagator store
  * (flavours x T timeslices). */
 int nbs_create(nbs_ctx** out, int L, int T, int flavours);
+/* Wait for the context's stream, then release every device and host buffer
+ * of the context (propagator store, blocks, tables, the L-parallel buffers).
+ * Graphs captured from it must be destroyed first.  NULL is a no-op. */
 int nbs_destroy(nbs_ctx* h);
 
-/* Select the arithmetic of the path (NBS_FP64 default, NBS_FP32 or NBS_BF16X3). */
+/* Select the arithmetic of the path (NBS_FP64 default, NBS_FP32 or NBS_BF16X3).
+ * The paper computes in FP64 throughout (Sec. 3, Sec. 5); NBS_FP32 and
+ * NBS_BF16X3 rescale each timeslice's propagators by a power of two in FP64
+ * and undo it exactly in FP64 after the inverse FFT of Eq. (2.6).  Blocks
+ * built in another mode are rebuilt by the next nbs_correlate; NBS_EINVAL
+ * for another mode. */
 int nbs_set_precision(nbs_ctx* h, int mode);
 
 /* Run every later call of the context on this cudaStream_t (0 = legacy default). */
 int nbs_set_stream(nbs_ctx* h, void* stream);
 
 /* Copy one timeslice of the light (u) and strange (s) propagators into the
- * context.  Layout of each: [z][y][x][i = 3*alpha + a][j = 3*alpha' + a'],
+ * context: the wall-source quark propagators S(x, t; t0) from which the
+ * blocks of Eq. (4.1) are built (Sec. 2; u = d in the isospin limit).  Layout of each: [z][y][x][i = 3*alpha + a][j = 3*alpha' + a'],
  * V*144 complex numbers of `dtype`; on_device selects device or host
  * pointers.  The library copies; the caller keeps ownership.  0 <= t < T. */
 int nbs_load_props(nbs_ctx* h, const void* u, const void* s, int t, int dtype, int on_device);
