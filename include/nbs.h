@@ -205,12 +205,14 @@ int nbs_zero_momentum(nbs_ctx* h, double* out);
 /* NBS_PARAM_FFT_BLOCK: threads per block of the strided (y, z) passes of the
  * 3-D FFTs: 64, 128 (default) or 256. */
 #define NBS_PARAM_FFT_BLOCK 2
-/* NBS_PARAM_TEST_SKIP_SLAB (test switch, 0 by default): 1 makes the FP32
- * two-phase contraction arm its first slab wait in every block without
- * issuing the copy, so that the bounded wait runs out with no copy in
- * flight and nbs_correlate (or a waited nbs_graph_launch of a graph captured
- * meanwhile) returns NBS_ETIMEOUT; it exercises the failure path without a
- * device fault.  Each block waits about one second before it gives up. */
+/* NBS_PARAM_TEST_SKIP_SLAB (test switch, 0 by default): 1 makes the
+ * TMA-staged quad-lane contraction (FP32, NBS_PARAM_CONTRACT_CFG 4) arm its
+ * first slab wait in every block without issuing the copy, so that the
+ * bounded wait runs out with no copy in flight and nbs_correlate (or a
+ * waited nbs_graph_launch of a graph captured meanwhile) returns
+ * NBS_ETIMEOUT; it exercises the failure path without a device fault.  Each
+ * block waits about one second before it gives up.  (The default two-phase
+ * kernel stages its slabs with cp.async gathers and has no bounded wait.) */
 #define NBS_PARAM_TEST_SKIP_SLAB 3
 int nbs_set_param(nbs_ctx* h, int param, int value);
 
@@ -219,8 +221,10 @@ int nbs_set_param(nbs_ctx* h, int param, int value);
  * every stage of later calls; nbs_profile() returns the accumulated device
  * milliseconds per stage, stage_ms[NBS_NSTAGES] = {rescale (a0), blocks (a1),
  * forward FFT (a2), effective blocks + contraction (a3, a4), inverse FFT (a5),
- * restore + output copy (a5)}, and the number of kernels launched. */
-#define NBS_NSTAGES 6
+ * restore + output copy (a5), effective-block rows (a3, where the FP32
+ * two-phase contraction builds them in a kernel of their own; this time is
+ * also part of stage 3)}, and the number of kernels launched. */
+#define NBS_NSTAGES 7
 int nbs_set_profiling(nbs_ctx* h, int on);
 int nbs_profile(nbs_ctx* h, double* stage_ms, long long* launches);
 
@@ -364,32 +368,37 @@ int nbs_plan_sizes(const nbs_plan* p, long long* sizes);
                                  back to back, or one term): form (0..3 shape, 4..7 the fixed
                                  forms), side-1 and side-2 table offsets, first and end shared
                                  index, chunk-local channel, n1, n2                            */
-#define NBS_PX_ROWCHUNKS 20   /* int32 [nchunks][96]: the two-phase kernel's chunks: base1, ncell1, base2,
-                                 ncell2, nrow1, nrow2, aent_off, naent, adesc_off, nadesc, rec_off, nstep,
-                                 ch_off, nch, nslot, seg_off, smem, nbuf, seg_base[W + 1], out_base[W + 1],
-                                 cfirst[W], padding (W = the block's warps, NBS_PRS_WARPS)                 */
-#define NBS_PX_ROWAENT   21   /* uint16: row entries, planar slab unit (bits 0..11: side * 1888 + (cell / 236)
-                                 * 472 + cell % 236) | code (bits 12..13: +1, -1, +2, -2)                 */
-#define NBS_PX_ROWADESC  22   /* uint32 per distinct row: entry offset in its chunk (bits 0..13) |
-                                 count << 14 | row slot << 19 (B2's rows from nrow1)                     */
-#define NBS_PX_ROWREC    23   /* uint32 [step][8 xi~][4 s]: B1 row (bits 0..11) | B2 row << 12 |
-                                 scale code << 24; four padding steps follow the last chunk              */
+#define NBS_PX_ROWCHUNKS 20   /* int32 [nchunks][96]: the product kernel's chunks: type1, type2, roff1,
+                                 nrow1, roff2, nrow2, rec_off, nstep, ch_off, nch, nslot, seg_off, smem, 0,
+                                 seg_base[W + 1], out_base[W + 1], cfirst[W], padding (W = the kernel's
+                                 record-walking warps, NBS_PRS_WARPS)                                      */
+#define NBS_PX_ROWENT    21   /* uint16: row entries, cell of the row's stored type (bits 0..11) | code
+                                 (bits 12..13: +1, -1, +2, -2)                                             */
+#define NBS_PX_ROWDESC   22   /* uint32 per row (all types, row order): entry offset (bits 0..23) |
+                                 count << 24 | type << 29; padding rows have count 0                      */
+#define NBS_PX_ROWREC    23   /* uint32 [step][8 xi~][4 s]: B1 row (bits 0..11, of type1) | B2 row << 12
+                                 (of type2) | scale code << 24; four padding steps follow the last chunk  */
 #define NBS_PX_ROWCH     24   /* int32: request-order channel of each chunk channel                       */
 #define NBS_PX_ROWSEGS   25   /* int32 [nsegs][4]: first step, end step, chunk-local channel, 0           */
 #define NBS_PX_ROWSCALES 26   /* double [32]: the scale of each code (code 31 = 0)                          */
+#define NBS_PX_ROWTYPES  27   /* int32 [ntypes][8]: stored type's first cell, cells, first row, rows, 0... */
 int nbs_plan_export(const nbs_plan* p, int what, void* dst);
-/* Sizes of the two-phase contraction's tables (rows of the effective blocks
- * per chunk of channels, Eqs. (4.2)-(4.3)): sizes[0..NBS_PRS_N-1]. */
+/* Sizes of the two-phase contraction's tables (the rows of the effective
+ * blocks per stored type, Eq. (4.2), and the product records per chunk of
+ * channels, Eq. (4.3)): sizes[0..NBS_PRS_N-1]. */
 #define NBS_PRS_OK       0   /* 1 if every chunk fits a block's shared memory     */
 #define NBS_PRS_NCHUNKS  1
-#define NBS_PRS_NAENT    2
-#define NBS_PRS_NADESC   3
+#define NBS_PRS_NENT     2   /* row entries                                      */
+#define NBS_PRS_NROWS    3   /* rows per momentum, all stored types              */
 #define NBS_PRS_NREC     4
 #define NBS_PRS_NCH      5
 #define NBS_PRS_NSEGS    6
 #define NBS_PRS_SMEM     7   /* the largest chunk's shared memory (bytes)        */
-#define NBS_PRS_WARPS    8   /* warps per block of the two-phase kernel          */
-#define NBS_PRS_N        9
+#define NBS_PRS_WARPS    8   /* record-walking (consumer) warps per block of the
+                                product kernel; four helper warps copy the rows
+                                and sum the slots                               */
+#define NBS_PRS_NTYPES   9   /* stored types with rows                          */
+#define NBS_PRS_N       10
 int nbs_plan_row_sizes(const nbs_plan* p, long long* sizes);
 
 #ifdef __cplusplus

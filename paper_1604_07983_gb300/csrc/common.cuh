@@ -116,7 +116,7 @@ size_t qseg_smem_bytes(int max_slot, int max_tab, int max_segs);
 cudaError_t launch_contract_qseg(const float2* FB, long long ncells, int L, int nchunks, int qb, const void* chunks,
                                  const void* segs, int max_segs, const int* group_ch, const unsigned short* tab,
                                  const float* codes, int max_cells, int max_slot, int max_tab, int max_row, float2* Ft,
-                                 int* flags, cudaStream_t st);
+                                 int* flags, int skip_first, cudaStream_t st);
 // quad-lane tensor-core contraction (split-BF16 x 3): same arguments
 size_t tcq_smem_bytes(int max_slot, int max_tab, int max_segs);
 cudaError_t launch_contract_tcq(const float2* FB, long long ncells, int L, int nchunks, int qb, const void* chunks,
@@ -145,11 +145,15 @@ inline MomGeom full_geom(int L) {
   for (int y = 0; y < 64; ++y) g.ymir[y] = y < L ? (L - y) % L : 0;
   return g;
 }
-cudaError_t launch_contract_rows(const float2* FB, long long ncells, const MomGeom& geom, int nchunks, int qb,
-                                 const void* chunks,
-                                 const unsigned short* aent, const unsigned* adesc, const unsigned* rec,
-                                 const void* segs, const int* row_ch, const float* scales, int smem, float2* Ft,
-                                 int* flags, int skip_first, cudaStream_t st);
+// phase A of the FP32 contraction: the rows of every stored type at every momentum (RQ: 2 NR 16-byte units
+// per momentum); types, desc, ent: Plan::row_types, row_desc, row_ent in device memory
+cudaError_t launch_eff_rows(const float2* FB, long long V, const void* types, const unsigned* desc,
+                            const unsigned short* ent, int NR, float2* RQ, int nsm, cudaStream_t st);
+// phase B; qlist: the momenta in visiting order as (q, -q) pairs (momentum_order), device memory
+cudaError_t launch_contract_rows(const float2* RQ, const MomGeom& geom, int NR, const int2* qlist, int nchunks, int qb,
+                                 const void* chunks, const unsigned* rec, const void* segs, const int* row_ch,
+                                 const float* scales, int smem, float2* Ft, int* flags, cudaStream_t st);
+std::vector<int2> momentum_order(const MomGeom& g);
 // ---- L-parallel path (slab.cu) -------------------------------------------------------
 #define NBS_SLAB_MAX_RANKS 64
 // ranks' z-planes [z0[p], z0[p+1]); y-sets: owner rank and local index of each y, set sizes

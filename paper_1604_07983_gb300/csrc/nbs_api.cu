@@ -90,7 +90,9 @@ struct nbs_ctx {
   DevBuf d_chunks, d_qchunks, d_qsegs, d_ctab, d_citems, d_ctoff, d_codes;
   int chunk_st1 = 0, chunk_st2 = 0, chunk_slot = 0, chunk_tab = 0, chunk_row = 0, quad_slot = 0;
   int chunk_qb = 32;
-  DevBuf d_rchunks, d_raent, d_radesc, d_rrec, d_rsegs, d_rch, d_rscales;  // two-phase contraction tables
+  DevBuf d_rchunks, d_rtypes, d_rdesc, d_rent, d_rrec, d_rsegs, d_rch, d_rscales;  // two-phase contraction tables
+  DevBuf d_qlist;  // momenta in the product kernel's visiting order
+  DevBuf RQ;       // effective-block rows of every stored type, momentum-major (FP32 two-phase path)
   int test_skip_slab = 0;  // NBS_PARAM_TEST_SKIP_SLAB (test switch)
   // one rank of the L-parallel path (nbs_slab_create): its z-planes, its mirror-closed y-set
   bool slab = false;
@@ -111,6 +113,7 @@ struct nbs_ctx {
   int last_nch = 0;
   int contract_cfg = 0;  // NBS_PARAM_CONTRACT_CFG, 0 = default
   int smem_optin = 0;    // the device's shared memory per block (opt-in)
+  int nsm = 0;           // the device's multiprocessors
 
   // profiling: CUDA events around each stage, resolved after the final sync
   bool prof = false;
@@ -258,18 +261,21 @@ int upload_tables(nbs_ctx* h) {
     float sc[NBS_ROW_SCALES];
     for (int i = 0; i < NBS_ROW_SCALES; ++i) sc[i] = (float)P.row_scales[i];
     if ((rc = ensure(h, h->d_rchunks, P.row_chunks.size() * sizeof(RowChunkHdr), "row chunks"))) return rc;
-    if ((rc = ensure(h, h->d_raent, std::max<size_t>(P.row_aent.size(), 8) * 2, "row entries"))) return rc;
-    if ((rc = ensure(h, h->d_radesc, std::max<size_t>(P.row_adesc.size(), 4) * 4, "row descriptors"))) return rc;
+    if ((rc = ensure(h, h->d_rtypes, P.row_types.size() * sizeof(RowTypeHdr), "row types"))) return rc;
+    if ((rc = ensure(h, h->d_rdesc, std::max<size_t>(P.row_desc.size(), 8) * 4, "row descriptors"))) return rc;
+    if ((rc = ensure(h, h->d_rent, std::max<size_t>(P.row_ent.size(), 8) * 2, "row entries"))) return rc;
     if ((rc = ensure(h, h->d_rrec, std::max<size_t>(P.row_rec.size(), 32) * 4, "row records"))) return rc;
     if ((rc = ensure(h, h->d_rsegs, std::max<size_t>(P.row_segs.size(), 1) * sizeof(RowSeg), "row segments"))) return rc;
     if ((rc = ensure(h, h->d_rch, std::max<size_t>(P.row_ch.size(), 1) * sizeof(int), "row channels"))) return rc;
     if ((rc = ensure(h, h->d_rscales, sizeof(sc), "row scales"))) return rc;
     CK(cudaMemcpyAsync(h->d_rchunks.p, P.row_chunks.data(), P.row_chunks.size() * sizeof(RowChunkHdr),
                        cudaMemcpyHostToDevice, h->st), "upload row chunks");
-    CK(cudaMemcpyAsync(h->d_raent.p, P.row_aent.data(), P.row_aent.size() * 2, cudaMemcpyHostToDevice, h->st),
-       "upload row entries");
-    CK(cudaMemcpyAsync(h->d_radesc.p, P.row_adesc.data(), P.row_adesc.size() * 4, cudaMemcpyHostToDevice, h->st),
+    CK(cudaMemcpyAsync(h->d_rtypes.p, P.row_types.data(), P.row_types.size() * sizeof(RowTypeHdr),
+                       cudaMemcpyHostToDevice, h->st), "upload row types");
+    CK(cudaMemcpyAsync(h->d_rdesc.p, P.row_desc.data(), P.row_desc.size() * 4, cudaMemcpyHostToDevice, h->st),
        "upload row descriptors");
+    CK(cudaMemcpyAsync(h->d_rent.p, P.row_ent.data(), P.row_ent.size() * 2, cudaMemcpyHostToDevice, h->st),
+       "upload row entries");
     CK(cudaMemcpyAsync(h->d_rrec.p, P.row_rec.data(), P.row_rec.size() * 4, cudaMemcpyHostToDevice, h->st),
        "upload row records");
     CK(cudaMemcpyAsync(h->d_rsegs.p, P.row_segs.data(), P.row_segs.size() * sizeof(RowSeg), cudaMemcpyHostToDevice,
@@ -277,6 +283,11 @@ int upload_tables(nbs_ctx* h) {
     CK(cudaMemcpyAsync(h->d_rch.p, P.row_ch.data(), P.row_ch.size() * sizeof(int), cudaMemcpyHostToDevice, h->st),
        "upload row channels");
     CK(cudaMemcpyAsync(h->d_rscales.p, sc, sizeof(sc), cudaMemcpyHostToDevice, h->st), "upload row scales");
+    const std::vector<int2> qo = momentum_order(h->slab ? h->smg : full_geom(h->L));
+    if (qo.empty()) return fail(h, NBS_EINVAL, "no momentum order for this geometry");
+    if ((rc = ensure(h, h->d_qlist, qo.size() * sizeof(int2), "momentum order"))) return rc;
+    CK(cudaMemcpyAsync(h->d_qlist.p, qo.data(), qo.size() * sizeof(int2), cudaMemcpyHostToDevice, h->st),
+       "upload momentum order");
     CK(cudaStreamSynchronize(h->st), "upload sync");
   }
   CK(cudaMemcpyAsync(h->d_groups.p, P.groups.data(), P.groups.size() * sizeof(GroupHdr), cudaMemcpyHostToDevice, h->st), "upload groups");
@@ -391,6 +402,11 @@ int build_blocks(nbs_ctx* h, int t) {
 }
 
 // every device buffer nbs_correlate(nch channels) needs, allocated now
+// the two-phase FP32 contraction runs: FP32 mode, the default contraction, tables that fit the device
+bool rows_path(const nbs_ctx* h) {
+  return h->mode == NBS_FP32 && h->contract_cfg == 0 && h->plan.rows_ok && h->plan.row_smem <= h->smem_optin;
+}
+
 template <typename T>
 int prepare(nbs_ctx* h, int nch) {
   const int V = h->V;
@@ -398,6 +414,9 @@ int prepare(nbs_ctx* h, int nch) {
   if ((rc = ensure(h, h->propsT, (size_t)h->nflav * 144 * V * sizeof(C<T>), "scaled propagators"))) return rc;
   if ((rc = ensure(h, h->FB, 4ull * h->plan.ncells * V * sizeof(C<T>), "baryon blocks"))) return rc;
   if ((rc = ensure(h, h->Ft, (size_t)nch * 64 * V * sizeof(C<T>), "momentum-space correlators"))) return rc;
+  if (sizeof(T) == 4 && rows_path(h) &&
+      (rc = ensure(h, h->RQ, (size_t)V * h->plan.row_nr * 32, "effective-block rows")))
+    return rc;
   return ensure(h, h->zm, (size_t)nch * 64 * sizeof(C<T>), "zero momentum");
 }
 
@@ -408,6 +427,9 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
   int rc;
   if ((rc = ensure(h, h->Ft, (size_t)nch * 64 * V * sizeof(C<T>), "momentum-space correlators"))) return rc;
   if ((rc = ensure(h, h->zm, (size_t)nch * 64 * sizeof(C<T>), "zero momentum"))) return rc;
+  if (sizeof(T) == 4 && rows_path(h) &&
+      (rc = ensure(h, h->RQ, (size_t)V * h->plan.row_nr * 32, "effective-block rows")))
+    return rc;
   const size_t per_t = (size_t)nch * 64 * V * sizeof(double2);
   CK(cudaMemsetAsync(h->flags, 0, sizeof(int), h->st), "clear NaN flag");
   if (!on_dev) {
@@ -428,14 +450,18 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
                            tcq_smem_bytes(h->quad_slot, h->chunk_tab, h->plan.max_quad_segs) <= (size_t)h->smem_optin;
     // the two-phase row kernel: FP32 default where its tables fit the device's shared memory
     const bool rows_fit = sizeof(T) == 4 && h->plan.rows_ok && h->plan.row_smem <= h->smem_optin;
-    const bool use_rows = rows_fit && h->mode == NBS_FP32 && h->contract_cfg == 0;
+    const bool use_rows = sizeof(T) == 4 && rows_path(h);
     const bool use_qseg = f32_chunks && quad_fits && (h->contract_cfg == 4 || (h->contract_cfg == 0 && !rows_fit));
     if (use_rows) {
-      CK(launch_contract_rows((const float2*)h->FB.p, h->plan.ncells, full_geom(h->L), (int)h->plan.row_chunks.size(),
-                              h->chunk_qb, h->d_rchunks.p, (const unsigned short*)h->d_raent.p,
-                              (const unsigned*)h->d_radesc.p, (const unsigned*)h->d_rrec.p, h->d_rsegs.p,
-                              (const int*)h->d_rch.p, (const float*)h->d_rscales.p, h->plan.row_smem,
-                              (float2*)h->Ft.p, h->flags, h->test_skip_slab, h->st),
+      cudaEvent_t e6 = stage_begin(h);
+      CK(launch_eff_rows((const float2*)h->FB.p, V, h->d_rtypes.p, (const unsigned*)h->d_rdesc.p,
+                         (const unsigned short*)h->d_rent.p, h->plan.row_nr, (float2*)h->RQ.p, h->nsm, h->st),
+         "effective-block rows");
+      stage_end(h, 6, e6);
+      CK(launch_contract_rows((const float2*)h->RQ.p, full_geom(h->L), h->plan.row_nr, (const int2*)h->d_qlist.p,
+                              (int)h->plan.row_chunks.size(), h->chunk_qb, h->d_rchunks.p, (const unsigned*)h->d_rrec.p,
+                              h->d_rsegs.p, (const int*)h->d_rch.p, (const float*)h->d_rscales.p, h->plan.row_smem,
+                              (float2*)h->Ft.p, h->flags, h->st),
          "contraction (rows)");
     } else if (h->mode == NBS_BF16X3 && quad_fits && h->contract_cfg != 2) {
       CK(launch_contract_tcq((const float2*)h->FB.p, h->plan.ncells, h->L, (int)h->plan.quad_chunks.size(),
@@ -456,7 +482,7 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
                               h->chunk_qb, h->d_qchunks.p, h->d_qsegs.p, h->plan.max_quad_segs,
                               (const int*)h->d_gch.p, (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
                               std::max(h->chunk_st1, h->chunk_st2), h->quad_slot, h->chunk_tab, h->chunk_row,
-                              (float2*)h->Ft.p, h->flags, h->st),
+                              (float2*)h->Ft.p, h->flags, h->test_skip_slab, h->st),
          "contraction");
     } else if (f32_chunks && (h->contract_cfg == 3 || h->contract_cfg == 0)) {
       CK(launch_contract_chunk2((const float2*)h->FB.p, h->L, (int)h->plan.chunks.size(), h->chunk_qb,
@@ -531,7 +557,7 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
   prof_resolve(h);
   if (*h->host_flags) {
     h->blocks_t = -1;
-    if (*h->host_flags & 2) return fail(h, NBS_ETIMEOUT, "a slab copy wait in the contraction gave up");
+    if (*h->host_flags & 2) return fail(h, NBS_ETIMEOUT, "a bounded wait in the contraction gave up");
     return fail(h, NBS_ENAN, "non-finite value in the propagators");
   }
   h->last_nch = nch;
@@ -578,9 +604,10 @@ int create_ctx(nbs_ctx** out, int L, int T, int flavours, bool store) {
   h->have.assign(T, -1);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "cudaGetDevice"); }
-  if ((e = cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device)) != cudaSuccess) {
+  if ((e = cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess) {
     delete h;
-    return cuda_fail(nullptr, e, "shared memory limit");
+    return cuda_fail(nullptr, e, "device attributes");
   }
   if ((e = fft_init()) != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "FFT twiddles"); }
   if ((e = cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking)) != cudaSuccess) {
@@ -619,8 +646,8 @@ int nbs_destroy(nbs_ctx* h) {
   DevBuf* bufs[] = {&h->props, &h->propsT, &h->FB, &h->Ft, &h->zm, &h->small, &h->stage[0], &h->stage[1],
                     &h->d_terms, &h->d_chtb, &h->d_chnl, &h->d_e1, &h->d_e2, &h->d_cells, &h->d_groups,
                     &h->d_gch, &h->d_items, &h->d_chunks, &h->d_qchunks, &h->d_qsegs, &h->d_ctab, &h->d_citems, &h->d_ctoff,
-                    &h->d_codes, &h->d_rchunks, &h->d_raent, &h->d_radesc, &h->d_rrec, &h->d_rsegs, &h->d_rch,
-                    &h->d_rscales, &h->s_FB, &h->s_FBm, &h->s_Ft, &h->s_F};
+                    &h->d_codes, &h->d_rchunks, &h->d_rtypes, &h->d_rdesc, &h->d_rent, &h->d_rrec, &h->d_rsegs,
+                    &h->d_rch, &h->d_rscales, &h->d_qlist, &h->RQ, &h->s_FB, &h->s_FBm, &h->s_Ft, &h->s_F};
   for (DevBuf* b : bufs) dev_free(b->p, h->free_fn, h->free_user);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   for (int b = 0; b < 2; ++b) {
@@ -944,13 +971,14 @@ int nbs_plan_row_sizes(const nbs_plan* p, long long* s) {
   const Plan& P = p->plan;
   s[NBS_PRS_OK] = P.rows_ok ? 1 : 0;
   s[NBS_PRS_NCHUNKS] = (long long)P.row_chunks.size();
-  s[NBS_PRS_NAENT] = (long long)P.row_aent.size();
-  s[NBS_PRS_NADESC] = (long long)P.row_adesc.size();
+  s[NBS_PRS_NENT] = (long long)P.row_ent.size();
+  s[NBS_PRS_NROWS] = (long long)P.row_desc.size();
   s[NBS_PRS_NREC] = (long long)P.row_rec.size();
   s[NBS_PRS_NCH] = (long long)P.row_ch.size();
   s[NBS_PRS_NSEGS] = (long long)P.row_segs.size();
   s[NBS_PRS_SMEM] = P.row_smem;
   s[NBS_PRS_WARPS] = NBS_ROW_WARPS;
+  s[NBS_PRS_NTYPES] = (long long)P.row_types.size();
   return NBS_OK;
 }
 
@@ -1022,8 +1050,12 @@ int nbs_plan_export(const nbs_plan* p, int what, void* dst) {
       static_assert(sizeof(RowChunkHdr) == 96 * sizeof(int), "row chunk header layout");
       std::memcpy(I, P.row_chunks.data(), P.row_chunks.size() * sizeof(RowChunkHdr));
       return NBS_OK;
-    case NBS_PX_ROWAENT: std::memcpy(dst, P.row_aent.data(), P.row_aent.size() * 2); return NBS_OK;
-    case NBS_PX_ROWADESC: std::memcpy(dst, P.row_adesc.data(), P.row_adesc.size() * 4); return NBS_OK;
+    case NBS_PX_ROWENT: std::memcpy(dst, P.row_ent.data(), P.row_ent.size() * 2); return NBS_OK;
+    case NBS_PX_ROWTYPES:
+      static_assert(sizeof(RowTypeHdr) == 8 * sizeof(int), "row type header layout");
+      std::memcpy(I, P.row_types.data(), P.row_types.size() * sizeof(RowTypeHdr));
+      return NBS_OK;
+    case NBS_PX_ROWDESC: std::memcpy(dst, P.row_desc.data(), P.row_desc.size() * 4); return NBS_OK;
     case NBS_PX_ROWREC: std::memcpy(dst, P.row_rec.data(), P.row_rec.size() * 4); return NBS_OK;
     case NBS_PX_ROWCH: std::memcpy(I, P.row_ch.data(), P.row_ch.size() * sizeof(int)); return NBS_OK;
     case NBS_PX_ROWSEGS:
@@ -1103,7 +1135,8 @@ int nbs_slab_create(nbs_ctx** out, int L, int nranks, int rank, const int* chann
       (rc = ensure(h, h->s_FB, 4ull * nc * h->svs * sizeof(float2), "slab blocks")) ||
       (rc = ensure(h, h->s_FBm, 4ull * nc * h->svm * sizeof(float2), "momentum-set blocks")) ||
       (rc = ensure(h, h->s_Ft, (size_t)n64 * h->svm * sizeof(float2), "momentum-set correlators")) ||
-      (rc = ensure(h, h->s_F, (size_t)n64 * h->svs * sizeof(float2), "slab correlators"))) {
+      (rc = ensure(h, h->s_F, (size_t)n64 * h->svs * sizeof(float2), "slab correlators")) ||
+      (rc = ensure(h, h->RQ, (size_t)h->svm * h->plan.row_nr * 32, "effective-block rows"))) {
     std::string m = h->err;
     nbs_destroy(h);
     return fail(nullptr, rc, m);
@@ -1178,17 +1211,20 @@ int nbs_slab_contract(nbs_ctx* h, const void* recv, void* send) {
   CK(fft_lines<float>(fbm, nc * ny * 4LL * L, 4 * L * ny, 4LL * L * ny * L, 4LL * L * ny, L, -1, h->fft_block, h->st),
      "z pass");
   CK(cudaMemsetAsync(h->flags, 0, sizeof(int), h->st), "clear flags");
-  CK(launch_contract_rows(fbm, nc, h->smg, (int)P.row_chunks.size(), h->chunk_qb, h->d_rchunks.p,
-                          (const unsigned short*)h->d_raent.p, (const unsigned*)h->d_radesc.p,
-                          (const unsigned*)h->d_rrec.p, h->d_rsegs.p, (const int*)h->d_rch.p,
-                          (const float*)h->d_rscales.p, P.row_smem, ft, h->flags, h->test_skip_slab, h->st),
+  CK(launch_eff_rows(fbm, h->svm, h->d_rtypes.p, (const unsigned*)h->d_rdesc.p, (const unsigned short*)h->d_rent.p,
+                     P.row_nr, (float2*)h->RQ.p, h->nsm, h->st),
+     "effective-block rows on the momentum set");
+  CK(launch_contract_rows((const float2*)h->RQ.p, h->smg, P.row_nr, (const int2*)h->d_qlist.p,
+                          (int)P.row_chunks.size(), h->chunk_qb, h->d_rchunks.p, (const unsigned*)h->d_rrec.p,
+                          h->d_rsegs.p, (const int*)h->d_rch.p, (const float*)h->d_rscales.p, P.row_smem, ft,
+                          h->flags, h->st),
      "contraction on the momentum set");
   CK(fft_lines<float>(ft, n64 * ny * L, L * ny, (long long)L * ny * L, (long long)L * ny, L, 1, h->fft_block, h->st),
      "inverse z pass");
   CK(launch_slab_move(SLAB_PACK_CORR, ft, send, n64, h->sg, h->soff[2], h->st), "pack for the inverse exchange");
   CK(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->st), "flags");
   CK(cudaStreamSynchronize(h->st), "sync");
-  if (*h->host_flags & 2) return fail(h, NBS_ETIMEOUT, "a slab copy wait in the contraction gave up");
+  if (*h->host_flags & 2) return fail(h, NBS_ETIMEOUT, "a bounded wait in the contraction gave up");
   return NBS_OK;
 }
 

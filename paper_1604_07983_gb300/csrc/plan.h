@@ -115,35 +115,44 @@ struct QuadChunkHdr {
 struct QuadSeg { int form, t1, t2, kbeg, kend, local, n1, n2; };
 
 // Two-phase contraction over distinct effective-block rows (kernels_rows.cu).
-// Within a chunk (whole channels of one slab group) every row of an effective
-// block -- one shared index xi~ and one held source spin of one side, i.e. a
-// sum of stored cells with coefficients -- is built once per momentum for all
-// four sink spins (phase A, Eq. (4.2)); a row is kept up to a scale: its
-// coefficients divided by the magnitude m of its term side are +-1 or +-2,
-// and its sign is fixed by its first entry.  Phase B forms the product of
-// Eq. (4.3) from the rows: record (xi~, s) names the row of B1 and of B2 for
-// output source-spin pair s and the scale m1 m2 sign1 sign2 (a code into
+// A row of an effective block -- one shared index xi~ and one held source
+// spin of one side, i.e. a sum of stored cells with coefficients -- is kept up
+// to a scale: its coefficients divided by the magnitude m of its term side are
+// +-1 or +-2, and its sign is fixed by its first entry.  Over all channels the
+// rows depend only on the stored type they sum (and not on the channel or the
+// side), a few hundred per type: phase A (Eq. (4.2)) builds every row of every
+// type once per momentum, for all four sink spins, into a momentum-major array
+// (its own kernel); phase B forms the product of Eq. (4.3) per chunk (whole
+// channels of one slab group, i.e. one pair of stored types) from the rows of
+// type1 at q and type2 at -q: record (xi~, s) names the row of B1 and of B2
+// for output source-spin pair s and the scale m1 m2 sign1 sign2 (a code into
 // Plan::row_scales).  Lane 4 kq + s of a warp takes record (8 step + kq, s),
 // so a warp step covers eight shared indices of all four s.
-#define NBS_ROW_WARPS 16
-#define NBS_ROW_SLAB 944            // cells per slab side in shared memory
-#define NBS_ROW_BOX 236             // cells per TMA box (four boxes per side)
-#define NBS_ROW_MAX_ROWS 4095       // row slots per side (12-bit row index in a record)
+#define NBS_ROW_WARPS 12            // consumer warps of the product kernel (record ranges)
+#define NBS_ROW_HELPERS 4           // its helper warps (row copies, slot sums)
+#define NBS_ROW_STAGES 3            // momenta of rows in flight per block
+#define NBS_ROW_MAX_ROWS 4095       // row slots per type (12-bit row index in a record)
 #define NBS_ROW_SCALES 32           // scale codes (code 31 = 0)
 #define NBS_ROW_SMEM_LIMIT 232448   // shared memory per block the tables are cut for (GB300 opt-in)
+// Rows of one stored type: per momentum they occupy 16-byte units
+// [2 roff, 2 roff + 2 nrow) of the momentum's block of 2 row_nr units: sink
+// spins 0, 1 of row r at 2 roff + r, spins 2, 3 at 2 roff + nrow + r.
+struct RowTypeHdr {
+  int base, ncell;                   // the stored type's cells
+  int roff, nrow;                    // first row (a multiple of 8) and rows (a multiple of 8, padding rows empty)
+  int pad[4];
+};
 struct RowChunkHdr {
-  int base1, ncell1, base2, ncell2;  // the group's two stored types
-  int nrow1, nrow2;                  // row slots of B1 (at q) and of B2 (at -q), multiples of 8
-  int aent_off, naent;               // phase-A entries (uint16) into Plan::row_aent
-  int adesc_off, nadesc;             // phase-A row descriptors (one per distinct row) into Plan::row_adesc
+  int type1, type2;                  // row types of B1 (at q) and of B2 (at -q)
+  int roff1, nrow1, roff2, nrow2;    // their first rows and row counts
   int rec_off, nstep;                // 32 records (uint32) per step into Plan::row_rec
   int ch_off, nch;                   // chunk channels into Plan::row_ch (request-order indices)
   int nslot, seg_off, smem;          // per-warp partial-sum slots; segments into Plan::row_segs; bytes
-  int nbuf;                          // row buffers: 2 (phase A of q + 1 overlaps phase B of q) or 1
+  int pad0;
   int seg_base[NBS_ROW_WARPS + 1];   // warp w walks segments seg_base[w] .. seg_base[w + 1] (relative)
   int out_base[NBS_ROW_WARPS + 1];   // its slots start at out_base[w] (chunk-local channel - cfirst[w])
   int cfirst[NBS_ROW_WARPS];
-  int pad[96 - 20 - 3 * NBS_ROW_WARPS];  // 96 ints
+  int pad[96 - 16 - 3 * NBS_ROW_WARPS];  // 96 ints
 };
 // Steps [sbeg, send) of chunk-local channel `local` (one flush at the end).
 struct RowSeg { int sbeg, send, local, pad; };
@@ -172,9 +181,11 @@ struct Plan {
   std::vector<QuadSeg> quad_segs;             // per-warp term runs of every quad chunk
   int max_quad_segs = 0;                      // most segments of one chunk
   bool rows_ok = false;                       // every chunk of the two-phase tables fits shared memory
+  std::vector<RowTypeHdr> row_types;
+  std::vector<unsigned> row_desc;             // per row (all types): entry offset (bits 0..23) | count << 24 | type << 29
+  std::vector<unsigned short> row_ent;        // cell of the type (bits 0..11) | coefficient code (bits 12..13: +1 -1 +2 -2)
+  int row_nr = 0;                             // rows per momentum (all types)
   std::vector<RowChunkHdr> row_chunks;
-  std::vector<unsigned short> row_aent;       // planar slab unit (bits 0..11) | coefficient code (bits 12..13: +1 -1 +2 -2)
-  std::vector<unsigned> row_adesc;            // entry offset in the chunk (bits 0..13) | count << 14 | row << 19
   std::vector<unsigned> row_rec;              // B1 row (bits 0..11) | B2 row << 12 | scale code << 24
   std::vector<int> row_ch;
   std::vector<RowSeg> row_segs;
@@ -196,7 +207,7 @@ std::string compile_plan(const std::vector<int>& channel_ids, Plan& out, int nfl
 // Two-phase contraction tables (plan_rows.cpp); smem_limit: bytes per block.
 void build_row_chunks(Plan& plan, int smem_limit);
 // Shared memory of one chunk of the two-phase contraction (kernels_rows.cu layout).
-size_t row_chunk_smem(int nbuf, int nrow, int nadesc, int naent, int nslot, int nseg, int nch);
+size_t row_chunk_smem(int nrow1, int nrow2, int nslot, int nseg, int nch);
 
 // Set the text that nbs_last_error(NULL) returns on this thread.
 void set_global_error(const std::string& msg);

@@ -126,8 +126,8 @@ def channel_names():
 
 PX = dict(TYPES=0, TYPETERMS=1, TYPECOEF=2, CELLS=3, TERMS=4, ENT1_CELL=5, ENT1_COEF=6, ENT2_CELL=7,
           ENT2_COEF=8, CHANNELS=9, GROUPS=10, GROUPCH=11, ITEMS=12, CHUNKS=13, CHUNKTAB=14, CHUNKITEMS=15,
-          QUADCHUNKS=18, QUADSEGS=19, ROWCHUNKS=20, ROWAENT=21, ROWADESC=22, ROWREC=23, ROWCH=24, ROWSEGS=25,
-          ROWSCALES=26,
+          QUADCHUNKS=18, QUADSEGS=19, ROWCHUNKS=20, ROWENT=21, ROWDESC=22, ROWREC=23, ROWCH=24, ROWSEGS=25,
+          ROWSCALES=26, ROWTYPES=27,
           TERMTABOFF=16, CODES=17)
 
 
@@ -168,15 +168,16 @@ def plan_tables(channel_ids, flavours: int = 2):
 def row_tables(L, p, get):
     """The two-phase contraction's tables (None where they do not fit shared memory)."""
     import numpy as np
-    rs = (ctypes.c_longlong * 9)()
+    rs = (ctypes.c_longlong * 10)()
     _check(L.nbs_plan_row_sizes(p, rs))
-    ok, nck, naent, nadesc, nrec, nch, nseg, smem, warps = list(rs)
+    ok, nck, nent, nrows, nrec, nch, nseg, smem, warps, ntypes = list(rs)
     if not ok:
         return None
-    return dict(warps=warps, chunks=get("ROWCHUNKS", (nck, 96), np.int32), aent=get("ROWAENT", (max(naent, 1),), np.uint16),
-                adesc=get("ROWADESC", (max(nadesc, 1),), np.uint32), rec=get("ROWREC", (max(nrec, 1),), np.uint32),
+    return dict(warps=warps, chunks=get("ROWCHUNKS", (nck, 96), np.int32), ent=get("ROWENT", (max(nent, 1),), np.uint16),
+                desc=get("ROWDESC", (max(nrows, 1),), np.uint32), rec=get("ROWREC", (max(nrec, 1),), np.uint32),
                 ch=get("ROWCH", (max(nch, 1),), np.int32), segs=get("ROWSEGS", (max(nseg, 1), 4), np.int32),
-                scales=get("ROWSCALES", (32,), np.float64), smem=smem)
+                scales=get("ROWSCALES", (32,), np.float64), types=get("ROWTYPES", (max(ntypes, 1), 8), np.int32),
+                smem=smem)
 
 
 # ---- torch-backed device allocator -------------------------------------------
@@ -359,14 +360,14 @@ class Context:
     def set_param(self, param: int, value: int):
         _check(self._lib.nbs_set_param(self.h, param, value), self.h)
 
-    STAGES = ("rescale", "blocks", "fft_fwd", "contract", "fft_inv", "restore_copy")
+    STAGES = ("rescale", "blocks", "fft_fwd", "contract", "fft_inv", "restore_copy", "eff_rows")
 
     def set_profiling(self, on: bool = True):
         _check(self._lib.nbs_set_profiling(self.h, int(on)), self.h)
 
     def profile(self):
         """(dict stage -> accumulated device ms, number of kernel launches)."""
-        ms = (ctypes.c_double * 6)()
+        ms = (ctypes.c_double * 7)()
         n = ctypes.c_longlong()
         _check(self._lib.nbs_profile(self.h, ms, ctypes.byref(n)), self.h)
         return dict(zip(self.STAGES, list(ms))), n.value

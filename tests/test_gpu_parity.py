@@ -470,10 +470,11 @@ def test_24cube_sampled_r(nbs):
 
 def test_slab_wait_timeout_is_reported_and_recoverable(nbs):
     """The failure path of the contraction's bounded slab wait, without a device fault: the test switch
-    NBS_PARAM_TEST_SKIP_SLAB makes the FP32 row kernel arm each block's first slab wait and issue no copy,
-    so nothing is in flight when the wait runs out (about a second).  nbs_correlate returns NBS_ETIMEOUT, a
-    waited replay of a graph captured with the switch on returns NBS_ETIMEOUT, and with the switch off the
-    same context gives the oracle's correlators again."""
+    NBS_PARAM_TEST_SKIP_SLAB makes the TMA-staged FP32 quad-lane kernel (contraction config 4) arm each
+    block's first slab wait and issue no copy, so nothing is in flight when the wait runs out (about a
+    second).  nbs_correlate returns NBS_ETIMEOUT, a waited replay of a graph captured with the switch on
+    returns NBS_ETIMEOUT, and with the switch off the same context gives the oracle's correlators again,
+    through that kernel and through the default one."""
     L = 8
     props = seeded(1771, L, 1, decay=0.5)
     names = nbs.channel_names()
@@ -481,6 +482,7 @@ def test_slab_wait_timeout_is_reported_and_recoverable(nbs):
     with nbs.Context(L, 1, precision=nbs.NBS_FP32) as ctx:
         ctx.load_props(torch.from_numpy(props[0][0]).cuda(), torch.from_numpy(props[0][1]).cuda(), 0)
         out = torch.empty((len(ids), 1, 4, 4, 2, 2, L ** 3), dtype=torch.complex128, device="cuda")
+        ctx.set_param(0, 4)             # NBS_PARAM_CONTRACT_CFG: the quad-lane kernel
         ctx.correlate(ids, 0, 1, out)   # allocates every buffer before the capture below
         ctx.set_param(3, 1)             # NBS_PARAM_TEST_SKIP_SLAB
         with pytest.raises(nbs.NBSError) as ei:
@@ -495,8 +497,14 @@ def test_slab_wait_timeout_is_reported_and_recoverable(nbs):
         ctx.correlate(ids, 0, 1, out)
         torch.cuda.synchronize()
         F = out.cpu().numpy()
+        ctx.set_param(0, 0)
+        ctx.correlate(ids, 0, 1, out)
+        torch.cuda.synchronize()
+        F0 = out.cpu().numpy()
     for k, c in enumerate(ids):
-        assert rel(F[k, 0], oracle(names[c], *props[0], L)) < FP32_TOL, names[c]
+        want = oracle(names[c], *props[0], L)
+        assert rel(F[k, 0], want) < FP32_TOL, names[c]
+        assert rel(F0[k, 0], want) < FP32_TOL, names[c]
 
 
 def test_batched_graph_replay_uneven_sizes_against_the_oracle(nbs):

@@ -442,20 +442,21 @@ def test_quad_runs_reproduce_the_term_products(lib, ids):
 
 @pytest.mark.parametrize("ids", [list(range(52)), [0], [24, 25, 51], list(range(0, 208, 5)), list(range(208))])
 def test_row_tables_reproduce_the_term_products(lib, ids):
-    """The two-phase contraction's tables, executed in FP64 on random slab values (one momentum) the way the
-    kernel does: phase A builds every listed row of a chunk (sum of +-1 / +-2 times slab cells, B2's cells
-    from 944 on), phase B walks each warp's segments, lane (kq, s) of step st takes record (8 st + kq, s):
-    scale times the outer product of its B1 row and B2 row into output pair s.  Every channel equals the plain
-    sum over its terms of E1 E2 built from the uncompressed gather lists; every step is walked by exactly one
-    warp, inside one channel, and each warp's channels fit its slots."""
+    """The two-phase contraction's tables, executed in FP64 on random stored blocks (one momentum q and its
+    mirror -q) the way the kernels do: phase A builds every row of every stored type at both momenta (sum of
+    +-1 / +-2 times the type's cells), phase B walks each chunk's warp segments, lane (kq, s) of step st
+    takes record (8 st + kq, s): scale times the outer product of its B1 row (of type1, at q) and B2 row
+    (of type2, at -q) into output pair s.  Every channel equals the plain sum over its terms of E1 E2 built
+    from the uncompressed gather lists; every step is walked by exactly one warp, inside one channel, and
+    each warp's channels fit its slots."""
     tb = nbs.plan_tables(ids)
     rt = tb["rows"]
     assert rt is not None
     T = tb["terms"]
     rng = np.random.default_rng(8)
     ncells = int(tb["cells"].shape[0])
-    A = rng.standard_normal((ncells, 4)) + 1j * rng.standard_normal((ncells, 4))  # B1's blocks at q
-    B = rng.standard_normal((ncells, 4)) + 1j * rng.standard_normal((ncells, 4))  # B2's blocks at -q
+    A = rng.standard_normal((ncells, 4)) + 1j * rng.standard_normal((ncells, 4))  # stored blocks at q
+    B = rng.standard_normal((ncells, 4)) + 1j * rng.standard_normal((ncells, 4))  # at -q
     nch = len(ids)
     want = np.zeros((nch, 4, 4, 4), complex)
     for t in range(len(T)):
@@ -471,31 +472,38 @@ def test_row_tables_reproduce_the_term_products(lib, ids):
             for h2 in range(nh2):
                 want[ch, :, :, _s_index(shape, h1, h2)] += np.einsum("ka,kb->ab", E1[:, h1], E2[:, h2])
     coef = np.array([1.0, -1.0, 2.0, -2.0])
+    # phase A: the rows of every type, at q (from A) and at -q (from B); padding rows stay NaN (no record
+    # may name them)
+    types = rt["types"]
+    NR = len(rt["desc"])
+    Rq = np.full((NR, 4), np.nan, complex)
+    Rm = np.full((NR, 4), np.nan, complex)
+    roff = 0
+    for t, (base, ncell, tr, nrow) in enumerate(types[:, :4].astype(int)):
+        assert tr == roff and tr % 8 == 0 and nrow % 8 == 0 and nrow <= 4095
+        roff += nrow
+        for r in range(tr, tr + nrow):
+            d = int(rt["desc"][r])
+            off, cnt, ty = d & 0xFFFFFF, (d >> 24) & 31, d >> 29
+            assert ty == t
+            if cnt == 0:
+                continue
+            e = rt["ent"][off:off + cnt].astype(np.int64)
+            cell = e & 0xFFF
+            assert np.all(cell < ncell) and np.all(np.diff(cell) > 0)
+            c = coef[(e >> 12) & 3][:, None]
+            Rq[r] = (c * A[base + cell]).sum(axis=0)
+            Rm[r] = (c * B[base + cell]).sum(axis=0)
+    assert roff == NR
     got = np.zeros_like(want)
     assert np.count_nonzero(rt["scales"][:31]) <= 31 and rt["scales"][31] == 0
+    W = rt["warps"]
     for ck in rt["chunks"]:
-        base1, ncell1, base2, ncell2, nrow1, nrow2, aent_off, naent, adesc_off, nadesc, rec_off, nstep, ch_off, \
-            nch_c, nslot, seg_off, smem, nbuf = (int(x) for x in ck[:18])
-        W = rt["warps"]
-        seg_base, out_base, cfirst = ck[18:19 + W], ck[19 + W:20 + 2 * W], ck[20 + 2 * W:20 + 3 * W]
-        assert nbuf in (1, 2)
-        assert smem <= rt["smem"] <= 232448 and nrow1 % 8 == 0 and nrow2 % 8 == 0 and max(nrow1, nrow2) <= 4095
-        # planar slab units: side s, cell c -> 16-byte unit of sink spins 0, 1 (spins 2, 3 236 units on)
-        unit = lambda side, c: side * 1888 + (c // 236) * 472 + c % 236
-        slab = np.full((4096, 4), np.nan, complex)
-        c1, c2 = np.arange(ncell1), np.arange(ncell2)
-        slab[unit(0, c1)] = A[base1 + c1]
-        slab[unit(1, c2)] = B[base2 + c2]
-        E = np.full((nrow1 + nrow2, 4), np.nan, complex)   # row slots no descriptor writes stay NaN
-        for d in rt["adesc"][adesc_off:adesc_off + nadesc].astype(np.int64):
-            off, cnt, r = d & 0x3FFF, (d >> 14) & 31, d >> 19
-            e = rt["aent"][aent_off + off: aent_off + off + cnt].astype(np.int64)
-            side_of = (e & 0xFFF) >= 1888
-            assert np.all(side_of == (r >= nrow1))     # B1's rows read side 1, B2's side 2
-            assert np.isnan(E[r]).all()   # each row slot written once
-            v = slab[e & 0xFFF]
-            assert np.isfinite(v).all()   # every unit names a staged cell
-            E[r] = (coef[(e >> 12) & 3][:, None] * v).sum(axis=0)
+        t1, t2, roff1, nrow1, roff2, nrow2, rec_off, nstep, ch_off, nch_c, nslot, seg_off, smem = \
+            (int(x) for x in ck[:13])
+        seg_base, out_base, cfirst = ck[14:15 + W], ck[15 + W:16 + 2 * W], ck[16 + 2 * W:16 + 3 * W]
+        assert (roff1, nrow1, roff2, nrow2) == (types[t1, 2], types[t1, 3], types[t2, 2], types[t2, 3])
+        assert smem <= rt["smem"] <= 232448
         rec = rt["rec"][rec_off: rec_off + 32 * nstep].astype(np.int64).reshape(nstep, 8, 4)
         seen = np.zeros(nstep, int)
         for w in range(W):
@@ -512,39 +520,30 @@ def test_row_tables_reproduce_the_term_products(lib, ids):
                             if code == 31:
                                 continue
                             assert r1 < nrow1 and r2 < nrow2
-                            got[ch, :, :, s] += rt["scales"][code] * np.outer(E[r1], E[nrow1 + r2])
+                            x, y = Rq[roff1 + r1], Rm[roff2 + r2]
+                            assert np.isfinite(x).all() and np.isfinite(y).all()
+                            got[ch, :, :, s] += rt["scales"][code] * np.outer(x, y)
         assert np.all(seen == 1)
     assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
 
 
 def test_row_loads_spread_over_the_banks_warp_wide(lib):
-    """Shared-memory wavefronts of the two-phase kernel's 16-byte loads, warp-wide (a load takes as many
-    wavefronts as its fullest 16-byte bank group has distinct addresses; ideal ceil(distinct / 8)): phase B's
-    row loads (rows numbered by colouring each warp step's rows over the groups) within 1.25x of ideal,
-    phase A's slab loads (rows batched 32 per warp instruction to spread the j-th entries' slab units)
-    within 1.7x, for the 52-channel tables.  Rows numbered in first-use order give about 1.6x and 2.2x."""
+    """Shared-memory wavefronts of the product kernel's 16-byte row loads, warp-wide (a load takes as many
+    wavefronts as its fullest 16-byte bank group has distinct addresses; ideal ceil(distinct / 8)): each
+    stored type's rows are numbered by colouring, over every chunk that reads the type, the rows one warp
+    step loads (B1's and B2's) over the groups; the loads stay within 1.3x of ideal for the 52-channel
+    tables (rows numbered in first-use order give about 1.6x)."""
     rt = nbs.plan_tables(list(range(52)))["rows"]
-    for phase in ("A", "B"):
-        act = ideal = 0
-        for ck in rt["chunks"]:
-            nrow1, adesc_off, nadesc, aent_off, rec_off, nstep = (int(ck[i]) for i in (4, 8, 9, 6, 10, 11))
-            if phase == "B":
-                rec = rt["rec"][rec_off: rec_off + 32 * nstep].astype(np.int64).reshape(nstep, 32)
-                groups = []
-                for w in rec:
-                    w = w[(w >> 24) != 31]
-                    groups += [w & 0xFFF, nrow1 + ((w >> 12) & 0xFFF)]
-            else:
-                d = rt["adesc"][adesc_off: adesc_off + nadesc].astype(np.int64)
-                groups = []
-                for w0 in range(0, nadesc, 32):
-                    dd = d[w0:w0 + 32]
-                    for j in range(int(((dd >> 14) & 31).max())):
-                        live = dd[((dd >> 14) & 31) > j]
-                        groups.append(rt["aent"][aent_off + (live & 0x3FFF) + j].astype(np.int64) & 0xFFF)
-            for g in groups:
+    act = ideal = 0
+    for ck in rt["chunks"]:
+        rec_off, nstep = int(ck[6]), int(ck[7])
+        rec = rt["rec"][rec_off: rec_off + 32 * nstep].astype(np.int64).reshape(nstep, 32)
+        for w in rec:
+            w = w[(w >> 24) != 31]
+            for g in (w & 0xFFF, (w >> 12) & 0xFFF):
                 u = np.unique(g)
                 if len(u):
                     act += np.bincount(u % 8).max()
                     ideal += -(-len(u) // 8)
-        assert act / ideal <= {"A": 1.7, "B": 1.25}[phase], (phase, act / ideal)
+    assert act / ideal <= 1.3, act / ideal
+
