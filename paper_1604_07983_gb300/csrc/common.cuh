@@ -147,8 +147,8 @@ inline MomGeom full_geom(int L) {
 }
 // phase A of the FP32 contraction: the rows of every stored type at every momentum (RQ: 2 NR 16-byte units
 // per momentum); types, desc, ent: Plan::row_types, row_desc, row_ent in device memory
-cudaError_t launch_eff_rows(const float2* FB, long long V, const void* types, const unsigned* desc,
-                            const unsigned short* ent, int NR, float2* RQ, int nsm, cudaStream_t st);
+cudaError_t launch_eff_rows(const float2* FB, long long V, const void* types, int ntypes, const unsigned* desc,
+                            const unsigned short* ent, int nent, int NR, float2* RQ, int nsm, cudaStream_t st);
 // phase B; qlist: the momenta in visiting order as (q, -q) pairs (momentum_order), device memory
 cudaError_t launch_contract_rows(const float2* RQ, const MomGeom& geom, int NR, const int2* qlist, int nchunks, int qb,
                                  const void* chunks, const unsigned* rec, const void* segs, const int* row_ch,

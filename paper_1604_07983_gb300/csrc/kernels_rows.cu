@@ -168,43 +168,102 @@ __device__ __forceinline__ bool mb_wait(unsigned a, unsigned parity, volatile in
 
 // Phase A: every row of every type at momenta [0, V).  A warp item is (four consecutive momenta, eight
 // consecutive rows of one type): lane = 8 (momentum offset) + (row offset).  Row r (global, of type t)
-// at momentum q: unit q 2 NR + roff_t + r holds sink spins 0, 1, that unit + nrow_t spins 2, 3.
-__global__ void __launch_bounds__(256) k_eff_rows(const float4* __restrict__ FB, long long V,
-                                                  const RowTypeHdr* __restrict__ types,
-                                                  const unsigned* __restrict__ desc,
-                                                  const unsigned short* __restrict__ ent, int NR,
-                                                  float4* __restrict__ RQ) {
+// at momentum q: unit q 2 NR + roff_t + r holds sink spins 0, 1, that unit + nrow_t spins 2, 3.  The row
+// tables sit in shared memory; a warp takes two items at a time and issues the loads of their first two
+// entries (nearly every row has one or two) before it uses any, so that four 32-byte loads per lane are in
+// flight.
+constexpr int EFF_THREADS = 256;
+
+struct EffItem {
+  long long q;
+  int r, cnt, off, base, roff, nrow;
+};
+
+__global__ void __launch_bounds__(EFF_THREADS) k_eff_rows(const float4* __restrict__ FB, long long V,
+                                                          const RowTypeHdr* __restrict__ types, int ntypes,
+                                                          const unsigned* __restrict__ desc,
+                                                          const unsigned short* __restrict__ ent, int nent, int NR,
+                                                          float4* __restrict__ RQ) {
+  extern __shared__ __align__(16) unsigned char eff_smem[];
+  int* const TY = reinterpret_cast<int*>(eff_smem);                  // [ntypes][3]: base, roff, nrow
+  unsigned* const DS = reinterpret_cast<unsigned*>(eff_smem + 128);  // [NR]
+  unsigned short* const ES = reinterpret_cast<unsigned short*>(DS + NR);  // [nent]
+  for (int i = threadIdx.x; i < ntypes; i += blockDim.x) {
+    TY[3 * i] = types[i].base;
+    TY[3 * i + 1] = types[i].roff;
+    TY[3 * i + 2] = types[i].nrow;
+  }
+  for (int i = threadIdx.x; i < NR; i += blockDim.x) DS[i] = desc[i];
+  for (int i = threadIdx.x; i < nent; i += blockDim.x) ES[i] = ent[i];
+  __syncthreads();
+
   const int lane = threadIdx.x & 31, noct = NR / 8;
   const long long nitems = (V + 3) / 4 * noct;
-  const long long stride = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long it = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += stride) {
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  auto item = [&](long long it, EffItem& m) {
     const long long qq = it / noct;
-    const int r = 8 * (int)(it - qq * noct) + (lane & 7);
-    const long long q = 4 * qq + (lane >> 3);
-    const unsigned d = __ldg(desc + r);
-    const int cnt = (int)((d >> 24) & 31u), t = (int)(d >> 29);
-    const unsigned short* e = ent + (d & 0xFFFFFFu);
-    const int base = __ldg(&types[t].base), roff = __ldg(&types[t].roff), nrow = __ldg(&types[t].nrow);
-    if (q >= V) continue;
-    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-    for (int j = 0; j < cnt; ++j) {
-      const unsigned x = __ldg(e + j);
-      float c = (x & 0x2000u) ? 2.f : 1.f;
-      c = (x & 0x1000u) ? -c : c;
-      const float4* src = FB + ((long long)(base + (int)(x & 0xFFFu)) * V + q) * 2;
-      const float4 v0 = __ldg(src), v1 = __ldg(src + 1);
-      a0.x = fmaf(c, v0.x, a0.x);
-      a0.y = fmaf(c, v0.y, a0.y);
-      a0.z = fmaf(c, v0.z, a0.z);
-      a0.w = fmaf(c, v0.w, a0.w);
-      a1.x = fmaf(c, v1.x, a1.x);
-      a1.y = fmaf(c, v1.y, a1.y);
-      a1.z = fmaf(c, v1.z, a1.z);
-      a1.w = fmaf(c, v1.w, a1.w);
+    m.r = 8 * (int)(it - qq * noct) + (lane & 7);
+    m.q = 4 * qq + (lane >> 3);
+    const unsigned d = DS[m.r];
+    const int t = (int)(d >> 29);
+    m.cnt = (it < nitems && m.q < V) ? (int)((d >> 24) & 31u) : -1;  // -1: nothing to store
+    m.off = (int)(d & 0xFFFFFFu);
+    m.base = TY[3 * t];
+    m.roff = TY[3 * t + 1];
+    m.nrow = TY[3 * t + 2];
+  };
+  auto coef = [](unsigned x) {
+    const float c = (x & 0x2000u) ? 2.f : 1.f;
+    return (x & 0x1000u) ? -c : c;
+  };
+  auto src = [&](const EffItem& m, unsigned x) { return FB + ((long long)(m.base + (int)(x & 0xFFFu)) * V + m.q) * 2; };
+  auto fma4 = [](float4& a, float c, const float4& v) {
+    a.x = fmaf(c, v.x, a.x);
+    a.y = fmaf(c, v.y, a.y);
+    a.z = fmaf(c, v.z, a.z);
+    a.w = fmaf(c, v.w, a.w);
+  };
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long it = 2 * (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); it < nitems; it += 2 * nwarps) {
+    EffItem m[2];
+    item(it, m[0]);
+    item(it + 1, m[1]);
+    unsigned x[2][2];
+    float4 v[2][2][2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        x[k][j] = m[k].cnt > j ? (unsigned)ES[m[k].off + j] : 0u;
+        if (m[k].cnt > j) {
+          const float4* p = src(m[k], x[k][j]);
+          v[k][j][0] = __ldg(p);
+          v[k][j][1] = __ldg(p + 1);
+        } else {
+          v[k][j][0] = v[k][j][1] = z4;
+        }
+      }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (m[k].cnt < 0) continue;
+      float4 a0 = z4, a1 = z4;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const float c = m[k].cnt > j ? coef(x[k][j]) : 0.f;
+        fma4(a0, c, v[k][j][0]);
+        fma4(a1, c, v[k][j][1]);
+      }
+      for (int j = 2; j < m[k].cnt; ++j) {
+        const unsigned xj = ES[m[k].off + j];
+        const float4* p = src(m[k], xj);
+        const float c = coef(xj);
+        fma4(a0, c, __ldg(p));
+        fma4(a1, c, __ldg(p + 1));
+      }
+      float4* dst = RQ + m[k].q * 2 * NR + m[k].roff + m[k].r;
+      dst[0] = a0;
+      dst[m[k].nrow] = a1;
     }
-    float4* dst = RQ + q * 2 * NR + roff + r;
-    dst[0] = a0;
-    dst[nrow] = a1;
   }
 }
 
@@ -416,15 +475,21 @@ size_t row_chunk_smem(int nrow1, int nrow2, int nslot, int nseg, int nch) {
   return 128 + row_layout(nrow1, nrow2, nslot, nseg, nch).total;
 }
 
-cudaError_t launch_eff_rows(const float2* FB, long long V, const void* types, const unsigned* desc,
-                            const unsigned short* ent, int NR, float2* RQ, int nsm, cudaStream_t st) {
-  if (!FB || !RQ || V <= 0 || NR <= 0 || NR % 8 || (reinterpret_cast<uintptr_t>(FB) & 15) ||
-      (reinterpret_cast<uintptr_t>(RQ) & 15))
+cudaError_t launch_eff_rows(const float2* FB, long long V, const void* types, int ntypes, const unsigned* desc,
+                            const unsigned short* ent, int nent, int NR, float2* RQ, int nsm, cudaStream_t st) {
+  if (!FB || !RQ || V <= 0 || NR <= 0 || NR % 8 || ntypes < 1 || ntypes > 8 || nent < 0 ||
+      (reinterpret_cast<uintptr_t>(FB) & 15) || (reinterpret_cast<uintptr_t>(RQ) & 15))
     return cudaErrorInvalidValue;
+  const size_t smem = 128 + 4 * (size_t)NR + 2 * (size_t)nent;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_eff_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   const long long items = (V + 3) / 4 * (NR / 8);
-  const long long blocks = std::min<long long>((items + 7) / 8, (long long)std::max(nsm, 1) * 8);
-  k_eff_rows<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<const float4*>(FB), V, (const RowTypeHdr*)types, desc,
-                                               ent, NR, reinterpret_cast<float4*>(RQ));
+  const long long blocks = std::min<long long>((items + 15) / 16, (long long)std::max(nsm, 1) * 4);
+  k_eff_rows<<<(unsigned)blocks, EFF_THREADS, smem, st>>>(reinterpret_cast<const float4*>(FB), V,
+                                                           (const RowTypeHdr*)types, ntypes, desc, ent, nent, NR,
+                                                           reinterpret_cast<float4*>(RQ));
   return cudaGetLastError();
 }
 

@@ -454,8 +454,9 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
     const bool use_qseg = f32_chunks && quad_fits && (h->contract_cfg == 4 || (h->contract_cfg == 0 && !rows_fit));
     if (use_rows) {
       cudaEvent_t e6 = stage_begin(h);
-      CK(launch_eff_rows((const float2*)h->FB.p, V, h->d_rtypes.p, (const unsigned*)h->d_rdesc.p,
-                         (const unsigned short*)h->d_rent.p, h->plan.row_nr, (float2*)h->RQ.p, h->nsm, h->st),
+      CK(launch_eff_rows((const float2*)h->FB.p, V, h->d_rtypes.p, (int)h->plan.row_types.size(),
+                         (const unsigned*)h->d_rdesc.p, (const unsigned short*)h->d_rent.p,
+                         (int)h->plan.row_ent.size(), h->plan.row_nr, (float2*)h->RQ.p, h->nsm, h->st),
          "effective-block rows");
       stage_end(h, 6, e6);
       CK(launch_contract_rows((const float2*)h->RQ.p, full_geom(h->L), h->plan.row_nr, (const int2*)h->d_qlist.p,
@@ -1211,8 +1212,9 @@ int nbs_slab_contract(nbs_ctx* h, const void* recv, void* send) {
   CK(fft_lines<float>(fbm, nc * ny * 4LL * L, 4 * L * ny, 4LL * L * ny * L, 4LL * L * ny, L, -1, h->fft_block, h->st),
      "z pass");
   CK(cudaMemsetAsync(h->flags, 0, sizeof(int), h->st), "clear flags");
-  CK(launch_eff_rows(fbm, h->svm, h->d_rtypes.p, (const unsigned*)h->d_rdesc.p, (const unsigned short*)h->d_rent.p,
-                     P.row_nr, (float2*)h->RQ.p, h->nsm, h->st),
+  CK(launch_eff_rows(fbm, h->svm, h->d_rtypes.p, (int)P.row_types.size(), (const unsigned*)h->d_rdesc.p,
+                     (const unsigned short*)h->d_rent.p, (int)P.row_ent.size(), P.row_nr, (float2*)h->RQ.p, h->nsm,
+                     h->st),
      "effective-block rows on the momentum set");
   CK(launch_contract_rows((const float2*)h->RQ.p, h->smg, P.row_nr, (const int2*)h->d_qlist.p,
                           (int)P.row_chunks.size(), h->chunk_qb, h->d_rchunks.p, (const unsigned*)h->d_rrec.p,
