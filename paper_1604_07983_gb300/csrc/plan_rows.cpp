@@ -404,6 +404,12 @@ void build_row_chunks(Plan& plan, int smem_limit) {
     }
   }
 
+  // largest chunks first: the product kernel's blocks run chunk by chunk in this order, so the launch ends
+  // on the shortest blocks
+  std::stable_sort(cbs.begin(), cbs.end(), [](const ChunkBuild& a, const ChunkBuild& b) {
+    return a.step_ch.size() > b.step_ch.size();
+  });
+
   // ---- row numbers per type: bank colouring over every chunk that reads the type ----
   std::vector<std::vector<int>> idx(ntypes);
   int roff = 0;
