@@ -33,9 +33,11 @@
 // again (after letting its copies in flight land) and the call reports the
 // timeout.
 //
-// The blocks run chunk by chunk, the chunks largest first (plan order), so the
-// launch ends on the shortest blocks.  Within a block the momenta are visited
-// in the order of a list that places -q right after q (as (q, -q) pairs).
+// The blocks run momentum block by momentum block, so the chunks of a momentum
+// block share its rows in L2, and within one the chunks come largest first
+// (plan order), so the launch ends on the shortest blocks.  Within a block the
+// momenta are visited in the order of a list that places -q right after q (as
+// (q, -q) pairs): the rows read at -q are the ones other chunks read at q.
 #include <vector>
 
 #include "common.cuh"
@@ -277,8 +279,9 @@ __global__ void __launch_bounds__((NBS_ROW_WARPS + NBS_ROW_HELPERS) * 32, 1) k_c
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const unsigned pad = (128u - (smem_u32(smem_raw) & 127u)) & 127u;
   unsigned char* const sb = smem_raw + pad;
-  const int nqb = (int)((V + qb - 1) / qb);  // blocks chunk-major: the chunks come largest first
-  const RowChunkHdr& ck = chunks[blockIdx.x / nqb];
+  // blocks momentum-block-major (the chunks of a momentum block share its rows in L2), the chunks of a
+  // block largest first (plan order), so the launch ends on the shortest blocks
+  const RowChunkHdr& ck = chunks[blockIdx.x % nchunks];
   const int nrow1 = ck.nrow1, nrow2 = ck.nrow2, nslot = ck.nslot, nch = ck.nch;
   const int nseg = ck.seg_base[NBS_ROW_WARPS];
   const RowLayout lay = row_layout(nrow1, nrow2, nslot, nseg, nch);
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__((NBS_ROW_WARPS + NBS_ROW_HELPERS) * 32, 1) k_c
   const unsigned MBF = smem_u32(sb + lay.mb), MBE = MBF + 8u * S;
   volatile int* const ABORT = reinterpret_cast<volatile int*>(sb + lay.mb + 16 * S);
 
-  const long long i0 = (long long)(blockIdx.x % nqb) * qb;  // this block: qlist[i0 .. i0 + n)
+  const long long i0 = (long long)(blockIdx.x / nchunks) * qb;  // this block: qlist[i0 .. i0 + n)
   const int n = (int)(min(V, i0 + qb) - i0);
   const int2* const QL = qlist + i0;
 

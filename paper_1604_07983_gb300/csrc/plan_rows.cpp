@@ -404,8 +404,8 @@ void build_row_chunks(Plan& plan, int smem_limit) {
     }
   }
 
-  // largest chunks first: the product kernel's blocks run chunk by chunk in this order, so the launch ends
-  // on the shortest blocks
+  // largest chunks first: within each momentum block the product kernel's blocks start in this order, so
+  // the launch ends on the shortest blocks
   std::stable_sort(cbs.begin(), cbs.end(), [](const ChunkBuild& a, const ChunkBuild& b) {
     return a.step_ch.size() > b.step_ch.size();
   });
