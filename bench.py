@@ -37,7 +37,8 @@ FP32_LANES, SM_MAX_MHZ = 128, 2070.0   # FP32 lanes per SM; the clock used when 
 # `python bench.py --L 16 --T 2 --steps 1 --warmup 1 --e2e-steps 1 --no-cpu-baseline`
 # (dram__bytes_read.sum + dram__bytes_write.sum over 4096 momenta); an entry is dropped
 # whenever its kernel changes, until it is captured again
-DRAM_BYTES_PER_Q = {"k_contract_qseg": 1.255847e9 / 4096}
+DRAM_BYTES_PER_Q = {"k_contract_qseg": 1.255847e9 / 4096, "k_contract_rows": 0.687230e9 / 4096,
+                    "k_eff_rows": 1.168500e9 / 4096}
 
 
 def parse():
@@ -475,8 +476,11 @@ def run_ours(args, rank, world, local_rank):
         nbytes = V * (len(tb["cells"]) * 32.0 + nr * 32.0)
         hbm = peaks.get("hbm_gbs", 6800.0)
         ach = nbytes / (rows_ms / 1e3) / 1e9
+        traffic = DRAM_BYTES_PER_Q.get("k_eff_rows", 0) * V or None
         roof_rows = {"kernel": "k_eff_rows", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                     "frac": ach / hbm, "ms": rows_ms,
+                     "frac": ach / hbm, "ms": rows_ms, "traffic": traffic,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at 16^3, "
+                                       "scaled by V" if traffic else None,
                      "work_per_launch": "%d stored cells + %d rows x 32 bytes x V" % (len(tb["cells"]), nr),
                      "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     line = {
