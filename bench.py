@@ -425,8 +425,7 @@ def run_ours(args, rank, world, local_rank):
     if dominant == "contract" and prec == P.NBS_BF16X3:
         peak = peaks.get("bf16_tflops", 1900.0)
         ach = 3 * flops_per_launch / (per_launch_ms["contract"] / 1e3) / 1e12
-        tc_cfg = tuned["cfg"] if tuned else args.contract_cfg
-        roof = {"kernel": "k_contract_tc" if tc_cfg == 2 else "k_contract_tcq", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+        roof = {"kernel": "k_contract_tcq", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None,
                 "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)" if "bf16_tflops" in peaks else "fallback",
                 "work_per_launch": "3 bf16 products x 8 flop x 64 x sum|xi~| (=%d) x V complex MACs of Eq. (4.3)"
@@ -442,9 +441,8 @@ def run_ours(args, rank, world, local_rank):
             peak_src = "nominal GB300 FP64 1.25 TFLOP/s"
         ach = flops_per_launch / (contract_ms / 1e3) / 1e12
         cfg = tuned["cfg"] if tuned else args.contract_cfg
-        kname = {0: "k_contract_rows", 4: "k_contract_qseg", 2: "k_contract_chunk", 3: "k_contract_chunk2",
-                 1: "k_contract_slab"}.get(cfg, "k_contract") if prec == P.NBS_FP32 else \
-            ("k_contract_slab" if cfg == 1 else "k_contract")
+        kname = {0: "k_contract_rows", 4: "k_contract_qseg"}.get(cfg, "k_contract") if prec == P.NBS_FP32 else \
+            "k_contract"
         traffic = None
         if kname in DRAM_BYTES_PER_Q and prec == P.NBS_FP32:
             traffic = DRAM_BYTES_PER_Q[kname] * V

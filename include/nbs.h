@@ -174,30 +174,23 @@ int nbs_zero_momentum(nbs_ctx* h, double* out);
 
 /* Launch-shape parameters (for tuning; results agree to rounding).
  * NBS_PARAM_CONTRACT_CFG selects the contraction kernel:
- *   0 = default: in FP32, when its tables fit shared memory, the two-phase
- *       row kernel (persistent blocks of 16 warps; per momentum every distinct
- *       effective-block row of a chunk of channels is built once for all four
- *       sink spins, Eq. (4.2), then each lane forms the 4 x 4 sink-spin outer
- *       products of one shared index and one source-spin pair, Eq. (4.3)),
- *       else config 4; in BF16X3 the quad-lane tensor-core form; in FP64 the
+ *   0 = default: in FP32, when its tables fit shared memory, the two-kernel
+ *       row contraction (every distinct effective-block row of every stored
+ *       type built once per momentum, Eq. (4.2), then per chunk of channels
+ *       the 4 x 4 sink-spin outer products of each shared index and
+ *       source-spin pair from bulk-copied rows, Eq. (4.3)), else config 4;
+ *       in BF16X3 the quad-lane tensor-core form; in FP64 the
  *       thread-per-momentum kernel (A = 2, W = 1);
- *   1 = the momentum-slab kernel (one block per momentum and channel group,
- *       stored blocks staged in shared memory);
- *   2 = the chunk kernel (FP32; persistent blocks that keep a chunk of
- *       channels' compressed gather tables in shared memory and sweep a block
- *       of momenta with double-buffered slabs; two lanes per shared index),
- *       else the default;
- *   3 = the chunk kernel's second form (FP32; same work split, cheaper inner
- *       loops: signed coefficient table, no divergence), else the default;
  *   4 = the quad-lane chunk kernel (FP32; persistent blocks of 16 warps,
  *       four lanes per shared index, one sink spin each, gathers straight
- *       from the staged slabs; each warp walks its share of the steps as runs
+ *       from TMA-staged slabs; each warp walks its share of the steps as runs
  *       of one table run), else the default;
  *   A*10 + W = the thread-per-momentum kernel with A sink spins alpha1 per
- *       thread (1, 2 or 4) and W warps per block (1, 2 or 4).
- * In NBS_BF16X3 mode the tensor-core kernels run: the quad-lane form
- * (fragments by movmatrix, no shared-memory staging) by default, the
- * two-lane form with shared-memory staging for config 2.
+ *       thread (1, 2 or 4) and W warps per block (1, 2 or 4); in FP32 also
+ *       the kernel where neither the row nor the quad-lane tables fit.
+ * In NBS_BF16X3 mode the quad-lane tensor-core kernel runs (fragments by
+ * movmatrix, no shared-memory staging); a channel set whose tables do not fit
+ * it is rejected with NBS_EINVAL.
  * NBS_EINVAL for any other value. */
 #define NBS_PARAM_CONTRACT_CFG 0
 /* NBS_PARAM_CHUNK_QBLOCK: momenta per block of the chunk contractions (default 32). */

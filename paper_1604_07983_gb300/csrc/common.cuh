@@ -84,29 +84,6 @@ cudaError_t fft3d_inverse(C<T>* data, long long nbatch, int L, cudaStream_t st, 
 template <typename T>
 cudaError_t launch_contract(const C<T>* FB, int L, const DevTerm* terms, const int* ch_tb, int nch,
                             const Ent<T>* e1, const Ent<T>* e2, C<T>* Ft, int cfg, cudaStream_t st);
-// momentum-slab contraction; groups points to GroupHdr[ngroups] (plan.h)
-template <typename T>
-cudaError_t launch_contract_slab(const C<T>* FB, int L, int ngroups, const void* groups, const int* group_ch,
-                                 const int* items, const DevTerm* terms, const Ent<T>* e1, const Ent<T>* e2, int st1,
-                                 int st2, int max_nch, C<T>* Ft, cudaStream_t st);
-template <typename T>
-size_t slab_smem_bytes(int st1, int st2, int max_nch);
-// persistent chunk contraction (FP32); chunks points to ChunkHdr[nchunks] (plan.h),
-// codes: device array of 32 floats (|coefficient| per code, code 31 = 0)
-size_t chunk_smem_bytes(int st1, int st2, int max_slot, int max_tab);
-cudaError_t launch_contract_chunk(const float2* FB, int L, int nchunks, int qb, const void* chunks, const int* group_ch,
-                                  const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
-                                  const float* codes, int st1, int st2, int max_slot, int max_tab, float2* Ft,
-                                  cudaStream_t st);
-// the same on the tensor cores, split-BF16 x 3 (kernels_tc.cu)
-size_t tc_smem_bytes(int st1, int st2, int max_slot, int max_tab);
-// second form of the chunk contraction (cheaper inner loops); max_row = the
-// largest gather row (n * held spins) of any term, at most 128
-size_t chunk2_smem_bytes(int st1, int st2, int max_slot, int max_tab);
-cudaError_t launch_contract_chunk2(const float2* FB, int L, int nchunks, int qb, const void* chunks,
-                                   const int* group_ch, const int* items, const DevTerm* terms, const int* tab_off,
-                                   const unsigned short* tab, const float* codes, int st1, int st2, int max_slot,
-                                   int max_tab, int max_row, float2* Ft, cudaStream_t st);
 // quad-lane chunk contraction (FP32): chunks points to QuadChunkHdr[nchunks],
 // segs to the per-warp runs QuadSeg[] (plan.h), max_segs = the most runs of one
 // chunk; max_cells = the largest stored type's cell count (<= 944)
@@ -123,14 +100,6 @@ cudaError_t launch_contract_tcq(const float2* FB, long long ncells, int L, int n
                                 const void* segs, int max_segs, const int* group_ch, const unsigned short* tab,
                                 const float* codes, int max_cells, int max_slot, int max_tab, int max_row, float2* Ft,
                                 int* flags, cudaStream_t st);
-cudaError_t launch_contract_tc(const float2* FB, int L, int nchunks, int qb, const void* chunks, const int* group_ch,
-                               const int* items, const DevTerm* terms, const int* tab_off, const unsigned short* tab,
-                               const float* codes, int st1, int st2, int max_slot, int max_tab, float2* Ft,
-                               cudaStream_t st);
-// two-phase contraction over distinct effective-block rows (kernels_rows.cu, FP32):
-// chunks points to RowChunkHdr[nchunks], segs to RowSeg[] (plan.h); scales: 32
-// floats; smem: the largest chunk's shared memory; skip_first (test switch):
-// arm the first slab wait without issuing its copy, so that it runs out
 // Momenta of a contraction launch: q = x + L (y + Ly z), x and z over [0, L), y over Ly values of a set
 // that contains -y (mod L) with every y; the index of -y is ymir[y].  The full cube: Ly = L,
 // ymir[y] = (L - y) mod L.

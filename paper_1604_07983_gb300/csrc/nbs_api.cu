@@ -85,10 +85,9 @@ struct nbs_ctx {
   std::vector<int> plan_ids;
   Plan plan;
   int plan_gen = 0;
-  DevBuf d_terms, d_chtb, d_chnl, d_e1, d_e2, d_cells, d_groups, d_gch, d_items;
-  int slab_st1 = 0, slab_st2 = 0, slab_nch = 0;
-  DevBuf d_chunks, d_qchunks, d_qsegs, d_ctab, d_citems, d_ctoff, d_codes;
-  int chunk_st1 = 0, chunk_st2 = 0, chunk_slot = 0, chunk_tab = 0, chunk_row = 0, quad_slot = 0;
+  DevBuf d_terms, d_chtb, d_chnl, d_e1, d_e2, d_cells, d_gch;
+  DevBuf d_qchunks, d_qsegs, d_ctab, d_codes;
+  int chunk_st1 = 0, chunk_st2 = 0, chunk_tab = 0, chunk_row = 0, quad_slot = 0;
   int chunk_qb = 32;
   DevBuf d_rchunks, d_rtypes, d_rdesc, d_rent, d_rrec, d_rsegs, d_rch, d_rscales;  // two-phase contraction tables
   DevBuf d_qlist;  // momenta in the product kernel's visiting order
@@ -209,21 +208,12 @@ int upload_tables(nbs_ctx* h) {
     const TermHdr& t = P.terms[i];
     terms[i] = {t.ch, t.K, t.shape, t.n1, t.n2, t.off1, t.off2, t.pad};
   }
-  h->slab_st1 = h->slab_st2 = h->slab_nch = 0;
-  for (const GroupHdr& g : P.groups) {
-    h->slab_st1 = std::max(h->slab_st1, g.ncell1);
-    h->slab_st2 = std::max(h->slab_st2, g.ncell2);
-    h->slab_nch = std::max(h->slab_nch, g.nslot);
-  }
-  if ((rc = ensure(h, h->d_groups, std::max<size_t>(P.groups.size(), 1) * sizeof(GroupHdr), "groups"))) return rc;
   if ((rc = ensure(h, h->d_gch, std::max<size_t>(P.group_ch.size(), 1) * sizeof(int), "group channels"))) return rc;
-  if ((rc = ensure(h, h->d_items, std::max<size_t>(P.items.size(), 1) * sizeof(int), "work items"))) return rc;
   if (P.chunks_ok) {
-    h->chunk_st1 = h->chunk_st2 = h->chunk_slot = h->chunk_tab = 0;
+    h->chunk_st1 = h->chunk_st2 = h->chunk_tab = 0;
     for (const ChunkHdr& c : P.chunks) {
       h->chunk_st1 = std::max(h->chunk_st1, c.ncell1);
       h->chunk_st2 = std::max(h->chunk_st2, c.ncell2);
-      h->chunk_slot = std::max(h->chunk_slot, c.nslot);
       h->chunk_tab = std::max(h->chunk_tab, c.tab_len);
     }
     h->quad_slot = 0;
@@ -235,16 +225,12 @@ int upload_tables(nbs_ctx* h) {
     }
     float codes[32] = {};
     for (size_t i = 0; i < P.coef_codes.size() && i < 31; ++i) codes[i] = (float)P.coef_codes[i];
-    if ((rc = ensure(h, h->d_chunks, std::max<size_t>(P.chunks.size(), 1) * sizeof(ChunkHdr), "chunks"))) return rc;
     if ((rc = ensure(h, h->d_qchunks, std::max<size_t>(P.quad_chunks.size(), 1) * sizeof(QuadChunkHdr), "quad chunks")))
       return rc;
     if ((rc = ensure(h, h->d_qsegs, std::max<size_t>(P.quad_segs.size(), 1) * sizeof(QuadSeg), "quad segments")))
       return rc;
     if ((rc = ensure(h, h->d_ctab, std::max<size_t>(P.chunk_tab.size(), 8) * 2, "chunk tables"))) return rc;
-    if ((rc = ensure(h, h->d_citems, std::max<size_t>(P.chunk_items.size(), 1) * sizeof(int), "chunk items"))) return rc;
-    if ((rc = ensure(h, h->d_ctoff, std::max<size_t>(P.term_tab_off.size(), 1) * sizeof(int), "table offsets"))) return rc;
     if ((rc = ensure(h, h->d_codes, sizeof(codes), "coefficient codes"))) return rc;
-    CK(cudaMemcpyAsync(h->d_chunks.p, P.chunks.data(), P.chunks.size() * sizeof(ChunkHdr), cudaMemcpyHostToDevice, h->st), "upload chunks");
     CK(cudaMemcpyAsync(h->d_qchunks.p, P.quad_chunks.data(), P.quad_chunks.size() * sizeof(QuadChunkHdr),
                        cudaMemcpyHostToDevice, h->st),
        "upload quad chunks");
@@ -252,8 +238,6 @@ int upload_tables(nbs_ctx* h) {
                        h->st),
        "upload quad segments");
     CK(cudaMemcpyAsync(h->d_ctab.p, P.chunk_tab.data(), P.chunk_tab.size() * 2, cudaMemcpyHostToDevice, h->st), "upload chunk tables");
-    CK(cudaMemcpyAsync(h->d_citems.p, P.chunk_items.data(), P.chunk_items.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload chunk items");
-    CK(cudaMemcpyAsync(h->d_ctoff.p, P.term_tab_off.data(), P.term_tab_off.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload table offsets");
     CK(cudaMemcpyAsync(h->d_codes.p, codes, sizeof(codes), cudaMemcpyHostToDevice, h->st), "upload codes");
     CK(cudaStreamSynchronize(h->st), "upload sync");
   }
@@ -290,9 +274,7 @@ int upload_tables(nbs_ctx* h) {
        "upload momentum order");
     CK(cudaStreamSynchronize(h->st), "upload sync");
   }
-  CK(cudaMemcpyAsync(h->d_groups.p, P.groups.data(), P.groups.size() * sizeof(GroupHdr), cudaMemcpyHostToDevice, h->st), "upload groups");
   CK(cudaMemcpyAsync(h->d_gch.p, P.group_ch.data(), P.group_ch.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload group channels");
-  CK(cudaMemcpyAsync(h->d_items.p, P.items.data(), P.items.size() * sizeof(int), cudaMemcpyHostToDevice, h->st), "upload items");
   if ((rc = ensure(h, h->d_terms, std::max<size_t>(terms.size(), 1) * sizeof(DevTerm), "terms"))) return rc;
   if ((rc = ensure(h, h->d_chtb, P.ch_term_begin.size() * sizeof(int), "term ranges"))) return rc;
   if ((rc = ensure(h, h->d_chnl, std::max<size_t>(P.ch_fl.size(), 3) * sizeof(int), "flavour content"))) return rc;
@@ -472,12 +454,7 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
                              (float2*)h->Ft.p, h->flags, h->st),
          "contraction (tensor cores)");
     } else if (h->mode == NBS_BF16X3) {
-      if (!h->plan.chunks_ok) return fail(h, NBS_EINVAL, "BF16X3 needs channel tables that fit the chunk kernel");
-      CK(launch_contract_tc((const float2*)h->FB.p, h->L, (int)h->plan.chunks.size(), h->chunk_qb, h->d_chunks.p,
-                            (const int*)h->d_gch.p, (const int*)h->d_citems.p, (const DevTerm*)h->d_terms.p,
-                            (const int*)h->d_ctoff.p, (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p,
-                            h->chunk_st1, h->chunk_st2, h->chunk_slot, h->chunk_tab, (float2*)h->Ft.p, h->st),
-         "contraction (tensor cores)");
+      return fail(h, NBS_EINVAL, "BF16X3 needs channel tables that fit the quad-lane kernel");
     } else if (use_qseg) {
       CK(launch_contract_qseg((const float2*)h->FB.p, h->plan.ncells, h->L, (int)h->plan.quad_chunks.size(),
                               h->chunk_qb, h->d_qchunks.p, h->d_qsegs.p, h->plan.max_quad_segs,
@@ -485,29 +462,10 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
                               std::max(h->chunk_st1, h->chunk_st2), h->quad_slot, h->chunk_tab, h->chunk_row,
                               (float2*)h->Ft.p, h->flags, h->test_skip_slab, h->st),
          "contraction");
-    } else if (f32_chunks && (h->contract_cfg == 3 || h->contract_cfg == 0)) {
-      CK(launch_contract_chunk2((const float2*)h->FB.p, h->L, (int)h->plan.chunks.size(), h->chunk_qb,
-                                h->d_chunks.p, (const int*)h->d_gch.p, (const int*)h->d_citems.p,
-                                (const DevTerm*)h->d_terms.p, (const int*)h->d_ctoff.p,
-                                (const unsigned short*)h->d_ctab.p, (const float*)h->d_codes.p, h->chunk_st1,
-                                h->chunk_st2, h->chunk_slot, h->chunk_tab, h->chunk_row, (float2*)h->Ft.p, h->st),
-         "contraction");
-    } else if (f32_chunks && h->contract_cfg == 2) {
-      CK(launch_contract_chunk((const float2*)h->FB.p, h->L, (int)h->plan.chunks.size(), h->chunk_qb, h->d_chunks.p,
-                               (const int*)h->d_gch.p, (const int*)h->d_citems.p, (const DevTerm*)h->d_terms.p,
-                               (const int*)h->d_ctoff.p, (const unsigned short*)h->d_ctab.p,
-                               (const float*)h->d_codes.p, h->chunk_st1, h->chunk_st2, h->chunk_slot, h->chunk_tab,
-                               (float2*)h->Ft.p, h->st),
-         "contraction");
-    } else if (h->contract_cfg == 1) {
-      CK(launch_contract_slab<T>((const C<T>*)h->FB.p, h->L, (int)h->plan.groups.size(), h->d_groups.p,
-                                 (const int*)h->d_gch.p, (const int*)h->d_items.p, (const DevTerm*)h->d_terms.p,
-                                 (const Ent<T>*)h->d_e1.p, (const Ent<T>*)h->d_e2.p, h->slab_st1, h->slab_st2,
-                                 h->slab_nch, (C<T>*)h->Ft.p, h->st),
-         "contraction");
     } else {
-      // configs 1 and 2 name other kernels; where the chunk kernel cannot run (FP64) use the default shape
-      const int cfg = h->contract_cfg <= 3 ? 0 : h->contract_cfg;
+      // the thread-per-momentum kernel: FP64, and FP32 where neither the row nor the quad-lane tables fit;
+      // configs below 10 (0, 4) take its default shape
+      const int cfg = h->contract_cfg < 10 ? 0 : h->contract_cfg;
       CK(launch_contract<T>((const C<T>*)h->FB.p, h->L, (const DevTerm*)h->d_terms.p, (const int*)h->d_chtb.p, nch,
                             (const Ent<T>*)h->d_e1.p, (const Ent<T>*)h->d_e2.p, (C<T>*)h->Ft.p, cfg, h->st),
          "contraction");
@@ -645,8 +603,8 @@ int nbs_destroy(nbs_ctx* h) {
   cudaStreamSynchronize(h->st);
   if (h->cst) cudaStreamSynchronize(h->cst);
   DevBuf* bufs[] = {&h->props, &h->propsT, &h->FB, &h->Ft, &h->zm, &h->small, &h->stage[0], &h->stage[1],
-                    &h->d_terms, &h->d_chtb, &h->d_chnl, &h->d_e1, &h->d_e2, &h->d_cells, &h->d_groups,
-                    &h->d_gch, &h->d_items, &h->d_chunks, &h->d_qchunks, &h->d_qsegs, &h->d_ctab, &h->d_citems, &h->d_ctoff,
+                    &h->d_terms, &h->d_chtb, &h->d_chnl, &h->d_e1, &h->d_e2, &h->d_cells,
+                    &h->d_gch, &h->d_qchunks, &h->d_qsegs, &h->d_ctab,
                     &h->d_codes, &h->d_rchunks, &h->d_rtypes, &h->d_rdesc, &h->d_rent, &h->d_rrec, &h->d_rsegs,
                     &h->d_rch, &h->d_rscales, &h->d_qlist, &h->RQ, &h->s_FB, &h->s_FBm, &h->s_Ft, &h->s_F};
   for (DevBuf* b : bufs) dev_free(b->p, h->free_fn, h->free_user);
@@ -845,8 +803,8 @@ int nbs_set_param(nbs_ctx* h, int param, int value) {
   switch (param) {
     case NBS_PARAM_CONTRACT_CFG: {
       const int a = value / 10, w = value % 10;
-      if (!(value >= 0 && value <= 4) && !((a == 1 || a == 2 || a == 4) && (w == 1 || w == 2 || w == 4)))
-        return fail(h, NBS_EINVAL, "contraction config must be 0, 1, 2, 3, 4 or A*10+W with A, W in {1, 2, 4}");
+      if (!(value == 0 || value == 4) && !((a == 1 || a == 2 || a == 4) && (w == 1 || w == 2 || w == 4)))
+        return fail(h, NBS_EINVAL, "contraction config must be 0, 4 or A*10+W with A, W in {1, 2, 4}");
       h->contract_cfg = value;
       return NBS_OK;
     }

@@ -117,9 +117,11 @@ def test_fp32_all_channels_L4(nbs):
         assert rel(F32[c, 0], ref) < FP32_TOL, names[c]
 
 
-@pytest.mark.parametrize("cfg", [1, 2, 3, 22, 11])
+@pytest.mark.parametrize("cfg", [0, 4, 22, 11])
 def test_contraction_variants_all_channels(nbs, cfg):
-    """Every contraction kernel and launch shape against the oracle, FP64 and FP32, all 52 channels."""
+    """Every contraction kernel and launch shape against the oracle, FP64 and FP32, all 52 channels: the
+    default (FP32: the row kernels; FP64: thread per momentum), the quad-lane kernel (config 4; FP64 takes
+    its default) and two thread-per-momentum shapes."""
     L = 3
     props = seeded(1721, L, 1)
     names = nbs.channel_names()
@@ -132,15 +134,15 @@ def test_contraction_variants_all_channels(nbs, cfg):
         assert rel(F32[c, 0], ref) < FP32_TOL, (cfg, names[c])
 
 
-def test_chunk_kernel_forms_agree_bitwise(nbs):
-    """The two forms of the chunk contraction (configs 2, 3) do the same FP32 operations in the same
-    order: identical results, here with a momentum block (24) that leaves a ragged last block at 4^3.
-    The quad-lane kernel (config 0, the default) sums in another order: equal to FP32 rounding."""
+def test_row_contraction_ragged_block_deterministic(nbs):
+    """The row contraction with a momentum block (24) that leaves a ragged last block at 4^3: two runs
+    give identical results (the slot sums are deterministic), and they agree with the quad-lane kernel
+    (config 4, another summation order) to FP32 rounding."""
     L = 4
     props = seeded(1723, L, 1, decay=0.5)
     ids = list(range(nbs.channel_count()))
     out = []
-    for cfg in (2, 3, 0):
+    for cfg in (0, 0, 4):
         with nbs.Context(L, 1, precision=nbs.NBS_FP32) as ctx:
             ctx.set_param(ctx.PARAM_CONTRACT_CFG, cfg)
             ctx.set_param(ctx.PARAM_CHUNK_QBLOCK, 24)
@@ -155,10 +157,10 @@ def test_chunk_kernel_forms_agree_bitwise(nbs):
         assert rel(out[2][c], out[0][c]) < 1e-6, c
 
 
-@pytest.mark.parametrize("cfg", [0, 2])
+@pytest.mark.parametrize("cfg", [0])
 def test_bf16x3_tensor_core_path_all_channels(nbs, cfg):
-    """Split-BF16 x 3 contraction on the tensor cores (config 0: quad-lane fragments by movmatrix,
-    config 2: shared-memory staging): every channel against the oracle at 2e-5."""
+    """Split-BF16 x 3 contraction on the tensor cores (quad-lane fragments by movmatrix): every channel
+    against the oracle at 2e-5."""
     L = 4
     props = seeded(1722, L, 2, decay=0.5)
     names = nbs.channel_names()
