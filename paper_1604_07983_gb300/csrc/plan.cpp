@@ -916,6 +916,31 @@ std::string compile_plan(const std::vector<int>& ids, Plan& plan, int nflav) {
     }
     plan.ch_term_begin.push_back((int)plan.terms.size());
   }
+  // ---- keep only the stored cells some gather entry reads: the others would be built and transformed
+  // for nothing.  Every type keeps its cells in their order, renumbered; the entries follow.
+  {
+    std::vector<char> used((size_t)plan.ncells, 0);
+    for (int c : plan.ent1_cell) used[(size_t)c] = 1;
+    for (int c : plan.ent2_cell) used[(size_t)c] = 1;
+    std::vector<int> renum((size_t)plan.ncells, -1);
+    int kept = 0;
+    for (auto& T : types) {
+      BlockType& bt = T.bt;
+      std::vector<int> cells;
+      for (int k = 0; k < bt.ncell; ++k)
+        if (used[(size_t)(bt.cell_off + k)]) {
+          renum[(size_t)(bt.cell_off + k)] = kept + (int)cells.size();
+          cells.push_back(bt.cells[k]);
+        }
+      bt.cells = std::move(cells);
+      bt.ncell = (int)bt.cells.size();
+      bt.cell_off = kept;
+      kept += bt.ncell;
+    }
+    for (int& c : plan.ent1_cell) c = renum[(size_t)c];
+    for (int& c : plan.ent2_cell) c = renum[(size_t)c];
+    plan.ncells = kept;
+  }
   for (auto& T : types) plan.types.push_back(T.bt);
 
   // ---- slab groups for the momentum-slab contraction -------------------------
