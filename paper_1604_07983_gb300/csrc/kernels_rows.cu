@@ -168,18 +168,13 @@ __device__ __forceinline__ bool mb_wait(unsigned a, unsigned parity, volatile in
   return false;
 }
 
-// Phase A: every row of every type at momenta [0, V).  A warp item is (four consecutive momenta, eight
-// consecutive rows of one type): lane = 8 (momentum offset) + (row offset).  Row r (global, of type t)
-// at momentum q: unit q 2 NR + roff_t + r holds sink spins 0, 1, that unit + nrow_t spins 2, 3.  The row
-// tables sit in shared memory; a warp takes two items at a time and issues the loads of their first two
-// entries (nearly every row has one or two) before it uses any, so that four 32-byte loads per lane are in
-// flight.
-constexpr int EFF_THREADS = 256;
-
-struct EffItem {
-  long long q;
-  int r, cnt, off, base, roff, nrow;
-};
+// Phase A: every row of every type at momenta [0, V).  A block takes tiles of (eight consecutive rows of
+// one type, 32 consecutive momenta); warp w builds row w of the tile with lane = momentum offset, so the
+// loads of a cell are one contiguous 1 KB run (32 momenta x 32 bytes) and a warp walks its row's entries
+// in lockstep.  The tile goes through shared memory so that each momentum's eight rows leave as one
+// 128-byte line per plane.  Row r (global, of type t) at momentum q: unit q 2 NR + roff_t + r holds sink
+// spins 0, 1, that unit + nrow_t spins 2, 3.  The row tables sit in shared memory.
+constexpr int EFF_THREADS = 256;  // eight warps: the eight rows of a tile
 
 __global__ void __launch_bounds__(EFF_THREADS) k_eff_rows(const float4* __restrict__ FB, long long V,
                                                           const RowTypeHdr* __restrict__ types, int ntypes,
@@ -187,85 +182,83 @@ __global__ void __launch_bounds__(EFF_THREADS) k_eff_rows(const float4* __restri
                                                           const unsigned short* __restrict__ ent, int nent, int NR,
                                                           float4* __restrict__ RQ) {
   extern __shared__ __align__(16) unsigned char eff_smem[];
-  int* const TY = reinterpret_cast<int*>(eff_smem);                  // [ntypes][3]: base, roff, nrow
-  unsigned* const DS = reinterpret_cast<unsigned*>(eff_smem + 128);  // [NR]
-  unsigned short* const ES = reinterpret_cast<unsigned short*>(DS + NR);  // [nent]
-  for (int i = threadIdx.x; i < ntypes; i += blockDim.x) {
+  float4* const TT = reinterpret_cast<float4*>(eff_smem);            // tile [plane][32 momenta][8 rows]
+  int* const TY = reinterpret_cast<int*>(eff_smem + 2 * 32 * 8 * 16);  // [ntypes][3]: base, roff, nrow
+  unsigned* const DS = reinterpret_cast<unsigned*>(eff_smem + 2 * 32 * 8 * 16 + 128);  // [NR]
+  unsigned short* const ES = reinterpret_cast<unsigned short*>(DS + NR);                // [nent]
+  for (int i = threadIdx.x; i < ntypes; i += EFF_THREADS) {
     TY[3 * i] = types[i].base;
     TY[3 * i + 1] = types[i].roff;
     TY[3 * i + 2] = types[i].nrow;
   }
-  for (int i = threadIdx.x; i < NR; i += blockDim.x) DS[i] = desc[i];
-  for (int i = threadIdx.x; i < nent; i += blockDim.x) ES[i] = ent[i];
+  for (int i = threadIdx.x; i < NR; i += EFF_THREADS) DS[i] = desc[i];
+  for (int i = threadIdx.x; i < nent; i += EFF_THREADS) ES[i] = ent[i];
   __syncthreads();
 
-  const int lane = threadIdx.x & 31, noct = NR / 8;
-  const long long nitems = (V + 3) / 4 * noct;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  auto item = [&](long long it, EffItem& m) {
-    const long long qq = it / noct;
-    m.r = 8 * (int)(it - qq * noct) + (lane & 7);
-    m.q = 4 * qq + (lane >> 3);
-    const unsigned d = DS[m.r];
-    const int t = (int)(d >> 29);
-    m.cnt = (it < nitems && m.q < V) ? (int)((d >> 24) & 31u) : -1;  // -1: nothing to store
-    m.off = (int)(d & 0xFFFFFFu);
-    m.base = TY[3 * t];
-    m.roff = TY[3 * t + 1];
-    m.nrow = TY[3 * t + 2];
-  };
-  auto coef = [](unsigned x) {
-    const float c = (x & 0x2000u) ? 2.f : 1.f;
-    return (x & 0x1000u) ? -c : c;
-  };
-  auto src = [&](const EffItem& m, unsigned x) { return FB + ((long long)(m.base + (int)(x & 0xFFFu)) * V + m.q) * 2; };
-  auto fma4 = [](float4& a, float c, const float4& v) {
-    a.x = fmaf(c, v.x, a.x);
-    a.y = fmaf(c, v.y, a.y);
-    a.z = fmaf(c, v.z, a.z);
-    a.w = fmaf(c, v.w, a.w);
-  };
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (long long it = 2 * (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); it < nitems; it += 2 * nwarps) {
-    EffItem m[2];
-    item(it, m[0]);
-    item(it + 1, m[1]);
-    unsigned x[2][2];
-    float4 v[2][2][2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        x[k][j] = m[k].cnt > j ? (unsigned)ES[m[k].off + j] : 0u;
-        if (m[k].cnt > j) {
-          const float4* p = src(m[k], x[k][j]);
-          v[k][j][0] = __ldg(p);
-          v[k][j][1] = __ldg(p + 1);
-        } else {
-          v[k][j][0] = v[k][j][1] = z4;
-        }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, noct = NR / 8;
+  const long long nq32 = (V + 31) / 32, ntiles = nq32 * noct;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long qb = tile / noct;
+    const int oct = (int)(tile - qb * noct);
+    // build: warp w, row 8 oct + w, momentum 32 qb + lane
+    {
+      const int r = 8 * oct + w;
+      const long long q = 32 * qb + lane;
+      const unsigned d = DS[r];
+      const int cnt = (int)((d >> 24) & 31u), t = (int)(d >> 29);
+      const unsigned short* e = ES + (d & 0xFFFFFFu);
+      const float4* const col = FB + 2 * min(q, V - 1);  // momentum q of cell 0 (clamped: q >= V is not stored)
+      const long long cstride = 2 * V;
+      const int base = TY[3 * t];
+      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+      int j = 0;
+      for (; j + 1 < cnt; j += 2) {  // two entries at a time: four 16-byte loads in flight
+        const unsigned x0 = e[j], x1 = e[j + 1];
+        const float4* p0 = col + (long long)(base + (int)(x0 & 0xFFFu)) * cstride;
+        const float4* p1 = col + (long long)(base + (int)(x1 & 0xFFFu)) * cstride;
+        const float4 u0 = __ldg(p0), u1 = __ldg(p0 + 1), v0 = __ldg(p1), v1 = __ldg(p1 + 1);
+        float c0 = (x0 & 0x2000u) ? 2.f : 1.f, c1 = (x1 & 0x2000u) ? 2.f : 1.f;
+        c0 = (x0 & 0x1000u) ? -c0 : c0;
+        c1 = (x1 & 0x1000u) ? -c1 : c1;
+        a0.x = fmaf(c1, v0.x, fmaf(c0, u0.x, a0.x));
+        a0.y = fmaf(c1, v0.y, fmaf(c0, u0.y, a0.y));
+        a0.z = fmaf(c1, v0.z, fmaf(c0, u0.z, a0.z));
+        a0.w = fmaf(c1, v0.w, fmaf(c0, u0.w, a0.w));
+        a1.x = fmaf(c1, v1.x, fmaf(c0, u1.x, a1.x));
+        a1.y = fmaf(c1, v1.y, fmaf(c0, u1.y, a1.y));
+        a1.z = fmaf(c1, v1.z, fmaf(c0, u1.z, a1.z));
+        a1.w = fmaf(c1, v1.w, fmaf(c0, u1.w, a1.w));
       }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      if (m[k].cnt < 0) continue;
-      float4 a0 = z4, a1 = z4;
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const float c = m[k].cnt > j ? coef(x[k][j]) : 0.f;
-        fma4(a0, c, v[k][j][0]);
-        fma4(a1, c, v[k][j][1]);
+      if (j < cnt) {
+        const unsigned x0 = e[j];
+        const float4* p0 = col + (long long)(base + (int)(x0 & 0xFFFu)) * cstride;
+        const float4 u0 = __ldg(p0), u1 = __ldg(p0 + 1);
+        float c0 = (x0 & 0x2000u) ? 2.f : 1.f;
+        c0 = (x0 & 0x1000u) ? -c0 : c0;
+        a0.x = fmaf(c0, u0.x, a0.x);
+        a0.y = fmaf(c0, u0.y, a0.y);
+        a0.z = fmaf(c0, u0.z, a0.z);
+        a0.w = fmaf(c0, u0.w, a0.w);
+        a1.x = fmaf(c0, u1.x, a1.x);
+        a1.y = fmaf(c0, u1.y, a1.y);
+        a1.z = fmaf(c0, u1.z, a1.z);
+        a1.w = fmaf(c0, u1.w, a1.w);
       }
-      for (int j = 2; j < m[k].cnt; ++j) {
-        const unsigned xj = ES[m[k].off + j];
-        const float4* p = src(m[k], xj);
-        const float c = coef(xj);
-        fma4(a0, c, __ldg(p));
-        fma4(a1, c, __ldg(p + 1));
-      }
-      float4* dst = RQ + m[k].q * 2 * NR + m[k].roff + m[k].r;
-      dst[0] = a0;
-      dst[m[k].nrow] = a1;
+      TT[lane * 8 + w] = a0;
+      TT[256 + lane * 8 + w] = a1;
     }
+    __syncthreads();
+    // store: unit u of the tile = (plane h, momentum m, row k), two per thread
+    {
+      const int t = (int)(DS[8 * oct] >> 29);
+      const int roff = TY[3 * t + 1], nrow = TY[3 * t + 2];
+      for (int u = threadIdx.x; u < 512; u += EFF_THREADS) {
+        const int h = u >> 8, m = (u >> 3) & 31, k = u & 7;
+        const long long q = 32 * qb + m;
+        if (q < V) RQ[q * 2 * NR + roff + 8 * oct + k + h * nrow] = TT[h * 256 + m * 8 + k];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -484,13 +477,18 @@ cudaError_t launch_eff_rows(const float2* FB, long long V, const void* types, in
   if (!FB || !RQ || V <= 0 || NR <= 0 || NR % 8 || ntypes < 1 || ntypes > 8 || nent < 0 ||
       (reinterpret_cast<uintptr_t>(FB) & 15) || (reinterpret_cast<uintptr_t>(RQ) & 15))
     return cudaErrorInvalidValue;
-  const size_t smem = 128 + 4 * (size_t)NR + 2 * (size_t)nent;
+  const size_t smem = 2 * 32 * 8 * 16 + 128 + 4 * (size_t)NR + 2 * (size_t)nent;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_eff_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const long long items = (V + 3) / 4 * (NR / 8);
-  const long long blocks = std::min<long long>((items + 15) / 16, (long long)std::max(nsm, 1) * 4);
+  // exactly the blocks that are resident at once (a grid-stride loop: a block queued behind them would
+  // start only when one of them has finished all of its tiles)
+  int per_sm = 0;
+  cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eff_rows, EFF_THREADS, smem);
+  if (oe != cudaSuccess) return oe;
+  const long long tiles = (V + 31) / 32 * (NR / 8);
+  const long long blocks = std::min<long long>(tiles, (long long)std::max(nsm, 1) * std::max(per_sm, 1));
   k_eff_rows<<<(unsigned)blocks, EFF_THREADS, smem, st>>>(reinterpret_cast<const float4*>(FB), V,
                                                            (const RowTypeHdr*)types, ntypes, desc, ent, nent, NR,
                                                            reinterpret_cast<float4*>(RQ));
