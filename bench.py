@@ -37,7 +37,8 @@ FP32_LANES, SM_MAX_MHZ = 128, 2070.0   # FP32 lanes per SM; the clock used when 
 # `python bench.py --L 16 --T 2 --steps 1 --warmup 1 --e2e-steps 1 --no-cpu-baseline`
 # (dram__bytes_read.sum + dram__bytes_write.sum over 4096 momenta); an entry is dropped
 # whenever its kernel changes, until it is captured again
-DRAM_BYTES_PER_Q = {"k_contract_qseg": 1.255847e9 / 4096, "k_contract_rows": 0.687230e9 / 4096}
+DRAM_BYTES_PER_Q = {"k_contract_qseg": 1.255847e9 / 4096, "k_contract_rows": 0.682957e9 / 4096,
+                    "k_eff_rows": 0.912326e9 / 4096}
 
 
 def parse():
@@ -460,6 +461,14 @@ def run_ours(args, rank, world, local_rank):
                 "peak_source": peak_src,
                 "work_per_launch": "8 flop x 64 x sum|xi~| (=%d) x V complex MACs of Eq. (4.3)"
                                    % int(tb["terms"][:, 1].sum())}
+        if kname == "k_contract_rows" and tb.get("rows") is not None:
+            # what the kernel issues: products of one channel that name the same two rows are merged, so it
+            # runs fewer multiply-adds than the terms of Eq. (4.3) count (every record of every step, padding
+            # records included, is a 4 x 4 complex outer product)
+            nstep = int(sum(int(c[7]) for c in tb["rows"]["chunks"]))
+            issued = 128.0 * 32 * nstep * V
+            roof["issued"] = {"achieved": issued / (contract_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                              "work_per_launch": "8 flop x 16 x 32 records x %d steps x V" % nstep}
     else:
         hbm = peaks.get("hbm_gbs", 6800.0)
         if dominant == "fft_fwd":

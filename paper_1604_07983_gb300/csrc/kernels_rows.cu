@@ -66,7 +66,7 @@ __host__ __device__ inline RowLayout row_layout(int nrow1, int nrow2, int nslot,
   L.seg = o;
   o += (unsigned)nseg * 16u;
   L.sc = o;
-  o += 128u;
+  o += 4u * NBS_ROW_SCALES;
   L.cs = o;
   o += (unsigned)((2 * nch + nslot + 1 + 3) / 4) * 16u;
   L.mb = o;

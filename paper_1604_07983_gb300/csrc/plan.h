@@ -125,14 +125,15 @@ struct QuadSeg { int form, t1, t2, kbeg, kend, local, n1, n2; };
 // (its own kernel); phase B forms the product of Eq. (4.3) per chunk (whole
 // channels of one slab group, i.e. one pair of stored types) from the rows of
 // type1 at q and type2 at -q: record (xi~, s) names the row of B1 and of B2
-// for output source-spin pair s and the scale m1 m2 sign1 sign2 (a code into
-// Plan::row_scales).  Lane 4 kq + s of a warp takes record (8 step + kq, s),
+// for output source-spin pair s and a scale (a code into Plan::row_scales):
+// the sum of m1 m2 sign1 sign2 over the channel's products that name these two
+// rows for this s.  Lane 4 kq + s of a warp takes record (8 step + kq, s),
 // so a warp step covers eight shared indices of all four s.
 #define NBS_ROW_WARPS 12            // consumer warps of the product kernel (record ranges)
 #define NBS_ROW_HELPERS 4           // its helper warps (row copies, slot sums)
 #define NBS_ROW_STAGES 3            // momenta of rows in flight per block
 #define NBS_ROW_MAX_ROWS 4095       // row slots per type (12-bit row index in a record)
-#define NBS_ROW_SCALES 32           // scale codes (code 31 = 0)
+#define NBS_ROW_SCALES 64           // scale codes (code 63 = 0)
 #define NBS_ROW_SMEM_LIMIT 232448   // shared memory per block the tables are cut for (GB300 opt-in)
 // Rows of one stored type: per momentum they occupy 16-byte units
 // [2 roff, 2 roff + 2 nrow) of the momentum's block of 2 row_nr units: sink
@@ -189,7 +190,7 @@ struct Plan {
   std::vector<unsigned> row_rec;              // B1 row (bits 0..11) | B2 row << 12 | scale code << 24
   std::vector<int> row_ch;
   std::vector<RowSeg> row_segs;
-  std::vector<double> row_scales;             // NBS_ROW_SCALES signed scales, code 31 = 0
+  std::vector<double> row_scales;             // NBS_ROW_SCALES signed scales, code 63 = 0
   int row_smem = 0;                           // the largest chunk's shared memory (bytes)
   std::string row_why;                        // why rows_ok is false
   // flops of the contraction per q (complex multiply-adds), for rooflines

@@ -6,13 +6,16 @@
 // thousand distinct sums of stored cells.  So every distinct row is listed
 // once (phase A builds it per momentum for all four sink spins), and the
 // product of Eq. (4.3) walks records that name, for each shared index xi~ and
-// output source-spin pair s, the row of each side and a scale (phase B).
+// output source-spin pair s, the row of each side and a scale (phase B); the
+// products of a channel that name the same two rows for the same s are merged
+// into one record with the sum of their scales.
 //
 // A row is kept up to a scale: with m the smallest coefficient magnitude of
 // its term side, its coefficients are m times +-1 or +-2, and it is stored
 // with the sign that makes its first entry (lowest cell) positive.  The
-// record's scale is then m1 m2 sign1 sign2, one of at most 31 values over a
-// plan (a code into Plan::row_scales).
+// product's scale is then m1 m2 sign1 sign2; a record's scale, the sum over
+// the products it merges, is one of at most 63 values over a plan (a code
+// into Plan::row_scales).
 //
 // Over all channels the rows depend only on the stored type they sum, so the
 // rows of each type are listed once (Plan::row_types, row_desc, row_ent: the
@@ -145,7 +148,7 @@ int scale_code(std::vector<double>& scales, double v, std::string& why) {
   for (size_t i = 0; i < scales.size(); ++i)
     if (std::fabs(scales[i] - v) <= 1e-12 * std::fabs(v)) return (int)i;
   if ((int)scales.size() >= NBS_ROW_SCALES - 1) {
-    why = "more than 31 distinct term scales";
+    why = "more than 63 distinct product scales";
     return -1;
   }
   scales.push_back(v);
@@ -367,37 +370,51 @@ void build_row_chunks(Plan& plan, int smem_limit) {
         const int local = c - c0;
         const int ci = plan.group_ch[g.ch_off + c];
         plan.row_ch.push_back(ci);
-        long long nrec = 0;
+        // the channel's products, merged: for each output pair s, every (B1 row, B2 row) the terms name
+        // once, with the sum of their scales (products whose scales cancel are dropped) -- the same sum of
+        // Eq. (4.3), term by term, regrouped by the rows it multiplies
+        std::map<std::pair<int, int>, double> merged[4];
+        double smax = 0;
         for (int j = 0; j < (int)g_terms[gi][c].size(); ++j) {
           const TermHdr& th = plan.terms[plan.ch_term_begin[ci] + j];
           const TermRows& tr = g_terms[gi][c][j];
           const int nh1 = held_count(th.shape), nh2 = 4 / nh1;
-          for (int k = 0; k < th.K; ++k) {
+          for (int k = 0; k < th.K; ++k)
             for (int s = 0; s < 4; ++s) {
               int h1, h2;
               held_of(th.shape, s, h1, h2);
               const RowOf& a = tr.r1[(size_t)k * nh1 + h1];
               const RowOf& b = tr.r2[(size_t)k * nh2 + h2];
-              PRec r = {NBS_ROW_SCALES - 1, -1, -1};
-              if (!a.empty && !b.empty) {
-                r.code = scale_code(scales, tr.m1 * tr.m2 * a.sign * b.sign, why);
-                if (r.code < 0) {
-                  plan.row_why = why;
-                  return;
-                }
-                r.r1 = trows[t1].id.at(a.key);
-                r.r2 = trows[t2].id.at(b.key);
-              }
-              cb.prec.push_back(r);
+              if (a.empty || b.empty) continue;
+              const double v = tr.m1 * tr.m2 * a.sign * b.sign;
+              merged[s][{trows[t1].id.at(a.key), trows[t2].id.at(b.key)}] += v;
+              smax = std::max(smax, std::fabs(v));
             }
-            ++nrec;
+        }
+        // records in steps of eight per s (lane 4 kq + s takes the kq-th of its s in a step)
+        std::vector<PRec> lists[4];
+        size_t nmax = 0;
+        for (int s = 0; s < 4; ++s) {
+          for (auto& kv : merged[s]) {
+            if (std::fabs(kv.second) <= 1e-12 * smax) continue;  // the terms' scales cancel
+            PRec r = {scale_code(scales, kv.second, why), kv.first.first, kv.first.second};
+            if (r.code < 0) {
+              plan.row_why = why;
+              return;
+            }
+            lists[s].push_back(r);
           }
+          nmax = std::max(nmax, lists[s].size());
         }
-        while (nrec % 8) {
-          for (int s = 0; s < 4; ++s) cb.prec.push_back({NBS_ROW_SCALES - 1, -1, -1});
-          ++nrec;
+        const size_t nsteps = (nmax + 7) / 8;
+        for (size_t st = 0; st < nsteps; ++st) {
+          for (int kq = 0; kq < 8; ++kq)
+            for (int s = 0; s < 4; ++s) {
+              const size_t k = 8 * st + (size_t)kq;
+              cb.prec.push_back(k < lists[s].size() ? lists[s][k] : PRec{NBS_ROW_SCALES - 1, -1, -1});
+            }
+          cb.step_ch.push_back(local);
         }
-        for (long long i = 0; i < nrec / 8; ++i) cb.step_ch.push_back(local);
       }
       cbs.push_back(std::move(cb));
       c0 = c1;

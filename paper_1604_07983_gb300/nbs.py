@@ -176,7 +176,7 @@ def row_tables(L, p, get):
     return dict(warps=warps, chunks=get("ROWCHUNKS", (nck, 96), np.int32), ent=get("ROWENT", (max(nent, 1),), np.uint16),
                 desc=get("ROWDESC", (max(nrows, 1),), np.uint32), rec=get("ROWREC", (max(nrec, 1),), np.uint32),
                 ch=get("ROWCH", (max(nch, 1),), np.int32), segs=get("ROWSEGS", (max(nseg, 1), 4), np.int32),
-                scales=get("ROWSCALES", (32,), np.float64), types=get("ROWTYPES", (max(ntypes, 1), 8), np.int32),
+                scales=get("ROWSCALES", (64,), np.float64), types=get("ROWTYPES", (max(ntypes, 1), 8), np.int32),
                 smem=smem)
 
 
