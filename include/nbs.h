@@ -369,12 +369,14 @@ int nbs_plan_sizes(const nbs_plan* p, long long* sizes);
                                  (bits 12..13: +1, -1, +2, -2)                                             */
 #define NBS_PX_ROWDESC   22   /* uint32 per row (all types, row order): entry offset (bits 0..23) |
                                  count << 24 | type << 29; padding rows have count 0                      */
-#define NBS_PX_ROWREC    23   /* uint32 [step][8][4 s]: B1 row (bits 0..11, of type1) | B2 row << 12 (of
+#define NBS_PX_ROWREC    23   /* uint32 [step][4 g][8]: B1 row (bits 0..11, of type1) | B2 row << 12 (of
                                  type2) | scale code << 24; one record per distinct (s, B1 row, B2 row)
                                  of a channel, its scale the sum over the products that name them; four
                                  padding steps follow the last chunk                                      */
 #define NBS_PX_ROWCH     24   /* int32: request-order channel of each chunk channel                       */
-#define NBS_PX_ROWSEGS   25   /* int32 [nsegs][4]: first step, end step, chunk-local channel, 0           */
+#define NBS_PX_ROWSEGS   25   /* int32 [nsegs][4]: first step, end step, chunk-local channel, lane-group
+                                 map (records of lane group g, lanes 8 g + kq, are for output source-spin
+                                 pair (map >> 2 g) & 3)                                                   */
 #define NBS_PX_ROWSCALES 26   /* double [64]: the scale of each code (code 63 = 0)                          */
 #define NBS_PX_ROWTYPES  27   /* int32 [ntypes][8]: stored type's first cell, cells, first row, rows, 0... */
 int nbs_plan_export(const nbs_plan* p, int what, void* dst);

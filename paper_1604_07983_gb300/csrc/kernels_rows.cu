@@ -17,12 +17,13 @@
 //     One helper thread copies the rows of type1 at q and of type2 at -q into
 //     a ring of NBS_ROW_STAGES stages (two bulk copies per momentum, completed
 //     on the stage's mbarrier); twelve consumer warps form the products: lane
-//     4 kq + s takes record (8 step + kq, s) -- read from global memory
-//     (L1/L2), two steps ahead -- naming the B1 row and B2 row of shared index
-//     xi~ for output source-spin pair s and a scale; it forms the 4 x 4 outer
-//     product over the sink spins alpha1, alpha2 and accumulates 16 complex
-//     values.  At the end of each channel segment the warp sums over its eight
-//     kq lanes into its slot (one slot buffer per stage).  The four helper
+//     8 g + kq takes record (step, g, kq) -- read from global memory
+//     (L1/L2), two steps ahead -- naming a B1 row and a B2 row for the output
+//     source-spin pair s its segment gives lane group g, and a scale; it forms
+//     the 4 x 4 outer product over the sink spins alpha1, alpha2 and
+//     accumulates 16 complex values.  At the end of each segment (a run of
+//     steps of one channel and one group map) the warp sums over the eight kq
+//     lanes of each group into its slot (one slot buffer per stage).  The four helper
 //     warps sum the slots of a finished momentum in warp order
 //     (deterministic) into F~[ch][spin][q] and then refill that stage.
 // Consumers wait on full[stage] (the copies' bytes) and arrive on
@@ -92,33 +93,42 @@ __device__ __forceinline__ void mb_expect_tx(unsigned a, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes) : "memory");
 }
 
-// sum a lane's 32 floats over the eight lanes of equal s (xor 16, 8, 4),
-// halving the kept length at each stage: lane 4 kq + s ends with the floats
-// 4 kq .. 4 kq + 3 of its original 32, summed over kq
+// sum a lane's 32 floats over the eight lanes of its group g (xor 4, 2, 1),
+// halving the kept length at each stage: lane 8 g + kq ends with the floats
+// 4 kq .. 4 kq + 3 of its original 32, summed over the group
 template <int M>
 __device__ __forceinline__ void kq_reduce(float (&acc)[32], int lane) {
   if constexpr (M >= 4) {
-    const bool up = lane & M;
+    constexpr int D = M / 4;  // partner distance: kq bit 2, 1, 0 for kept lengths 16, 8, 4
+    const bool up = lane & D;
 #pragma unroll
     for (int j = 0; j < M; ++j) {
       const float keep = up ? acc[M + j] : acc[j];
       const float give = up ? acc[j] : acc[M + j];
-      acc[j] = keep + __shfl_xor_sync(0xffffffffu, give, M);
+      acc[j] = keep + __shfl_xor_sync(0xffffffffu, give, D);
     }
     kq_reduce<M / 2>(acc, lane);
   }
 }
 
-// acc holds complex 4 alpha1 + alpha2 (floats 2 c, 2 c + 1) for output pair s;
-// add the channel's sum into slot[16 alpha1 + 4 alpha2 + s] and clear acc
-__device__ __forceinline__ void rows_flush(float (&acc)[32], int lane, float2* slot) {
+// acc holds complex 4 alpha1 + alpha2 (floats 2 c, 2 c + 1) for the output pair s
+// of the lane's group g = lane >> 3, s = (map >> 2 g) & 3; add the segment's sum
+// into slot[16 alpha1 + 4 alpha2 + s] and clear acc.  Groups that share an s add
+// in turn, group 0 first.
+__device__ __forceinline__ void rows_flush(float (&acc)[32], int lane, float2* slot, int map) {
   kq_reduce<16>(acc, lane);
-  const int kq = lane >> 2, s = lane & 3;
+  const int kq = lane & 7, g = lane >> 3, s = (map >> (2 * g)) & 3;
   float2* o = slot + 8 * kq + s;  // complex 2 kq: alpha1 = kq >> 1, alpha2 = 2 (kq & 1)
-  o[0].x += acc[0];
-  o[0].y += acc[1];
-  o[4].x += acc[2];
-  o[4].y += acc[3];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    if (g == p) {
+      o[0].x += acc[0];
+      o[0].y += acc[1];
+      o[4].x += acc[2];
+      o[4].y += acc[3];
+    }
+    __syncwarp();
+  }
 #pragma unroll
   for (int j = 0; j < 32; ++j) acc[j] = 0.f;
 }
@@ -429,12 +439,14 @@ __global__ void __launch_bounds__((NBS_ROW_WARPS + NBS_ROW_HELPERS) * 32, 1) k_c
           }
       };
       int si = s_begin, seg_end = si < s_end ? SEG[si].send : 0, local = si < s_end ? SEG[si].local : 0;
+      int map = si < s_end ? SEG[si].map : 0;
       auto after_step = [&](int st) {
         if (st + 1 == seg_end) {
-          rows_flush(acc, lane, out_w + local * 64);
+          rows_flush(acc, lane, out_w + local * 64, map);
           if (++si < s_end) {
             seg_end = SEG[si].send;
             local = SEG[si].local;
+            map = SEG[si].map;
           }
         }
       };

@@ -127,8 +127,10 @@ struct QuadSeg { int form, t1, t2, kbeg, kend, local, n1, n2; };
 // type1 at q and type2 at -q: record (xi~, s) names the row of B1 and of B2
 // for output source-spin pair s and a scale (a code into Plan::row_scales):
 // the sum of m1 m2 sign1 sign2 over the channel's products that name these two
-// rows for this s.  Lane 4 kq + s of a warp takes record (8 step + kq, s),
-// so a warp step covers eight shared indices of all four s.
+// rows for this s.  Lane 8 g + kq of a warp takes record (step, g, kq): a
+// warp step covers eight records in each of four lane groups, and a group's
+// records are for one s (the step's group map), so that the four lists of a
+// channel, of unequal length, share the steps.
 #define NBS_ROW_WARPS 12            // consumer warps of the product kernel (record ranges)
 #define NBS_ROW_HELPERS 4           // its helper warps (row copies, slot sums)
 #define NBS_ROW_STAGES 3            // momenta of rows in flight per block
@@ -155,8 +157,9 @@ struct RowChunkHdr {
   int cfirst[NBS_ROW_WARPS];
   int pad[96 - 16 - 3 * NBS_ROW_WARPS];  // 96 ints
 };
-// Steps [sbeg, send) of chunk-local channel `local` (one flush at the end).
-struct RowSeg { int sbeg, send, local, pad; };
+// Steps [sbeg, send) of chunk-local channel `local` (one flush at the end);
+// lane group g (lanes 8 g + kq) holds records of output pair s = (map >> 2 g) & 3.
+struct RowSeg { int sbeg, send, local, map; };
 
 struct Plan {
   std::vector<int> channels;                  // built-in ids, in request order

@@ -156,11 +156,11 @@ int scale_code(std::vector<double>& scales, double v, std::string& why) {
 }
 
 // contiguous split of the chunk's steps into NBS_ROW_WARPS ranges: a warp's
-// cost is its steps plus kFlush per channel piece it holds; bisection on the
+// cost is its steps plus kFlush per segment (a run of one key) it holds; bisection on the
 // largest cost, greedy fill
 constexpr double kFlush = 2.0;
 
-std::vector<int> split_steps(const std::vector<int>& step_ch) {
+std::vector<int> split_steps(const std::vector<int>& step_ch) {  // a flush where the key changes
   const int n = (int)step_ch.size();
   auto fill = [&](double cap, std::vector<int>* starts) {
     int w = 0, cur = -1;
@@ -228,11 +228,11 @@ void color_rows(const std::vector<std::pair<const std::vector<PRecT>*, int>>& sr
   for (const auto& src : srcs) {
     const std::vector<PRecT>& prec = *src.first;
     const int side = src.second;
-    const size_t nq = prec.size() / 32;  // warp steps of 32 records
+    const size_t nq = prec.size() / 8;  // quarter-warps: lanes 8 q .. 8 q + 7 of a warp step
     for (size_t qi = 0; qi < nq; ++qi) {
-      int rows[32], m = 0;
-      for (int j = 0; j < 32; ++j) {
-        const PRecT& r = prec[qi * 32 + j];
+      int rows[8], m = 0;
+      for (int j = 0; j < 8; ++j) {
+        const PRecT& r = prec[qi * 8 + j];
         const int id = side ? r.r2 : r.r1;
         if (id < 0) continue;
         bool dup = false;
@@ -251,13 +251,16 @@ void color_rows(const std::vector<std::pair<const std::vector<PRecT>*, int>>& sr
   }
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return weight[a] > weight[b]; });
   int used[8] = {};
+  const int cap = (n + 7) / 8 + 1;  // classes stay within one row of even: padding rows cost bytes and room
   for (int r : order) {
     long long cost[8] = {};
     for (auto& kv : adj[r])
       if (color[kv.first] >= 0) cost[color[kv.first]] += kv.second;
-    int best = 0;
-    for (int c = 1; c < 8; ++c)
-      if (cost[c] < cost[best] || (cost[c] == cost[best] && used[c] < used[best])) best = c;
+    int best = -1;
+    for (int c = 0; c < 8; ++c)
+      if (used[c] < cap &&
+          (best < 0 || cost[c] < cost[best] || (cost[c] == cost[best] && used[c] < used[best])))
+        best = c;
     color[r] = best;
     ++used[best];
   }
@@ -268,9 +271,62 @@ void color_rows(const std::vector<std::pair<const std::vector<PRecT>*, int>>& sr
   npad = std::max(8, 8 * big);
 }
 
-}  // namespace
+// The records of one (channel, s) list, regrouped over the list's quarters (the eight lanes of one lane
+// group in one warp step): a 16-byte shared-memory load of a warp is served in four phases of eight lanes,
+// and a phase takes as many wavefronts as its fullest 16-byte bank group (row mod 8) has distinct rows.
+// Each quarter is filled greedily with the records that add no second row to a bank group on either side
+// (a row already in the quarter adds none), preferring the records whose bank groups are the most common
+// among those left; every quarter but the list's last stays full.
+template <typename PRecT>
+void regroup_quarters(std::vector<PRecT>& prec, const std::vector<size_t>& qs, const std::vector<int>& idx1,
+                      const std::vector<int>& idx2) {
+  std::vector<PRecT> pool;
+  for (size_t b : qs)
+    for (int k = 0; k < 8; ++k)
+      if (prec[b + k].r1 >= 0) pool.push_back(prec[b + k]);
+  int cnt1[8] = {}, cnt2[8] = {};
+  for (const PRecT& r : pool) {
+    ++cnt1[idx1[r.r1] & 7];
+    ++cnt2[idx2[r.r2] & 7];
+  }
+  std::vector<char> used(pool.size(), 0);
+  size_t left = pool.size();
+  for (size_t b : qs) {
+    int row1[8], row2[8];
+    for (int c = 0; c < 8; ++c) row1[c] = row2[c] = -1;
+    for (int k = 0; k < 8; ++k) {
+      PRecT pick = {NBS_ROW_SCALES - 1, -1, -1};
+      if (left) {
+        long best = -1;
+        int bpen = 0, bab = 0;
+        for (size_t j = 0; j < pool.size(); ++j) {
+          if (used[j]) continue;
+          const int c1 = idx1[pool[j].r1] & 7, c2 = idx2[pool[j].r2] & 7;
+          const int pen = (row1[c1] >= 0 && row1[c1] != pool[j].r1) + (row2[c2] >= 0 && row2[c2] != pool[j].r2);
+          const int ab = cnt1[c1] + cnt2[c2];
+          if (best < 0 || pen < bpen || (pen == bpen && ab > bab)) {
+            best = (long)j;
+            bpen = pen;
+            bab = ab;
+          }
+        }
+        used[best] = 1;
+        --left;
+        pick = pool[best];
+        const int c1 = idx1[pick.r1] & 7, c2 = idx2[pick.r2] & 7;
+        --cnt1[c1];
+        --cnt2[c2];
+        if (row1[c1] < 0) row1[c1] = pick.r1;
+        if (row2[c2] < 0) row2[c2] = pick.r2;
+      }
+      prec[b + k] = pick;
+    }
+  }
+}
 
-void build_row_chunks(Plan& plan, int smem_limit) {
+// One attempt at the row tables: chunks are cut with each type's rows estimated as its distinct rows
+// (rounded up to 8) plus `margin`, the room its bank colouring may add.
+void build_rows_once(Plan& plan, int smem_limit, int margin) {
   plan.rows_ok = false;
   plan.row_types.clear();
   plan.row_desc.clear();
@@ -327,7 +383,7 @@ void build_row_chunks(Plan& plan, int smem_limit) {
   // row counts after the bank colouring, estimated (8 colour classes of nearly equal size)
   std::vector<int> nrow_est(ntypes);
   for (int t = 0; t < ntypes; ++t) {
-    nrow_est[t] = (int)(trows[t].keys.size() + 7) / 8 * 8 + 32;
+    nrow_est[t] = (int)(trows[t].keys.size() + 7) / 8 * 8 + margin;
     if ((int)trows[t].keys.size() > NBS_ROW_MAX_ROWS) {
       plan.row_why = "more than 4095 distinct rows of one stored type";
       return;
@@ -340,7 +396,9 @@ void build_row_chunks(Plan& plan, int smem_limit) {
   struct ChunkBuild {
     RowChunkHdr h;
     std::vector<PRec> prec;
-    std::vector<int> step_ch;
+    std::vector<int> step_ch;   // chunk-local channel of each step
+    std::vector<int> step_map;  // its lane-group map: the s of group g in bits 2 g, 2 g + 1
+    std::vector<std::vector<size_t>> list_q;  // per (channel, s) list: the first record of each of its quarters
   };
   std::vector<ChunkBuild> cbs;
   for (size_t gi = 0; gi < plan.groups.size(); ++gi) {
@@ -351,11 +409,11 @@ void build_row_chunks(Plan& plan, int smem_limit) {
       int c1 = c0 + 1;
       for (; c1 < g.nch; ++c1) {  // take channel c1 as well?
         const int nch = c1 - c0 + 1;
-        if (row_chunk_smem(nrow_est[t1], nrow_est[t2], nch + NBS_ROW_WARPS, nch + NBS_ROW_WARPS, nch) >
+        if (row_chunk_smem(nrow_est[t1], nrow_est[t2], nch + NBS_ROW_WARPS, 4 * nch + NBS_ROW_WARPS, nch) >
             (size_t)smem_limit)
           break;
       }
-      if (row_chunk_smem(nrow_est[t1], nrow_est[t2], 1 + NBS_ROW_WARPS, 1 + NBS_ROW_WARPS, 1) > (size_t)smem_limit) {
+      if (row_chunk_smem(nrow_est[t1], nrow_est[t2], 1 + NBS_ROW_WARPS, 4 + NBS_ROW_WARPS, 1) > (size_t)smem_limit) {
         plan.row_why = "one channel's rows exceed a block's shared memory";
         return;
       }
@@ -391,9 +449,12 @@ void build_row_chunks(Plan& plan, int smem_limit) {
               smax = std::max(smax, std::fabs(v));
             }
         }
-        // records in steps of eight per s (lane 4 kq + s takes the kq-th of its s in a step)
+        // lane groups: lane 8 g + kq is in group g; a group takes eight records of one s per step, so that
+        // the list of s is cut into ceil(n_s / 8) group-steps.  The channel's group-steps (s = 0, 1, 2, 3 in
+        // turn) fill the four groups one after the other, H = ceil(total / 4) each, so that the lists of
+        // unequal length share the steps; a step's map names the s of each group (bits 2 g, 2 g + 1)
         std::vector<PRec> lists[4];
-        size_t nmax = 0;
+        std::vector<std::pair<int, size_t>> gs;  // (s, first record) of each group-step
         for (int s = 0; s < 4; ++s) {
           for (auto& kv : merged[s]) {
             if (std::fabs(kv.second) <= 1e-12 * smax) continue;  // the terms' scales cancel
@@ -404,16 +465,36 @@ void build_row_chunks(Plan& plan, int smem_limit) {
             }
             lists[s].push_back(r);
           }
-          nmax = std::max(nmax, lists[s].size());
+          for (size_t k = 0; k < lists[s].size(); k += 8) gs.push_back({s, k});
         }
-        const size_t nsteps = (nmax + 7) / 8;
-        for (size_t st = 0; st < nsteps; ++st) {
-          for (int kq = 0; kq < 8; ++kq)
-            for (int s = 0; s < 4; ++s) {
-              const size_t k = 8 * st + (size_t)kq;
-              cb.prec.push_back(k < lists[s].size() ? lists[s][k] : PRec{NBS_ROW_SCALES - 1, -1, -1});
+        const size_t H = (gs.size() + 3) / 4;
+        std::vector<size_t> qpos[4];
+        for (size_t e = 0; e < gs.size(); ++e)
+          qpos[gs[e].first].push_back(((cb.step_ch.size() + e % H) * 4 + e / H) * 8);
+        for (int s = 0; s < 4; ++s)
+          if (!qpos[s].empty()) cb.list_q.push_back(std::move(qpos[s]));
+        for (size_t st = 0; st < H; ++st) {
+          int map = 0;
+          for (int g = 0; g < 4; ++g) {
+            // a group past its last group-step keeps the s of its last one (padding records), so that
+            // its map does not change
+            const size_t e = (size_t)g * H + st;
+            const size_t last = std::min(gs.size(), (size_t)(g + 1) * H);
+            const int sg = e < last ? gs[e].first : ((size_t)g * H < last ? gs[last - 1].first : 0);
+            map |= sg << (2 * g);
+          }
+          for (int g = 0; g < 4; ++g)
+            for (int kq = 0; kq < 8; ++kq) {
+              const size_t e = (size_t)g * H + st;
+              PRec r = {NBS_ROW_SCALES - 1, -1, -1};
+              if (e < std::min(gs.size(), (size_t)(g + 1) * H)) {
+                const size_t k = gs[e].second + (size_t)kq;
+                if (k < lists[gs[e].first].size()) r = lists[gs[e].first][k];
+              }
+              cb.prec.push_back(r);
             }
           cb.step_ch.push_back(local);
+          cb.step_map.push_back(map);
         }
       }
       cbs.push_back(std::move(cb));
@@ -482,6 +563,10 @@ void build_row_chunks(Plan& plan, int smem_limit) {
     }
   }
 
+  // ---- each list's records regrouped over its quarters (final row numbers known) ----
+  for (ChunkBuild& cb : cbs)
+    for (const std::vector<size_t>& qs : cb.list_q) regroup_quarters(cb.prec, qs, idx[cb.h.type1], idx[cb.h.type2]);
+
   // ---- chunks: final records, warp ranges and segments, shared memory ----
   for (ChunkBuild& cb : cbs) {
     RowChunkHdr h = cb.h;
@@ -498,7 +583,10 @@ void build_row_chunks(Plan& plan, int smem_limit) {
                                (unsigned)r.code << 24);
     }
     h.nstep = (int)cb.step_ch.size();
-    const std::vector<int> starts = split_steps(cb.step_ch);
+    // a warp flushes where the channel or the group map changes
+    std::vector<int> key(cb.step_ch.size());
+    for (size_t i = 0; i < key.size(); ++i) key[i] = cb.step_ch[i] << 8 | cb.step_map[i];
+    const std::vector<int> starts = split_steps(key);
     h.seg_off = (int)plan.row_segs.size();
     int nslot = 0;
     for (int w = 0; w < NBS_ROW_WARPS; ++w) {
@@ -510,8 +598,8 @@ void build_row_chunks(Plan& plan, int smem_limit) {
       h.cfirst[w] = cb.step_ch[a];
       for (int i = a; i < b;) {
         int j = i;
-        while (j < b && cb.step_ch[j] == cb.step_ch[i]) ++j;
-        plan.row_segs.push_back({i, j, cb.step_ch[i], 0});
+        while (j < b && key[j] == key[i]) ++j;
+        plan.row_segs.push_back({i, j, cb.step_ch[i], cb.step_map[i]});
         i = j;
       }
       nslot += cb.step_ch[b - 1] - cb.step_ch[a] + 1;
@@ -533,6 +621,17 @@ void build_row_chunks(Plan& plan, int smem_limit) {
   for (size_t i = 0; i < scales.size(); ++i) plan.row_scales[i] = scales[i];
   plan.rows_ok = !plan.row_chunks.empty();
   if (!plan.rows_ok) plan.row_why = "no chunks";
+}
+
+}  // namespace
+
+void build_row_chunks(Plan& plan, int smem_limit) {
+  // a chunk cut on too small an estimate of its rows can exceed the limit once its rows are numbered:
+  // cut again with more room
+  for (int margin = 32; margin <= 512; margin *= 2) {
+    build_rows_once(plan, smem_limit, margin);
+    if (plan.rows_ok || plan.row_why != "a chunk exceeds a block's shared memory") return;
+  }
 }
 
 }  // namespace nbs
