@@ -185,6 +185,7 @@ __device__ __forceinline__ bool mb_wait(unsigned a, unsigned parity, volatile in
 // 128-byte line per plane.  Row r (global, of type t) at momentum q: unit q 2 NR + roff_t + r holds sink
 // spins 0, 1, that unit + nrow_t spins 2, 3.  The row tables sit in shared memory.
 constexpr int EFF_THREADS = 256;  // eight warps: the eight rows of a tile
+constexpr int EFF_TILE_BYTES = 2 * 2 * 32 * 8 * 16;  // two tile buffers
 
 __global__ void __launch_bounds__(EFF_THREADS) k_eff_rows(const float4* __restrict__ FB, long long V,
                                                           const RowTypeHdr* __restrict__ types, int ntypes,
@@ -192,10 +193,12 @@ __global__ void __launch_bounds__(EFF_THREADS) k_eff_rows(const float4* __restri
                                                           const unsigned short* __restrict__ ent, int nent, int NR,
                                                           float4* __restrict__ RQ) {
   extern __shared__ __align__(16) unsigned char eff_smem[];
-  float4* const TT = reinterpret_cast<float4*>(eff_smem);            // tile [plane][32 momenta][8 rows]
-  int* const TY = reinterpret_cast<int*>(eff_smem + 2 * 32 * 8 * 16);  // [ntypes][3]: base, roff, nrow
-  unsigned* const DS = reinterpret_cast<unsigned*>(eff_smem + 2 * 32 * 8 * 16 + 128);  // [NR]
-  unsigned short* const ES = reinterpret_cast<unsigned short*>(DS + NR);                // [nent]
+  // two tile buffers [buffer][plane][32 momenta][8 rows], the row slot k of momentum m at k ^ (m & 7), so
+  // that the eight lanes of a quarter-warp (eight momenta, one row) write eight different bank groups
+  float4* const TT = reinterpret_cast<float4*>(eff_smem);
+  int* const TY = reinterpret_cast<int*>(eff_smem + EFF_TILE_BYTES);                 // [ntypes][3]
+  unsigned* const DS = reinterpret_cast<unsigned*>(eff_smem + EFF_TILE_BYTES + 128);  // [NR]
+  unsigned short* const ES = reinterpret_cast<unsigned short*>(DS + NR);              // [nent]
   for (int i = threadIdx.x; i < ntypes; i += EFF_THREADS) {
     TY[3 * i] = types[i].base;
     TY[3 * i + 1] = types[i].roff;
@@ -207,9 +210,13 @@ __global__ void __launch_bounds__(EFF_THREADS) k_eff_rows(const float4* __restri
 
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, noct = NR / 8;
   const long long nq32 = (V + 31) / 32, ntiles = nq32 * noct;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  int buf = 0;
+  // one barrier per tile: a warp that reaches the build of tile i + 2 (into this buffer again) has passed
+  // the barrier after the build of tile i + 1, which every warp reaches only after its stores of tile i
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, buf ^= 1) {
     const long long qb = tile / noct;
     const int oct = (int)(tile - qb * noct);
+    float4* const TB = TT + buf * 512;
     // build: warp w, row 8 oct + w, momentum 32 qb + lane
     {
       const int r = 8 * oct + w;
@@ -221,41 +228,40 @@ __global__ void __launch_bounds__(EFF_THREADS) k_eff_rows(const float4* __restri
       const long long cstride = 2 * V;
       const int base = TY[3 * t];
       float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+      auto add = [&](unsigned x, const float4& u0, const float4& u1) {
+        float c = (x & 0x2000u) ? 2.f : 1.f;
+        c = (x & 0x1000u) ? -c : c;
+        a0.x = fmaf(c, u0.x, a0.x);
+        a0.y = fmaf(c, u0.y, a0.y);
+        a0.z = fmaf(c, u0.z, a0.z);
+        a0.w = fmaf(c, u0.w, a0.w);
+        a1.x = fmaf(c, u1.x, a1.x);
+        a1.y = fmaf(c, u1.y, a1.y);
+        a1.z = fmaf(c, u1.z, a1.z);
+        a1.w = fmaf(c, u1.w, a1.w);
+      };
       int j = 0;
-      for (; j + 1 < cnt; j += 2) {  // two entries at a time: four 16-byte loads in flight
-        const unsigned x0 = e[j], x1 = e[j + 1];
-        const float4* p0 = col + (long long)(base + (int)(x0 & 0xFFFu)) * cstride;
-        const float4* p1 = col + (long long)(base + (int)(x1 & 0xFFFu)) * cstride;
-        const float4 u0 = __ldg(p0), u1 = __ldg(p0 + 1), v0 = __ldg(p1), v1 = __ldg(p1 + 1);
-        float c0 = (x0 & 0x2000u) ? 2.f : 1.f, c1 = (x1 & 0x2000u) ? 2.f : 1.f;
-        c0 = (x0 & 0x1000u) ? -c0 : c0;
-        c1 = (x1 & 0x1000u) ? -c1 : c1;
-        a0.x = fmaf(c1, v0.x, fmaf(c0, u0.x, a0.x));
-        a0.y = fmaf(c1, v0.y, fmaf(c0, u0.y, a0.y));
-        a0.z = fmaf(c1, v0.z, fmaf(c0, u0.z, a0.z));
-        a0.w = fmaf(c1, v0.w, fmaf(c0, u0.w, a0.w));
-        a1.x = fmaf(c1, v1.x, fmaf(c0, u1.x, a1.x));
-        a1.y = fmaf(c1, v1.y, fmaf(c0, u1.y, a1.y));
-        a1.z = fmaf(c1, v1.z, fmaf(c0, u1.z, a1.z));
-        a1.w = fmaf(c1, v1.w, fmaf(c0, u1.w, a1.w));
+      for (; j + 3 < cnt; j += 4) {  // four entries at a time: eight 16-byte loads in flight
+        unsigned x[4];
+        float4 u[4][2];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          x[k] = e[j + k];
+          const float4* p = col + (long long)(base + (int)(x[k] & 0xFFFu)) * cstride;
+          u[k][0] = __ldg(p);
+          u[k][1] = __ldg(p + 1);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) add(x[k], u[k][0], u[k][1]);
       }
-      if (j < cnt) {
-        const unsigned x0 = e[j];
-        const float4* p0 = col + (long long)(base + (int)(x0 & 0xFFFu)) * cstride;
-        const float4 u0 = __ldg(p0), u1 = __ldg(p0 + 1);
-        float c0 = (x0 & 0x2000u) ? 2.f : 1.f;
-        c0 = (x0 & 0x1000u) ? -c0 : c0;
-        a0.x = fmaf(c0, u0.x, a0.x);
-        a0.y = fmaf(c0, u0.y, a0.y);
-        a0.z = fmaf(c0, u0.z, a0.z);
-        a0.w = fmaf(c0, u0.w, a0.w);
-        a1.x = fmaf(c0, u1.x, a1.x);
-        a1.y = fmaf(c0, u1.y, a1.y);
-        a1.z = fmaf(c0, u1.z, a1.z);
-        a1.w = fmaf(c0, u1.w, a1.w);
+      for (; j < cnt; ++j) {
+        const unsigned x = e[j];
+        const float4* p = col + (long long)(base + (int)(x & 0xFFFu)) * cstride;
+        add(x, __ldg(p), __ldg(p + 1));
       }
-      TT[lane * 8 + w] = a0;
-      TT[256 + lane * 8 + w] = a1;
+      const int sw = w ^ (lane & 7);
+      TB[lane * 8 + sw] = a0;
+      TB[256 + lane * 8 + sw] = a1;
     }
     __syncthreads();
     // store: unit u of the tile = (plane h, momentum m, row k), two per thread
@@ -265,10 +271,9 @@ __global__ void __launch_bounds__(EFF_THREADS) k_eff_rows(const float4* __restri
       for (int u = threadIdx.x; u < 512; u += EFF_THREADS) {
         const int h = u >> 8, m = (u >> 3) & 31, k = u & 7;
         const long long q = 32 * qb + m;
-        if (q < V) RQ[q * 2 * NR + roff + 8 * oct + k + h * nrow] = TT[h * 256 + m * 8 + k];
+        if (q < V) RQ[q * 2 * NR + roff + 8 * oct + k + h * nrow] = TB[h * 256 + m * 8 + (k ^ (m & 7))];
       }
     }
-    __syncthreads();
   }
 }
 
@@ -489,7 +494,7 @@ cudaError_t launch_eff_rows(const float2* FB, long long V, const void* types, in
   if (!FB || !RQ || V <= 0 || NR <= 0 || NR % 8 || ntypes < 1 || ntypes > 8 || nent < 0 ||
       (reinterpret_cast<uintptr_t>(FB) & 15) || (reinterpret_cast<uintptr_t>(RQ) & 15))
     return cudaErrorInvalidValue;
-  const size_t smem = 2 * 32 * 8 * 16 + 128 + 4 * (size_t)NR + 2 * (size_t)nent;
+  const size_t smem = EFF_TILE_BYTES + 128 + 4 * (size_t)NR + 2 * (size_t)nent;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_eff_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -519,6 +519,18 @@ void build_rows_once(Plan& plan, int smem_limit, int margin) {
     }
     int npad = 0;
     color_rows(srcs, (int)trows[t].keys.size(), idx[t], npad);
+    // within each colour, rows numbered by decreasing entry count: the eight rows of an octet (one of each
+    // colour) that the row kernel builds side by side then have similar counts
+    {
+      std::vector<int> byc[8];
+      for (int i = 0; i < (int)idx[t].size(); ++i) byc[idx[t][i] & 7].push_back(i);
+      for (int c = 0; c < 8; ++c) {
+        std::stable_sort(byc[c].begin(), byc[c].end(), [&](int a, int b) {
+          return trows[t].keys[a]->size() > trows[t].keys[b]->size();
+        });
+        for (size_t k = 0; k < byc[c].size(); ++k) idx[t][byc[c][k]] = c + 8 * (int)k;
+      }
+    }
     if (npad > NBS_ROW_MAX_ROWS) {
       plan.row_why = "too many rows after bank colouring";
       return;
