@@ -96,7 +96,13 @@ int nbs_set_stream(nbs_ctx* h, void* stream);
  * context: the wall-source quark propagators S(x, t; t0) from which the
  * blocks of Eq. (4.1) are built (Sec. 2; u = d in the isospin limit).  Layout of each: [z][y][x][i = 3*alpha + a][j = 3*alpha' + a'],
  * V*144 complex numbers of `dtype`; on_device selects device or host
- * pointers.  The library copies; the caller keeps ownership.  0 <= t < T. */
+ * pointers.  The library copies; the caller keeps ownership.  0 <= t < T.
+ * A host copy is issued on the context's own load stream after the work
+ * already enqueued on the context's stream, so that it overlaps the compute
+ * of timeslices loaded before it; the blocks of t wait for it, and host
+ * memory given to it must stay unchanged until the next nbs_correlate,
+ * nbs_blocks or nbs_graph_launch (with wait) returns.  A device copy is
+ * issued on the context's stream. */
 int nbs_load_props(nbs_ctx* h, const void* u, const void* s, int t, int dtype, int on_device);
 /* The same for a context with flavours = 3: the u, d and s propagators
  * (same layout and dtype).  NBS_EINVAL on a flavours = 2 context (and

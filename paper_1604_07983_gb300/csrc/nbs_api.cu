@@ -66,6 +66,12 @@ struct nbs_ctx {
   cudaStream_t st = 0;
   cudaStream_t cst = nullptr;
   cudaEvent_t ev_done[2] = {nullptr, nullptr};   // staging buffer b copied out
+  // host-to-device propagator loads run on their own stream, after everything already on st; the blocks of
+  // timeslice t wait for ev_loaded[t] while load_pending[t] is set
+  cudaStream_t lst = nullptr;
+  cudaEvent_t ev_mark = nullptr;
+  std::vector<cudaEvent_t> ev_loaded;
+  std::vector<char> load_pending;
   cudaEvent_t ev_ready[2] = {nullptr, nullptr};  // staging buffer b written
   std::string err;
   nbs_free_fn free_fn = nullptr;  // allocator at creation
@@ -360,6 +366,10 @@ int build_blocks(nbs_ctx* h, int t) {
   if ((rc = ensure(h, h->propsT, (size_t)nf * 144 * V * sizeof(C<T>), "scaled propagators"))) return rc;
   if ((rc = ensure(h, h->FB, 4ull * P.ncells * V * sizeof(C<T>), "baryon blocks"))) return rc;
   const char* base = (const char*)h->props.p + (size_t)t * nf * V * 144 * sizeof(double2);
+  if (h->load_pending[t]) {  // its propagators are still being copied in on the load stream
+    CK(cudaStreamWaitEvent(h->st, h->ev_loaded[t], 0), "wait load");
+    h->load_pending[t] = 0;
+  }
   PropPtrs pp = {};
   for (int f = 0; f < nf; ++f) pp.p[f] = base + (size_t)f * V * 144 * sizeof(double2);
   const int c64 = h->have[t] == NBS_C64;
@@ -513,6 +523,7 @@ int correlate(nbs_ctx* h, int nch, int t0, int t1, void* out, int on_dev) {
   }
   if (!on_dev) CK(cudaStreamSynchronize(h->cst), "copy sync");
   CK(cudaStreamSynchronize(h->st), "sync");
+  CK(cudaStreamSynchronize(h->lst), "load sync");  // every load issued before the call has landed
   prof_resolve(h);
   if (*h->host_flags) {
     h->blocks_t = -1;
@@ -577,6 +588,13 @@ int create_ctx(nbs_ctx** out, int L, int T, int flavours, bool store) {
     cudaEventCreateWithFlags(&h->ev_done[b], cudaEventDisableTiming);
     cudaEventCreateWithFlags(&h->ev_ready[b], cudaEventDisableTiming);
   }
+  if ((e = cudaStreamCreateWithFlags(&h->lst, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&h->ev_mark, cudaEventDisableTiming)) != cudaSuccess) {
+    nbs_destroy(h);
+    return cuda_fail(nullptr, e, "load stream");
+  }
+  h->ev_loaded.assign(T, nullptr);
+  h->load_pending.assign(T, 0);
   if (cudaMallocHost(&h->host_flags, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     nbs_destroy(h);
@@ -602,6 +620,7 @@ int nbs_destroy(nbs_ctx* h) {
   if (!h) return NBS_OK;
   cudaStreamSynchronize(h->st);
   if (h->cst) cudaStreamSynchronize(h->cst);
+  if (h->lst) cudaStreamSynchronize(h->lst);
   DevBuf* bufs[] = {&h->props, &h->propsT, &h->FB, &h->Ft, &h->zm, &h->small, &h->stage[0], &h->stage[1],
                     &h->d_terms, &h->d_chtb, &h->d_chnl, &h->d_e1, &h->d_e2, &h->d_cells,
                     &h->d_gch, &h->d_qchunks, &h->d_qsegs, &h->d_ctab,
@@ -615,6 +634,10 @@ int nbs_destroy(nbs_ctx* h) {
   }
   if (h->cst) cudaStreamDestroy(h->cst);
   if (h->gst) cudaStreamDestroy(h->gst);
+  for (cudaEvent_t e : h->ev_loaded)
+    if (e) cudaEventDestroy(e);
+  if (h->ev_mark) cudaEventDestroy(h->ev_mark);
+  if (h->lst) cudaStreamDestroy(h->lst);
   if (h->host_flags) cudaFreeHost(h->host_flags);
   delete h;
   return NBS_OK;
@@ -642,8 +665,25 @@ int load_props(nbs_ctx* h, const void* const* src, int n, int t, int dtype, int 
   const size_t bytes = (size_t)h->V * 144 * (dtype == NBS_C128 ? sizeof(double2) : sizeof(float2));
   char* base = (char*)h->props.p + (size_t)t * h->nflav * h->V * 144 * sizeof(double2);
   cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  // from the host: on the load stream, after the work already on st (which may still read this slot), so
+  // that the copies overlap the compute of the timeslices loaded before; from the device: on st itself
+  // (the caller's producers of the source are ordered there)
+  cudaStream_t ls = h->st;
+  if (!on_device) {
+    if (!h->ev_loaded[t]) CK(cudaEventCreateWithFlags(&h->ev_loaded[t], cudaEventDisableTiming), "load event");
+    CK(cudaEventRecord(h->ev_mark, h->st), "load mark");
+    CK(cudaStreamWaitEvent(h->lst, h->ev_mark, 0), "load after st");
+    ls = h->lst;
+  } else if (h->load_pending[t]) {  // a host load of this slot still in flight
+    CK(cudaStreamWaitEvent(h->st, h->ev_loaded[t], 0), "wait load");
+    h->load_pending[t] = 0;
+  }
   for (int f = 0; f < n; ++f)
-    CK(cudaMemcpyAsync(base + (size_t)f * h->V * 144 * sizeof(double2), src[f], bytes, k, h->st), "copy propagator");
+    CK(cudaMemcpyAsync(base + (size_t)f * h->V * 144 * sizeof(double2), src[f], bytes, k, ls), "copy propagator");
+  if (!on_device) {
+    CK(cudaEventRecord(h->ev_loaded[t], h->lst), "loaded");
+    h->load_pending[t] = 1;
+  }
   h->have[t] = (signed char)dtype;
   if (h->blocks_t == t) h->blocks_t = -1;
   return NBS_OK;
@@ -676,6 +716,7 @@ int nbs_blocks(nbs_ctx* h, int t) {
   if (rc) return rc;
   CK(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->st), "NaN flag");
   CK(cudaStreamSynchronize(h->st), "sync");
+  CK(cudaStreamSynchronize(h->lst), "load sync");
   prof_resolve(h);
   if (*h->host_flags) {
     h->blocks_t = -1;
@@ -724,6 +765,8 @@ int nbs_graph_capture(nbs_ctx* h, const int* channel_ids, int n_channels, int t_
   if (!h->gst && (e = cudaStreamCreateWithFlags(&h->gst, cudaStreamNonBlocking)) != cudaSuccess)
     return cuda_fail(h, e, "capture stream");
   CK(cudaStreamSynchronize(h->st), "sync before capture");
+  CK(cudaStreamSynchronize(h->lst), "loads before capture");  // no wait on a load event inside the capture
+  std::fill(h->load_pending.begin(), h->load_pending.end(), 0);
   cudaStream_t user = h->st;
   h->st = h->gst;
   if ((e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed)) != cudaSuccess) {
@@ -768,10 +811,16 @@ int nbs_graph_launch(nbs_graph* graph, int wait) {
     if (h->have[t] != graph->have[t - graph->t0])
       return fail(h, NBS_ESTATE, "propagator storage of timeslice " + std::to_string(t) + " changed since the capture");
   *h->host_flags = 0;
+  for (int t = graph->t0; t < graph->t1; ++t)  // propagators loaded since the capture
+    if (h->load_pending[t]) {
+      CK(cudaStreamWaitEvent(h->st, h->ev_loaded[t], 0), "wait load");
+      h->load_pending[t] = 0;
+    }
   CK(cudaGraphLaunch(graph->exec, h->st), "graph launch");
   h->blocks_t = -1;
   if (!wait) return NBS_OK;
   CK(cudaStreamSynchronize(h->st), "sync");
+  CK(cudaStreamSynchronize(h->lst), "load sync");
   if (*h->host_flags & 2) return fail(h, NBS_ETIMEOUT, "a slab copy wait in the contraction gave up");
   if (*h->host_flags) return fail(h, NBS_ENAN, "non-finite value in the propagators");
   return NBS_OK;
