@@ -392,7 +392,7 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     # five repetitions of the whole sequence (load and correlate, each including its copies); the median
-    # is reported, all three are listed
+    # is reported, all five are listed
     reps = []
     for _ in range(5):
         if dist:
