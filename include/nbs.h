@@ -382,7 +382,8 @@ int nbs_plan_sizes(const nbs_plan* p, long long* sizes);
 #define NBS_PX_ROWCH     24   /* int32: request-order channel of each chunk channel                       */
 #define NBS_PX_ROWSEGS   25   /* int32 [nsegs][4]: first step, end step, chunk-local channel, lane-group
                                  map (records of lane group g, lanes 8 g + kq, are for output source-spin
-                                 pair (map >> 2 g) & 3)                                                   */
+                                 pair (map >> 2 g) & 3; bits 8 + 2 g: the group's turn among the groups
+                                 of its s when the warp adds them into the slot, bits 16..18: the turns) */
 #define NBS_PX_ROWSCALES 26   /* double [64]: the scale of each code (code 63 = 0)                          */
 #define NBS_PX_ROWTYPES  27   /* int32 [ntypes][8]: stored type's first cell, cells, first row, rows, 0... */
 int nbs_plan_export(const nbs_plan* p, int what, void* dst);

@@ -114,14 +114,15 @@ __device__ __forceinline__ void kq_reduce(float (&acc)[32], int lane) {
 // acc holds complex 4 alpha1 + alpha2 (floats 2 c, 2 c + 1) for the output pair s
 // of the lane's group g = lane >> 3, s = (map >> 2 g) & 3; add the segment's sum
 // into slot[16 alpha1 + 4 alpha2 + s] and clear acc.  Groups that share an s add
-// in turn, group 0 first.
+// in turn, lowest group first (map bits 8 + 2 g: the group's turn; bits 16..18:
+// the number of turns).
 __device__ __forceinline__ void rows_flush(float (&acc)[32], int lane, float2* slot, int map) {
   kq_reduce<16>(acc, lane);
   const int kq = lane & 7, g = lane >> 3, s = (map >> (2 * g)) & 3;
+  const int rank = (map >> (8 + 2 * g)) & 3, passes = (map >> 16) & 7;  // turn of this group, turns
   float2* o = slot + 8 * kq + s;  // complex 2 kq: alpha1 = kq >> 1, alpha2 = 2 (kq & 1)
-#pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    if (g == p) {
+  for (int p = 0; p < passes; ++p) {
+    if (rank == p) {
       o[0].x += acc[0];
       o[0].y += acc[1];
       o[4].x += acc[2];
@@ -254,7 +255,16 @@ __global__ void __launch_bounds__(EFF_THREADS) k_eff_rows(const float4* __restri
 #pragma unroll
         for (int k = 0; k < 4; ++k) add(x[k], u[k][0], u[k][1]);
       }
-      for (; j < cnt; ++j) {
+      if (j + 1 < cnt) {  // two more (most rows have two entries): four loads in flight
+        const unsigned x0 = e[j], x1 = e[j + 1];
+        const float4* p0 = col + (long long)(base + (int)(x0 & 0xFFFu)) * cstride;
+        const float4* p1 = col + (long long)(base + (int)(x1 & 0xFFFu)) * cstride;
+        const float4 u0 = __ldg(p0), u1 = __ldg(p0 + 1), v0 = __ldg(p1), v1 = __ldg(p1 + 1);
+        add(x0, u0, u1);
+        add(x1, v0, v1);
+        j += 2;
+      }
+      if (j < cnt) {
         const unsigned x = e[j];
         const float4* p = col + (long long)(base + (int)(x & 0xFFFu)) * cstride;
         add(x, __ldg(p), __ldg(p + 1));

@@ -158,7 +158,8 @@ struct RowChunkHdr {
   int pad[96 - 16 - 3 * NBS_ROW_WARPS];  // 96 ints
 };
 // Steps [sbeg, send) of chunk-local channel `local` (one flush at the end);
-// lane group g (lanes 8 g + kq) holds records of output pair s = (map >> 2 g) & 3.
+// lane group g (lanes 8 g + kq) holds records of output pair s = (map >> 2 g) & 3;
+// bits 8 + 2 g: the group's turn among the groups of its s, bits 16..18: the turns.
 struct RowSeg { int sbeg, send, local, map; };
 
 struct Plan {

@@ -611,7 +611,17 @@ void build_rows_once(Plan& plan, int smem_limit, int margin) {
       for (int i = a; i < b;) {
         int j = i;
         while (j < b && key[j] == key[i]) ++j;
-        plan.row_segs.push_back({i, j, cb.step_ch[i], cb.step_map[i]});
+        // the group map, each group's rank among the groups of its s (bits 8 + 2 g), and the number of
+        // groups that share the most common s (bits 16..18): the flush adds the groups in that many turns
+        const int m = cb.step_map[i];
+        int word = m, passes = 1;
+        for (int g = 0; g < 4; ++g) {
+          int rank = 0;
+          for (int h = 0; h < g; ++h) rank += ((m >> (2 * h)) & 3) == ((m >> (2 * g)) & 3);
+          word |= rank << (8 + 2 * g);
+          passes = std::max(passes, rank + 1);
+        }
+        plan.row_segs.push_back({i, j, cb.step_ch[i], word | passes << 16});
         i = j;
       }
       nslot += cb.step_ch[b - 1] - cb.step_ch[a] + 1;

@@ -516,6 +516,11 @@ def test_row_tables_reproduce_the_term_products(lib, ids):
             segs = rt["segs"][seg_off + seg_base[w]: seg_off + seg_base[w + 1]]
             for sb, se, local, gmap in segs:
                 assert cfirst[w] <= local < cfirst[w] + out_base[w + 1] - out_base[w]
+                # the flush's turns: group g's rank among the lower groups of its s, and the largest count
+                sg = [(gmap >> 2 * g) & 3 for g in range(4)]
+                ranks = [sum(sg[h] == sg[g] for h in range(g)) for g in range(4)]
+                assert [(gmap >> 8 + 2 * g) & 3 for g in range(4)] == ranks
+                assert gmap >> 16 == max(ranks) + 1
                 seen[sb:se] += 1
                 ch = rt["ch"][ch_off + local]
                 for st in range(sb, se):
