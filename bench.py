@@ -37,8 +37,8 @@ FP32_LANES, SM_MAX_MHZ = 128, 2070.0   # FP32 lanes per SM; the clock used when 
 # `python bench.py --L 16 --T 2 --steps 1 --warmup 1 --e2e-steps 1 --no-cpu-baseline`
 # (dram__bytes_read.sum + dram__bytes_write.sum over 4096 momenta); an entry is dropped
 # whenever its kernel changes, until it is captured again
-DRAM_BYTES_PER_Q = {"k_contract_qseg": 1.255847e9 / 4096, "k_contract_rows": 0.629183e9 / 4096,
-                    "k_eff_rows": 0.900247e9 / 4096}
+DRAM_BYTES_PER_Q = {"k_contract_qseg": 1.255847e9 / 4096, "k_contract_rows": 0.631365e9 / 4096,
+                    "k_eff_rows": 0.900618e9 / 4096}
 
 
 def parse():
