@@ -192,24 +192,20 @@ __global__ void __launch_bounds__(256) k_restore(const C<T>* __restrict__ Ft, lo
   double2* dst = out + ch * ch_stride;
   const long long stride = (long long)gridDim.x * blockDim.x;
   if constexpr (sizeof(T) == 4) {
+    // one complex value per lane and load: each warp store writes 512 contiguous bytes
     constexpr int RS = 4;
     const float inv = 1.0f / (float)norm;
-    const float4* s4 = reinterpret_cast<const float4*>(src);  // n is even, Ft 16-byte aligned
-    const long long n2 = n / 2;
-    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n2; i0 += RS * stride) {
-      float4 z[RS];
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += RS * stride) {
+      float2 z[RS];
 #pragma unroll
       for (int u = 0; u < RS; ++u) {
         const long long i = i0 + u * stride;
-        z[u] = i < n2 ? __ldcs(s4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        z[u] = i < n ? __ldcs(reinterpret_cast<const float2*>(src) + i) : make_float2(0.f, 0.f);
       }
 #pragma unroll
       for (int u = 0; u < RS; ++u) {
         const long long i = i0 + u * stride;
-        if (i < n2) {
-          dst[2 * i] = make_double2(scaled_double(z[u].x * inv, ex), scaled_double(z[u].y * inv, ex));
-          dst[2 * i + 1] = make_double2(scaled_double(z[u].z * inv, ex), scaled_double(z[u].w * inv, ex));
-        }
+        if (i < n) __stcs(dst + i, make_double2(scaled_double(z[u].x * inv, ex), scaled_double(z[u].y * inv, ex)));
       }
     }
   } else {
@@ -253,7 +249,7 @@ template <typename T>
 cudaError_t launch_restore(const C<T>* Ft, int V, int nch, const int* ch_fl, const int* exps, int nflav, double2* out,
                            long long ch_stride, cudaStream_t st, long long norm) {
   long long n = 64LL * V;
-  if (sizeof(T) == 4) n /= 8;  // 16-byte loads, four per thread per pass
+  if (sizeof(T) == 4) n /= 4;  // four values per thread per pass
   int bx = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096));
   dim3 grid(bx, nch);
   k_restore<T><<<grid, 256, 0, st>>>(Ft, (long long)V, ch_fl, exps, nflav, out, ch_stride, norm ? norm : (long long)V);
